@@ -1,0 +1,188 @@
+/*
+ * sgweno.h -- C ABI of the GB300 sparse-grid fifth-order WENO library (libsgweno.so).
+ *
+ * The library advances a scalar conservation law u_t + div f(u) = 0 (Eq. 1 of Zhu &
+ * Zhang, arXiv 2007.10196) on every semi-coarsened grid of the sparse-grid combination
+ * technique with the fifth-order finite-difference WENO scheme and Lax-Friedrichs flux
+ * splitting (Section 2.1, Eqs. 2-7) inside third-order TVD Runge-Kutta (Section 2.2),
+ * then prolongs every grid onto the finest grid with fifth-order WENO interpolation
+ * (Section 2.2.1, Eqs. 8-11) and forms the signed combination sum (Eqs. 12-15).  The
+ * three steps are the algorithm of Section 2.2.2.
+ *
+ * Conventions shared by every call:
+ *  - All functions return sg_status (SG_OK = 0).  Nothing aborts, traps or throws across
+ *    the ABI.  After any error the handle stays valid and destroyable; sg_last_error()
+ *    returns a message for the calling thread's last failure.
+ *  - Handles are not thread safe: one host thread at a time per handle.
+ *  - Host buffers passed in are owned by the caller and only read or written during the
+ *    call.  Device memory is owned by the library (allocated through the allocator hook if
+ *    one is installed, else cudaMalloc) and released by sg_destroy.
+ *  - Grid arrays are stored axis 0 fastest: index = i_0 + n_0 (i_1 + n_1 (i_2 + ...)).
+ *  - Grid g has levels l^g and n_k = N_r 2^{l^g_k} periodic nodes x_j = lo_k + j h_k,
+ *    h_k = (hi_k - lo_k)/n_k, j = 0..n_k-1 (vertex-centred, Section 2.2).
+ *  - Grids are enumerated q = 0..d-1, levels with |l| = N_L - q in lexicographic order
+ *    (l_0 most significant); grid g has combination coefficient (-1)^q C(d-1, q), Eq. (13).
+ *  - There is no CPU fallback.  Every computation runs in the library's CUDA kernels on
+ *    the current CUDA device; SG_ERR_CUDA reports a CUDA runtime failure.
+ */
+#ifndef SGWENO_H
+#define SGWENO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SG_OK = 0,
+    SG_ERR_ARG = 1,         /* invalid argument (range, size, NULL pointer) */
+    SG_ERR_STATE = 2,       /* call out of order (e.g. step before init) */
+    SG_ERR_NOMEM = 3,       /* device or host allocation failed */
+    SG_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    SG_ERR_NONFINITE = 5,   /* a NaN or Inf appeared in the solution */
+    SG_ERR_TIMEOUT = 6,     /* a bounded wait ran out */
+    SG_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
+} sg_status;
+
+/* PDE of Eq. (1): linear advection f_k(u) = a_k u, or Burgers f_k(u) = u^2/2 on every axis. */
+enum { SG_PDE_ADVECTION = 0, SG_PDE_BURGERS = 1 };
+/* Boundary conditions: periodic only. */
+enum { SG_BC_PERIODIC = 0 };
+/* Precision of the component-grid states and the WENO arithmetic.  The combination sum
+ * (the finest-grid accumulator) and every reduction are FP64 in both. */
+enum { SG_F64 = 0, SG_F32 = 1 };
+/* SG_PLAIN: one kernel launch per component grid per RK stage.
+ * SG_BATCHED: one persistent launch per RK stage over a (grid, tile) work queue covering
+ * every grid of the handle (or of every member of a batch). */
+enum { SG_PLAIN = 0, SG_BATCHED = 1 };
+/* Spatial scheme: WENO5-JS nonlinear weights (Eq. 5) or the fifth-order linear scheme that
+ * replaces them by d_r = (0.1, 0.6, 0.3) (Section 3). */
+enum { SG_WENO5 = 0, SG_LINEAR5 = 1 };
+/* Prolongation: WENO5 interpolation (Eq. 11) or fifth-order Lagrange (Eq. 8). */
+enum { SG_PROLONG_WENO5 = 0, SG_PROLONG_LAGRANGE5 = 1 };
+/* Time step, common to every grid and set by the finest grid (Section 3):
+ * SG_DT_POW53: dt = dt_coef * h^{5/3}, h = min_k (hi_k - lo_k)/(N_r 2^{N_L});
+ * SG_DT_CFL:   dt = cfl / sum_k (alpha_k / h_k), alpha_k = max over all grids of
+ *              max |f_k'(u)| at the start of the step.
+ * Either way the last step is shortened so that the run ends exactly at t_end. */
+enum { SG_DT_POW53 = 0, SG_DT_CFL = 1 };
+/* Initial condition kinds for sg_init. SG_IC_SINE: u_0(x) = p0 + p1 sin(p2 (x_0+...+x_{d-1}) + p3). */
+enum { SG_IC_SINE = 0 };
+/* Reductions (FP64).  MASS = sum u prod h, ENERGY = sum u^2 prod h, MIN/MAX of the values;
+ * L1_EXACT = mean |u - u_exact|, LINF_EXACT = max |u - u_exact| against the exact solution of
+ * the SG_IC_SINE initial condition at the current time (advection: translation; Burgers:
+ * characteristic solution by Newton's method, valid before the shock time). */
+enum {
+    SG_REDUCE_MASS = 0, SG_REDUCE_ENERGY = 1, SG_REDUCE_MIN = 2, SG_REDUCE_MAX = 3,
+    SG_REDUCE_L1_EXACT = 4, SG_REDUCE_LINF_EXACT = 5
+};
+
+#define SG_MAX_DIM 6
+#define SG_WHICH_COMBINED (-1)
+
+typedef struct sg_ctx *sg_handle;
+
+/* Parameters.  Fill with sg_params_init, then override fields. */
+typedef struct {
+    size_t struct_size;          /* sizeof(sg_params), set by sg_params_init */
+    double lo[SG_MAX_DIM];       /* domain [lo_k, hi_k] per axis; default [0, 4] */
+    double hi[SG_MAX_DIM];
+    int bc[SG_MAX_DIM];          /* SG_BC_PERIODIC */
+    double adv_speed[SG_MAX_DIM];/* a_k for linear advection; default 1 */
+    int precision;               /* SG_F64 (default) or SG_F32 */
+    int exec;                    /* SG_PLAIN (default) or SG_BATCHED */
+    int scheme;                  /* SG_WENO5 (default) or SG_LINEAR5 */
+    int prolong;                 /* SG_PROLONG_WENO5 (default) or SG_PROLONG_LAGRANGE5 */
+    double eps;                  /* epsilon of Eqs. (5) and (9); default 1e-3 */
+    int dt_rule;                 /* SG_DT_POW53 (default) or SG_DT_CFL */
+    double dt_coef;              /* default 1.0 */
+    double cfl;                  /* default 0.4 */
+    void *cuda_stream;           /* cudaStream_t to run on; NULL = a stream the handle owns */
+    int graph_steps;             /* time steps per captured CUDA graph; 0 = default (16), <0 = no graph */
+    int tile_points;             /* points per work-queue tile; 0 = autotune */
+} sg_params;
+
+/* Fills *p with the defaults listed above.  SG_ERR_ARG if p is NULL. */
+sg_status sg_params_init(sg_params *p);
+
+/* Creates a sparse-grid problem (Section 2.2): dim in [1, 6], root_cells = N_r >= 5 (the
+ * stencil needs five distinct points on every periodic line), level = N_L with
+ * 0 <= N_L <= 16 and N_r 2^{N_L} <= 2^20, pde one of SG_PDE_*.  Allocates every component
+ * grid's three RK arrays on the device.  *out receives the handle.  Errors: SG_ERR_ARG for
+ * out-of-range arguments, SG_ERR_UNSUPPORTED for a non-periodic bc, SG_ERR_NOMEM, SG_ERR_CUDA. */
+sg_status sg_create(int dim, int root_cells, int level, int pde, const sg_params *params,
+                    sg_handle *out);
+
+/* Step 1 of the algorithm: restricts an analytic initial condition to every component grid
+ * on the device (point values at the nodes) and sets t = 0.  ic_kind = SG_IC_SINE with
+ * n_params = 4 (p0, p1, p2, p3).  SG_ERR_ARG on a wrong kind or count. */
+sg_status sg_init(sg_handle h, int ic_kind, const double *ic_params, int n_params);
+
+/* Sets component grid `grid` from a host array of its n_0 n_1 ... values in the handle's
+ * precision (double for SG_F64, float for SG_F32), bytes = count * element size, and sets
+ * t = 0.  SG_ERR_ARG if grid is out of range or bytes does not match. */
+sg_status sg_init_grid(sg_handle h, int grid, const void *host_values, size_t bytes);
+
+/* Step 2: advances every component grid with the common time step until t = t_end (last
+ * step shortened) or until max_steps further steps have been taken.  *t_reached (may be
+ * NULL) receives the time reached (for a batch: the smallest over members).  Errors:
+ * SG_ERR_STATE before init, SG_ERR_NONFINITE if a stage produced NaN/Inf (the state then
+ * holds that stage's output), SG_ERR_ARG if t_end is not finite or max_steps < 0. */
+sg_status sg_step(sg_handle h, double t_end, long max_steps, double *t_reached);
+
+/* Step 3: prolongs every component grid onto the finest grid (axis 0 first) and forms
+ * uhat = sum_g c_g P U_g in FP64 on the device.  For a batch, does so for every member.
+ * SG_ERR_STATE before init. */
+sg_status sg_prolong_combine(sg_handle h);
+
+/* Copies to the host: which = SG_WHICH_COMBINED (-1) the FP64 combined solution on the
+ * finest grid ((N_r 2^{N_L})^d doubles), or which = g >= 0 component grid g in the handle's
+ * precision.  dst_bytes must be at least the size.  Synchronises the handle's stream.
+ * SG_ERR_STATE for -1 before sg_prolong_combine, SG_ERR_ARG for a small buffer. */
+sg_status sg_read(sg_handle h, int which, void *host_dst, size_t dst_bytes);
+
+/* FP64 reduction of the combined solution (which = -1) or of grid g, kind one of
+ * SG_REDUCE_*.  L1_EXACT / LINF_EXACT need which = -1 and an SG_IC_SINE initial condition
+ * (SG_ERR_STATE otherwise). */
+sg_status sg_reduce(sg_handle h, int which, int kind, double *out);
+
+/* Number of component grids G. */
+sg_status sg_num_grids(sg_handle h, int *n);
+
+/* levels[dim], shape[dim] (node counts) and combination coefficient of grid g; any output
+ * pointer may be NULL. */
+sg_status sg_grid_info(sg_handle h, int g, int *levels, long *shape, double *coeff);
+
+/* Time and number of steps taken since the last init. */
+sg_status sg_time(sg_handle h, double *t, long *steps);
+
+/* Groups n independent problems (each from sg_create) into one batch: sg_step on the batch
+ * advances every member, each with its own time step, with one persistent launch per RK
+ * stage over all members' grids; members that reach t_end drop out.  Members must share
+ * dim, pde, precision, scheme and eps.  The batch does not own its members: destroy the
+ * batch first, then the members.  sg_read / sg_reduce / sg_init apply to members only. */
+sg_status sg_batch_create(const sg_handle *members, int n, sg_handle *batch);
+
+/* Releases the handle and its device memory.  NULL is accepted. */
+sg_status sg_destroy(sg_handle h);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char *sg_last_error(void);
+
+/* Optional device allocator hook (e.g. a framework's caching allocator).  alloc returns a
+ * device pointer of at least `bytes` bytes aligned to 256, or NULL; release frees it.
+ * Pass NULLs to restore cudaMalloc/cudaFree.  Must not be changed while handles exist. */
+typedef void *(*sg_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*sg_free_fn)(void *ptr, size_t bytes, void *ctx);
+sg_status sg_set_allocator(sg_alloc_fn alloc, sg_free_fn release, void *ctx);
+
+/* Build and kernel information, for diagnostics and the benchmark: *n_launches receives the
+ * number of kernels this handle launched since creation. */
+sg_status sg_launch_count(sg_handle h, long *n_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGWENO_H */

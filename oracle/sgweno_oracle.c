@@ -1,0 +1,606 @@
+/*
+ * sgweno_oracle.c -- plain, slow FP64 CPU oracle for the sparse-grid fifth-order WENO
+ * method of Zhu & Zhang, "Fast sparse grid simulations of fifth order WENO scheme for
+ * high dimensional hyperbolic PDEs" (arXiv 2007.10196).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg may load this library.  The CUDA library never calls it, and the two
+ * share no code, headers or tables.
+ *
+ * Every routine is scalar double arithmetic written in the order the paper prints the
+ * formula, with no blocking, fusion or reordering.  It must be compiled with
+ * -ffp-contract=off so that no multiply-add is fused; then each line below is a fixed
+ * sequence of IEEE-754 double operations.
+ *
+ * Equation numbers are the paper's (global numbering): (2) flux difference, (3)-(6) the
+ * WENO5 reconstruction, (7) Lax-Friedrichs splitting, (8)-(11) WENO5 interpolation,
+ * (12)-(15) the combination formulas.
+ *
+ * Readings where the paper is silent (all shared with the CUDA path by specification):
+ *  - grid nodes are vertex-centred and periodic: n_k = N_r 2^{l_k} unique nodes
+ *    x_j = lo_k + j h_k, h_k = (hi_k - lo_k)/n_k (Section 2.2);
+ *  - the TVD-RK3 scheme cited in Section 2.2 is the Shu-Osher form;
+ *  - the LF alpha of (7) is max |f_k'(u)| over one component grid, recomputed from the
+ *    input of every RK stage;
+ *  - the time step is common to all grids and set by the finest grid (Section 3):
+ *    dt = coef * h^{5/3} (accuracy tests) or dt = cfl / sum_k(alpha_k / h_k) with
+ *    alpha_k the maximum over all grids; the last step is shortened to land on T;
+ *  - the WENO interpolation for x in [x_{i-1/2}, x_{i+1/2}) assigns a fine node to the
+ *    nearest coarse node, a midpoint to the right-hand node; at a coincident node (s = 0)
+ *    the interpolant is the node value itself, and an axis already at the finest level
+ *    is copied, not interpolated;
+ *  - prolongation runs axis 0, 1, ..., d-1 (Section 2.2.1);
+ *  - the combination sums grids in enumeration order (q = 0, 1, ...; lexicographic
+ *    levels within each q, l_0 most significant), into an accumulator that starts at 0.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXD 6
+
+typedef struct {
+    int dim;           /* d, 1..6 */
+    int nr;            /* N_r, root cells per axis */
+    int nl;            /* N_L, finest level */
+    int pde;           /* 0: linear advection f_k = a_k u;  1: Burgers f_k = u^2/2 */
+    int scheme;        /* 0: WENO5-JS weights (5);  1: fifth-order linear scheme, w_r = d_r */
+    int prolong;       /* 0: WENO5 interpolation (11);  1: fifth-order Lagrange (8) */
+    double eps;        /* epsilon of (5) and (9) */
+    double lo[ORC_MAXD], hi[ORC_MAXD];
+    double adv[ORC_MAXD];   /* a_k for linear advection */
+} orc_problem;
+
+/* ------------------------------------------------------------------------------------
+ * Grid set, Section 2.2 and combination formula (13):
+ *   coefficient of every grid with |l| = N_L - q is (-1)^q C(d-1, q), q = 0..d-1.
+ * ---------------------------------------------------------------------------------- */
+static long binom(int n, int k)
+{
+    long r = 1;
+    int i;
+    if (k < 0 || k > n) return 0;
+    for (i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+/* Enumerates the grids; writes levels[g*dim + k] and coeff[g] if non-NULL.  Returns G. */
+int orc_grid_set(int dim, int nl, int *levels, double *coeff)
+{
+    int g = 0, q, k;
+    int l[ORC_MAXD];
+    if (dim < 1 || dim > ORC_MAXD || nl < 0) return -1;
+    for (q = 0; q < dim; ++q) {
+        int target = nl - q;
+        if (target < 0) break;
+        /* lexicographic walk over l in [0, nl]^dim, l_0 most significant */
+        for (k = 0; k < dim; ++k) l[k] = 0;
+        for (;;) {
+            int s = 0;
+            for (k = 0; k < dim; ++k) s += l[k];
+            if (s == target) {
+                if (levels) for (k = 0; k < dim; ++k) levels[g * dim + k] = l[k];
+                if (coeff) coeff[g] = (double)((q % 2 == 0) ? 1 : -1) * (double)binom(dim - 1, q);
+                ++g;
+            }
+            /* increment the last axis first so that l_0 varies slowest */
+            k = dim - 1;
+            while (k >= 0) {
+                if (l[k] < nl) { ++l[k]; break; }
+                l[k] = 0;
+                --k;
+            }
+            if (k < 0) break;
+        }
+    }
+    return g;
+}
+
+static long grid_points(const orc_problem *P, const int *levels, long *n)
+{
+    long tot = 1;
+    int k;
+    for (k = 0; k < P->dim; ++k) {
+        n[k] = (long)P->nr << levels[k];
+        tot *= n[k];
+    }
+    return tot;
+}
+
+long orc_grid_points(const orc_problem *P, const int *levels)
+{
+    long n[ORC_MAXD];
+    return grid_points(P, levels, n);
+}
+
+/* Node spacing of one axis: h_k = (hi_k - lo_k) / n_k. */
+static double spacing(const orc_problem *P, int k, long nk)
+{
+    return (P->hi[k] - P->lo[k]) / (double)nk;
+}
+
+/* ------------------------------------------------------------------------------------
+ * One-sided WENO5 reconstruction, Section 2.1, Eqs. (3)-(6).
+ * (a, b, c, d, e) = (f_{i-2}, f_{i-1}, f_i, f_{i+1}, f_{i+2}) gives fhat_{i+1/2} for the
+ * positive wind; the negative wind uses the mirror image (f_{i+3}, ..., f_{i-1}).
+ * ---------------------------------------------------------------------------------- */
+double orc_weno5_side(double a, double b, double c, double d, double e, double eps, int linear)
+{
+    /* candidate fluxes, Eq. (4) */
+    double q0 = (1.0 / 3.0) * a - (7.0 / 6.0) * b + (11.0 / 6.0) * c;
+    double q1 = -(1.0 / 6.0) * b + (5.0 / 6.0) * c + (1.0 / 3.0) * d;
+    double q2 = (1.0 / 3.0) * c + (5.0 / 6.0) * d - (1.0 / 6.0) * e;
+    double al0, al1, al2;
+    if (linear) {
+        /* fifth-order linear scheme: w_r = d_r (Section 3) */
+        al0 = 0.1;
+        al1 = 0.6;
+        al2 = 0.3;
+    } else {
+        /* smoothness indicators, Eq. (6) */
+        double t0 = a - 2.0 * b + c, s0 = a - 4.0 * b + 3.0 * c;
+        double t1 = b - 2.0 * c + d, s1 = b - d;
+        double t2 = c - 2.0 * d + e, s2 = 3.0 * c - 4.0 * d + e;
+        double b0 = (13.0 / 12.0) * (t0 * t0) + 0.25 * (s0 * s0);
+        double b1 = (13.0 / 12.0) * (t1 * t1) + 0.25 * (s1 * s1);
+        double b2 = (13.0 / 12.0) * (t2 * t2) + 0.25 * (s2 * s2);
+        /* unnormalised weights, Eq. (5): alpha_r = d_r / (eps + beta_r)^2 */
+        al0 = 0.1 / ((eps + b0) * (eps + b0));
+        al1 = 0.6 / ((eps + b1) * (eps + b1));
+        al2 = 0.3 / ((eps + b2) * (eps + b2));
+    }
+    /* Eq. (3) with w_r = alpha_r / sum alpha */
+    return (al0 * q0 + al1 * q1 + al2 * q2) / (al0 + al1 + al2);
+}
+
+/* Flux of one axis, Eq. (1): f_k(u) = a_k u (advection) or u^2/2 (Burgers). */
+static double flux(const orc_problem *P, int k, double u)
+{
+    if (P->pde == 1) return (0.5 * u) * u;
+    return P->adv[k] * u;
+}
+
+/* |f_k'(u)|: |a_k| (advection) or |u| (Burgers). */
+static double wave_speed(const orc_problem *P, int k, double u)
+{
+    if (P->pde == 1) return fabs(u);
+    return fabs(P->adv[k]);
+}
+
+/* Lax-Friedrichs alpha of Eq. (7) for axis k over one grid: max_j |f_k'(u_j)|. */
+double orc_lf_alpha(const orc_problem *P, const int *levels, const double *u, int k)
+{
+    long n[ORC_MAXD];
+    long N = grid_points(P, levels, n), p;
+    double a = 0.0;
+    for (p = 0; p < N; ++p) {
+        double s = wave_speed(P, k, u[p]);
+        if (s > a) a = s;
+    }
+    return a;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Spatial operator L(u) = - sum_k (fhat_{i+1/2} - fhat_{i-1/2}) / h_k, Eq. (2) applied
+ * dimension by dimension (Section 2.1), with the LF split (7) and fhat = fhat^+ + fhat^-.
+ * L accumulates axis 0 first: L = ((0 - D_0) - D_1) - ..., D_k = (F_r - F_l) * (1/h_k).
+ * ---------------------------------------------------------------------------------- */
+void orc_spatial_operator(const orc_problem *P, const int *levels, const double *u, double *L)
+{
+    long n[ORC_MAXD], stride[ORC_MAXD];
+    long N = grid_points(P, levels, n), p;
+    int k;
+    stride[0] = 1;
+    for (k = 1; k < P->dim; ++k) stride[k] = stride[k - 1] * n[k - 1];
+    for (p = 0; p < N; ++p) L[p] = 0.0;
+
+    for (k = 0; k < P->dim; ++k) {
+        long nk = n[k], sk = stride[k], i, line;
+        double alpha = orc_lf_alpha(P, levels, u, k);
+        double rdx = 1.0 / spacing(P, k, nk);
+        double *fp = (double *)malloc(sizeof(double) * nk);
+        double *fm = (double *)malloc(sizeof(double) * nk);
+        double *F = (double *)malloc(sizeof(double) * nk);
+        long nlines = N / nk;
+        for (line = 0; line < nlines; ++line) {
+            /* base offset of this line: the index with i_k = 0 */
+            long below = line % sk, above = line / sk;
+            long base = below + above * sk * nk;
+            for (i = 0; i < nk; ++i) {
+                double uj = u[base + i * sk];
+                double fj = flux(P, k, uj);
+                fp[i] = 0.5 * (fj + alpha * uj);
+                fm[i] = 0.5 * (fj - alpha * uj);
+            }
+            for (i = 0; i < nk; ++i) {
+                /* interface i+1/2, periodic neighbours */
+                long im2 = (i - 2 + 2 * nk) % nk, im1 = (i - 1 + nk) % nk;
+                long ip1 = (i + 1) % nk, ip2 = (i + 2) % nk, ip3 = (i + 3) % nk;
+                double fplus = orc_weno5_side(fp[im2], fp[im1], fp[i], fp[ip1], fp[ip2],
+                                              P->eps, P->scheme == 1);
+                double fminus = orc_weno5_side(fm[ip3], fm[ip2], fm[ip1], fm[i], fm[im1],
+                                               P->eps, P->scheme == 1);
+                F[i] = fplus + fminus;
+            }
+            for (i = 0; i < nk; ++i) {
+                long il = (i - 1 + nk) % nk;
+                L[base + i * sk] = L[base + i * sk] - (F[i] - F[il]) * rdx;
+            }
+        }
+        free(fp);
+        free(fm);
+        free(F);
+    }
+}
+
+/* ------------------------------------------------------------------------------------
+ * Third-order TVD Runge-Kutta (Shu-Osher form), cited in Section 2.2:
+ *   u1 = u + dt L(u)
+ *   u2 = 3/4 u + 1/4 (u1 + dt L(u1))
+ *   u  = 1/3 u + 2/3 (u2 + dt L(u2))
+ * work must hold 3 * N doubles.
+ * ---------------------------------------------------------------------------------- */
+void orc_rk3_step(const orc_problem *P, const int *levels, double *u, double dt, double *work)
+{
+    long n[ORC_MAXD];
+    long N = grid_points(P, levels, n), p;
+    double *u1 = work, *u2 = work + N, *L = work + 2 * N;
+    orc_spatial_operator(P, levels, u, L);
+    for (p = 0; p < N; ++p) u1[p] = u[p] + dt * L[p];
+    orc_spatial_operator(P, levels, u1, L);
+    for (p = 0; p < N; ++p) u2[p] = 0.75 * u[p] + 0.25 * (u1[p] + dt * L[p]);
+    orc_spatial_operator(P, levels, u2, L);
+    for (p = 0; p < N; ++p) u[p] = (1.0 / 3.0) * u[p] + (2.0 / 3.0) * (u2[p] + dt * L[p]);
+}
+
+/* Finest-grid spacing per axis: (hi_k - lo_k) / (N_r 2^{N_L}). */
+static double fine_spacing(const orc_problem *P, int k)
+{
+    return (P->hi[k] - P->lo[k]) / (double)((long)P->nr << P->nl);
+}
+
+/* Nominal time step, Section 3.
+ * rule 0: dt = coef * (min_k h_k)^{5/3} on the finest grid.
+ * rule 1: dt = cfl / sum_k (alpha_k / h_k), alpha_k = max over all grids of max|f_k'(u)|.
+ * grids: all component grids concatenated in enumeration order. */
+double orc_dt(const orc_problem *P, int G, const int *levels, const double *grids,
+              int rule, double coef, double cfl)
+{
+    int k, g;
+    if (rule == 0) {
+        double h = fine_spacing(P, 0);
+        for (k = 1; k < P->dim; ++k) {
+            double hk = fine_spacing(P, k);
+            if (hk < h) h = hk;
+        }
+        return coef * pow(h, 5.0 / 3.0);
+    } else {
+        double s = 0.0;
+        for (k = 0; k < P->dim; ++k) {
+            double a = 0.0;
+            const double *u = grids;
+            for (g = 0; g < G; ++g) {
+                double ag = orc_lf_alpha(P, levels + g * P->dim, u, k);
+                if (ag > a) a = ag;
+                u += orc_grid_points(P, levels + g * P->dim);
+            }
+            s = s + a / fine_spacing(P, k);
+        }
+        return cfl / s;
+    }
+}
+
+/* ------------------------------------------------------------------------------------
+ * Step 2 of the algorithm (Section 2.2.2): march every component grid with the common
+ * time step until t_end (last step shortened) or max_steps steps.  Returns the number of
+ * steps taken; *t_out receives the time reached.
+ * ---------------------------------------------------------------------------------- */
+long orc_solve(const orc_problem *P, int G, const int *levels, double *grids, double t0,
+               double t_end, long max_steps, int rule, double coef, double cfl, double *t_out)
+{
+    long Nmax = 0, steps = 0;
+    int g;
+    double t = t0;
+    double *work;
+    for (g = 0; g < G; ++g) {
+        long Ng = orc_grid_points(P, levels + g * P->dim);
+        if (Ng > Nmax) Nmax = Ng;
+    }
+    work = (double *)malloc(sizeof(double) * 3 * Nmax);
+    while (t < t_end && steps < max_steps) {
+        double dt = orc_dt(P, G, levels, grids, rule, coef, cfl);
+        double *u = grids;
+        if (dt > t_end - t) dt = t_end - t;
+        for (g = 0; g < G; ++g) {
+            orc_rk3_step(P, levels + g * P->dim, u, dt, work);
+            u += orc_grid_points(P, levels + g * P->dim);
+        }
+        t = t + dt;
+        ++steps;
+    }
+    free(work);
+    if (t_out) *t_out = t;
+    return steps;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Step 1: restriction of u_0(x) = b + a sin(w * (x_0 + ... + x_{d-1}) + phi) to a grid
+ * ("functions are evaluated at grid points").  The sum runs over axes in order.
+ * ---------------------------------------------------------------------------------- */
+void orc_restrict_sine(const orc_problem *P, const int *levels, double b, double a, double w,
+                       double phi, double *u)
+{
+    long n[ORC_MAXD], idx[ORC_MAXD];
+    long N = grid_points(P, levels, n), p;
+    int k;
+    for (p = 0; p < N; ++p) {
+        long r = p;
+        double S = 0.0;
+        for (k = 0; k < P->dim; ++k) {
+            idx[k] = r % n[k];
+            r /= n[k];
+            S = S + (P->lo[k] + (double)idx[k] * spacing(P, k, n[k]));
+        }
+        u[p] = b + a * sin(w * S + phi);
+    }
+}
+
+/* ------------------------------------------------------------------------------------
+ * One-dimensional fifth-order interpolation at x = x_i + s h, s in [-1/2, 1/2),
+ * Section 2.2.1, Eqs. (8)-(11).  (a..e) = (u_{i-2}, ..., u_{i+2}).
+ * P_k are the quadratics through the substencils S_0, S_1, S_2; C_k the linear weights
+ * printed after (8); beta_k of (10) evaluate to the formulas of Eq. (6).
+ * lagrange != 0 gives the Lagrange interpolant (8); otherwise the WENO interpolant (11).
+ * ---------------------------------------------------------------------------------- */
+double orc_weno5_interp(double a, double b, double c, double d, double e, double s, double eps,
+                        int lagrange)
+{
+    double g0 = 0.5 * (a - 4.0 * b + 3.0 * c), k0 = 0.5 * (a - 2.0 * b + c);
+    double g1 = 0.5 * (d - b), k1 = 0.5 * (b - 2.0 * c + d);
+    double g2 = 0.5 * (-3.0 * c + 4.0 * d - e), k2 = 0.5 * (c - 2.0 * d + e);
+    double P0 = c + s * (g0 + s * k0);
+    double P1 = c + s * (g1 + s * k1);
+    double P2 = c + s * (g2 + s * k2);
+    double C0 = ((s - 1.0) * (s - 2.0)) / 12.0;
+    double C1 = (4.0 - s * s) / 6.0;
+    double C2 = ((s + 1.0) * (s + 2.0)) / 12.0;
+    double w0, w1, w2;
+    if (s == 0.0) return c;  /* coincident node */
+    if (lagrange) {
+        return C0 * P0 + C1 * P1 + C2 * P2;
+    } else {
+        double t0 = a - 2.0 * b + c, s0 = a - 4.0 * b + 3.0 * c;
+        double t1 = b - 2.0 * c + d, s1 = b - d;
+        double t2 = c - 2.0 * d + e, s2 = 3.0 * c - 4.0 * d + e;
+        double b0 = (13.0 / 12.0) * (t0 * t0) + 0.25 * (s0 * s0);
+        double b1 = (13.0 / 12.0) * (t1 * t1) + 0.25 * (s1 * s1);
+        double b2 = (13.0 / 12.0) * (t2 * t2) + 0.25 * (s2 * s2);
+        /* Eq. (9): tilde C_k = C_k / (eps + beta_k)^2, w_k = tilde C_k / sum */
+        w0 = C0 / ((eps + b0) * (eps + b0));
+        w1 = C1 / ((eps + b1) * (eps + b1));
+        w2 = C2 / ((eps + b2) * (eps + b2));
+        return (w0 * P0 + w1 * P1 + w2 * P2) / (w0 + w1 + w2);
+    }
+}
+
+/* Coarse centre and offset of fine node jf on an axis refined by ratio r = 2^{N_L - l}:
+ * t = jf / r, centre i = floor(t + 1/2), s = t - i in [-1/2, 1/2). */
+static void fine_to_coarse(long jf, long r, long *ic, double *s)
+{
+    long i = jf / r, m = jf % r;
+    if (2 * m < r) {
+        *ic = i;
+        *s = (double)m / (double)r;
+    } else {
+        *ic = i + 1;
+        *s = (double)(m - r) / (double)r;
+    }
+}
+
+/* ------------------------------------------------------------------------------------
+ * Prolongation P^{N_L..N_L} U of one grid onto the finest grid, dimension by dimension,
+ * axis 0 first (Section 2.2.1).  out holds (N_r 2^{N_L})^d values; work must hold two
+ * arrays of that size.
+ * ---------------------------------------------------------------------------------- */
+void orc_prolong_grid(const orc_problem *P, const int *levels, const double *u, double *out,
+                      double *work)
+{
+    long n[ORC_MAXD], m[ORC_MAXD];
+    long Nf = (long)P->nr << P->nl;
+    long N = grid_points(P, levels, n), p;
+    int k, j;
+    double *src = work, *dst = work + 0;
+    double *bufA = work, *bufB = NULL;
+    long tot;
+    /* two ping-pong buffers of Nf^d each */
+    tot = 1;
+    for (k = 0; k < P->dim; ++k) tot *= Nf;
+    bufB = work + tot;
+    for (p = 0; p < N; ++p) bufA[p] = u[p];
+    for (k = 0; k < P->dim; ++k) m[k] = n[k];
+    src = bufA;
+    dst = bufB;
+    for (k = 0; k < P->dim; ++k) {
+        long r, below, above, Min, Mout, q;
+        if (levels[k] == P->nl) continue;  /* axis already at the finest level */
+        r = 1L << (P->nl - levels[k]);
+        below = 1;
+        for (j = 0; j < k; ++j) below *= m[j];
+        above = 1;
+        for (j = k + 1; j < P->dim; ++j) above *= m[j];
+        Min = m[k];
+        Mout = Nf;
+        for (q = 0; q < below * above; ++q) {
+            long lo_i = q % below, hi_i = q / below, jf;
+            const double *line = src + lo_i + hi_i * below * Min;
+            double *oline = dst + lo_i + hi_i * below * Mout;
+            for (jf = 0; jf < Mout; ++jf) {
+                long ic;
+                double s;
+                fine_to_coarse(jf, r, &ic, &s);
+                {
+                    double a = line[((ic - 2) % Min + Min) % Min * below];
+                    double b = line[((ic - 1) % Min + Min) % Min * below];
+                    double c = line[((ic) % Min + Min) % Min * below];
+                    double d = line[((ic + 1) % Min + Min) % Min * below];
+                    double e = line[((ic + 2) % Min + Min) % Min * below];
+                    oline[jf * below] = orc_weno5_interp(a, b, c, d, e, s, P->eps, P->prolong == 1);
+                }
+            }
+        }
+        m[k] = Nf;
+        {
+            double *t = src;
+            src = dst;
+            dst = t;
+        }
+    }
+    tot = 1;
+    for (k = 0; k < P->dim; ++k) tot *= Nf;
+    for (p = 0; p < tot; ++p) out[p] = src[p];
+}
+
+/* Step 3 (combination), Eqs. (12)-(15): uhat = sum_g c_g P U_g, grids in enumeration
+ * order.  grids: concatenated in enumeration order.  work: 3 * Nf^d doubles. */
+void orc_combine(const orc_problem *P, int G, const int *levels, const double *coeff,
+                 const double *grids, double *uhat, double *work)
+{
+    long Nf = (long)P->nr << P->nl, tot = 1, p;
+    int k, g;
+    const double *u = grids;
+    double *pu = work, *pw = work + 0;
+    for (k = 0; k < P->dim; ++k) tot *= Nf;
+    pw = work + tot;
+    for (p = 0; p < tot; ++p) uhat[p] = 0.0;
+    for (g = 0; g < G; ++g) {
+        orc_prolong_grid(P, levels + g * P->dim, u, pu, pw);
+        for (p = 0; p < tot; ++p) uhat[p] = uhat[p] + coeff[g] * pu[p];
+        u += orc_grid_points(P, levels + g * P->dim);
+    }
+}
+
+/* Pointwise prolongation: the value of P U at one finest-grid node J, evaluated by the
+ * same dimension-by-dimension recursion (axis d-1 interpolates values that are fine in
+ * axes 0..d-2).  Each intermediate value is computed by exactly the arithmetic of
+ * orc_prolong_grid, so the two agree bit for bit. */
+static double prolong_rec(const orc_problem *P, const int *levels, const long *n,
+                          const double *u, int k, const long *J, long *ci)
+{
+    /* value of the array after prolonging axes 0..k, at fine indices J[0..k] and coarse
+     * indices ci[k+1..d-1] */
+    long Nf = (long)P->nr << P->nl;
+    long ic, r, t;
+    double s, v[5];
+    if (k < 0) {
+        long p = 0, st = 1;
+        int j;
+        for (j = 0; j < P->dim; ++j) {
+            p += ci[j] * st;
+            st *= n[j];
+        }
+        return u[p];
+    }
+    if (levels[k] == P->nl) {
+        ci[k] = J[k];
+        return prolong_rec(P, levels, n, u, k - 1, J, ci);
+    }
+    r = 1L << (P->nl - levels[k]);
+    (void)Nf;
+    fine_to_coarse(J[k], r, &ic, &s);
+    if (s == 0.0) {
+        ci[k] = ((ic % n[k]) + n[k]) % n[k];
+        return prolong_rec(P, levels, n, u, k - 1, J, ci);
+    }
+    for (t = 0; t < 5; ++t) {
+        ci[k] = (((ic - 2 + t) % n[k]) + n[k]) % n[k];
+        v[t] = prolong_rec(P, levels, n, u, k - 1, J, ci);
+    }
+    return orc_weno5_interp(v[0], v[1], v[2], v[3], v[4], s, P->eps, P->prolong == 1);
+}
+
+double orc_prolong_point(const orc_problem *P, const int *levels, const double *u, const long *J)
+{
+    long n[ORC_MAXD], ci[ORC_MAXD];
+    grid_points(P, levels, n);
+    return prolong_rec(P, levels, n, u, P->dim - 1, J, ci);
+}
+
+/* uhat at one finest-grid node, summed over grids in enumeration order. */
+double orc_combine_point(const orc_problem *P, int G, const int *levels, const double *coeff,
+                         const double *grids, const long *J)
+{
+    double acc = 0.0;
+    const double *u = grids;
+    int g;
+    for (g = 0; g < G; ++g) {
+        acc = acc + coeff[g] * orc_prolong_point(P, levels + g * P->dim, u, J);
+        u += orc_grid_points(P, levels + g * P->dim);
+    }
+    return acc;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Diagnostics: mass sum_j u_j prod_k h_k of one grid (conserved under periodic boundary
+ * conditions, Eq. (2) telescopes), and the exact solutions the error norms use.
+ * ---------------------------------------------------------------------------------- */
+double orc_mass(const orc_problem *P, const int *levels, const double *u)
+{
+    long n[ORC_MAXD];
+    long N = grid_points(P, levels, n), p;
+    double vol = 1.0, s = 0.0;
+    int k;
+    for (k = 0; k < P->dim; ++k) vol = vol * spacing(P, k, n[k]);
+    for (p = 0; p < N; ++p) s = s + u[p];
+    return s * vol;
+}
+
+/* Exact solution for u_0 = b + a sin(w sum_k x_k + phi):
+ *   advection:  u(x, t) = u_0(x - a t);
+ *   Burgers:    u = u_0(x - u t 1), i.e. u = b + a sin(w (S - d u t) + phi), solved by
+ *               Newton's method (valid before the shock time 1/(a w d)). */
+double orc_exact_sine(const orc_problem *P, double b, double a, double w, double phi,
+                      const double *x, double t)
+{
+    int k, it;
+    double S = 0.0;
+    if (P->pde == 0) {
+        for (k = 0; k < P->dim; ++k) S = S + (x[k] - P->adv[k] * t);
+        return b + a * sin(w * S + phi);
+    }
+    for (k = 0; k < P->dim; ++k) S = S + x[k];
+    {
+        double d = (double)P->dim, u = b + a * sin(w * S + phi);
+        for (it = 0; it < 100; ++it) {
+            double arg = w * (S - d * u * t) + phi;
+            double F = u - b - a * sin(arg);
+            double dF = 1.0 + a * w * d * t * cos(arg);
+            double du = F / dF;
+            u = u - du;
+            if (fabs(du) <= 1e-16 * (1.0 + fabs(u))) break;
+        }
+        return u;
+    }
+}
+
+/* L^1 (mean absolute) and L^inf errors of the combined solution on the finest grid. */
+void orc_error_norms(const orc_problem *P, const double *uhat, double b, double a, double w,
+                     double phi, double t, double *l1, double *linf)
+{
+    long Nf = (long)P->nr << P->nl, tot = 1, p;
+    int k;
+    double x[ORC_MAXD], s = 0.0, mx = 0.0;
+    for (k = 0; k < P->dim; ++k) tot *= Nf;
+    for (p = 0; p < tot; ++p) {
+        long r = p;
+        double err;
+        for (k = 0; k < P->dim; ++k) {
+            x[k] = P->lo[k] + (double)(r % Nf) * fine_spacing(P, k);
+            r /= Nf;
+        }
+        err = fabs(uhat[p] - orc_exact_sine(P, b, a, w, phi, x, t));
+        s = s + err;
+        if (err > mx) mx = err;
+    }
+    *l1 = s / (double)tot;
+    *linf = mx;
+}
