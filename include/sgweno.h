@@ -80,6 +80,7 @@ enum {
 
 #define SG_MAX_DIM 6
 #define SG_WHICH_COMBINED (-1)
+#define SG_WHICH_ALL_GRIDS (-2)
 
 typedef struct sg_ctx *sg_handle;
 
@@ -124,6 +125,11 @@ sg_status sg_init(sg_handle h, int ic_kind, const double *ic_params, int n_param
  * t = 0.  SG_ERR_ARG if grid is out of range or bytes does not match. */
 sg_status sg_init_grid(sg_handle h, int grid, const void *host_values, size_t bytes);
 
+/* Sets every component grid at once from one host array holding the grids concatenated in
+ * enumeration order (sum_g n^g_0 ... n^g_{d-1} values in the handle's precision), and sets
+ * t = 0.  One host-to-device copy; SG_ERR_ARG if bytes does not match. */
+sg_status sg_init_grids(sg_handle h, const void *host_values, size_t bytes);
+
 /* Step 2: advances every component grid with the common time step until t = t_end (last
  * step shortened) or until max_steps further steps have been taken.  *t_reached (may be
  * NULL) receives the time reached (for a batch: the smallest over members).  Errors:
@@ -137,8 +143,8 @@ sg_status sg_step(sg_handle h, double t_end, long max_steps, double *t_reached);
 sg_status sg_prolong_combine(sg_handle h);
 
 /* Copies to the host: which = SG_WHICH_COMBINED (-1) the FP64 combined solution on the
- * finest grid ((N_r 2^{N_L})^d doubles), or which = g >= 0 component grid g in the handle's
- * precision.  dst_bytes must be at least the size.  Synchronises the handle's stream.
+ * finest grid ((N_r 2^{N_L})^d doubles), which = g >= 0 component grid g in the handle's
+ * precision, or which = SG_WHICH_ALL_GRIDS (-2) every grid concatenated in enumeration order.  dst_bytes must be at least the size.  Synchronises the handle's stream.
  * SG_ERR_STATE for -1 before sg_prolong_combine, SG_ERR_ARG for a small buffer. */
 sg_status sg_read(sg_handle h, int which, void *host_dst, size_t dst_bytes);
 

@@ -310,12 +310,16 @@ long orc_solve(const orc_problem *P, int G, const int *levels, double *grids, do
     while (t < t_end && steps < max_steps) {
         double dt = orc_dt(P, G, levels, grids, rule, coef, cfl);
         double *u = grids;
-        if (dt > t_end - t) dt = t_end - t;
+        int last = 0;
+        if (dt >= t_end - t) {  /* shortened last step: the run ends exactly at t_end */
+            dt = t_end - t;
+            last = 1;
+        }
         for (g = 0; g < G; ++g) {
             orc_rk3_step(P, levels + g * P->dim, u, dt, work);
             u += orc_grid_points(P, levels + g * P->dim);
         }
-        t = t + dt;
+        t = last ? t_end : t + dt;
         ++steps;
     }
     free(work);

@@ -1,0 +1,923 @@
+// sg_api.cu -- the C ABI of include/sgweno.h: handle lifecycle, the grid table and work
+// queue, device-side time-step control replayed through CUDA graphs, prolongation and
+// combination, reductions.  All numerical work runs in the kernels of sg_kernels.cuh.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sg_device.h"
+#include "sg_launch.h"
+#include "sgweno.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+sg_alloc_fn g_alloc = nullptr;
+sg_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+long g_live_handles = 0;
+
+sg_status fail(sg_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define SG_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            cudaGetLastError();                                                            \
+            return fail(SG_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+        }                                                                                  \
+    } while (0)
+
+#define SG_TRY(expr)                    \
+    do {                                \
+        sg_status s_ = (expr);          \
+        if (s_ != SG_OK) return s_;     \
+    } while (0)
+
+// Device buffer through the allocator hook (or cudaMalloc).
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    sg_status alloc(size_t b) {
+        release();
+        if (b == 0) b = 256;
+        void* q = nullptr;
+        if (g_alloc) {
+            q = g_alloc(b, g_alloc_ctx);
+        } else if (cudaMalloc(&q, b) != cudaSuccess) {
+            cudaGetLastError();
+            q = nullptr;
+        }
+        if (!q) return fail(SG_ERR_NOMEM, "device allocation of %zu bytes failed", b);
+        p = q;
+        bytes = b;
+        return SG_OK;
+    }
+    void release() {
+        if (!p) return;
+        if (g_free) g_free(p, bytes, g_alloc_ctx);
+        else cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+struct PinnedInst {
+    InstState* p = nullptr;
+    int n = 0;
+    ~PinnedInst() {
+        if (p) cudaFreeHost(p);
+    }
+    sg_status alloc(int count) {
+        if (cudaMallocHost((void**)&p, sizeof(InstState) * (size_t)count) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return fail(SG_ERR_NOMEM, "pinned host allocation failed");
+        }
+        n = count;
+        std::memset(p, 0, sizeof(InstState) * (size_t)count);
+        return SG_OK;
+    }
+};
+
+long long binom(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    long long r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+// Levels with |l| = target, l_k in [0, nl], lexicographic with l_0 most significant.
+void compositions(int dim, int nl, int k, int remaining, std::array<int, SG_MAXD>& cur,
+                  std::vector<std::array<int, SG_MAXD>>& out) {
+    if (k == dim - 1) {
+        if (remaining <= nl) {
+            cur[k] = remaining;
+            out.push_back(cur);
+        }
+        return;
+    }
+    for (int l = 0; l <= std::min(nl, remaining); ++l) {
+        cur[k] = l;
+        compositions(dim, nl, k + 1, remaining - l, cur, out);
+    }
+}
+
+}  // namespace
+
+struct sg_ctx {
+    bool is_batch = false;
+    int dim = 0, nr = 0, nl = 0, pde = 0;
+    sg_params prm{};
+    int esize = 8;
+    int ppt = 2;
+    // grids (single handle)
+    int G = 0;
+    std::vector<std::array<int, SG_MAXD>> levels;
+    std::vector<double> coeff;
+    std::vector<long long> npts;
+    std::vector<long long> offset;  // element offset of each grid inside a state region
+    long long total_pts = 0;
+    DevBuf arena;  // [U0 region][U1 region][U2 region]
+    // device tables (single handle or batch)
+    std::vector<GridDesc> hgrids;
+    std::vector<WorkItem> hitems;
+    DevBuf dgrids, ditems, alpha, flags, dinst, partial;
+    PinnedInst hinst;
+    int ninst = 1;
+    int blocks_total = 1;
+    long long max_grid_pts = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t graph = nullptr;
+    int graph_nsteps = 0;
+    long long graph_kernels = 0;
+    // state
+    bool initialized = false;
+    bool combined = false;
+    bool ic_sine = false;
+    double ic[4] = {0, 0, 0, 0};
+    double t = 0.0;
+    long long steps = 0;
+    long long launches = 0;
+    // combination
+    DevBuf uhat, pro_a, pro_b;
+    long long fine_pts = 0;
+    // batch
+    std::vector<sg_ctx*> members;
+
+    ~sg_ctx() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+PhysParams phys_of(const sg_ctx* h) {
+    PhysParams ph{};
+    ph.dim = h->dim;
+    ph.pde = h->pde;
+    ph.scheme = h->prm.scheme;
+    ph.prolong = h->prm.prolong;
+    ph.eps = h->prm.eps;
+    for (int k = 0; k < SG_MAXD; ++k) ph.adv[k] = k < h->dim ? h->prm.adv_speed[k] : 0.0;
+    return ph;
+}
+
+double fine_spacing(const sg_ctx* h, int k) {
+    return (h->prm.hi[k] - h->prm.lo[k]) / (double)((long long)h->nr << h->nl);
+}
+
+// Nominal step of the h^{5/3} rule: coef * (min_k h_k)^{5/3} on the finest grid.
+double dt_pow53(const sg_ctx* h) {
+    double hm = fine_spacing(h, 0);
+    for (int k = 1; k < h->dim; ++k) hm = std::min(hm, fine_spacing(h, k));
+    return h->prm.dt_coef * std::pow(hm, 5.0 / 3.0);
+}
+
+void fill_inst(const sg_ctx* h, InstState& s, int grid0, double t_end, long long max_steps) {
+    s.t = h->t;
+    s.dt = 0.0;
+    s.t_end = t_end;
+    s.dt_nom = dt_pow53(h);
+    s.cfl = h->prm.cfl;
+    for (int k = 0; k < SG_MAXD; ++k) s.hf[k] = k < h->dim ? fine_spacing(h, k) : 1.0;
+    s.steps = h->steps;
+    s.step_limit = max_steps > (1LL << 62) - h->steps ? (1LL << 62) : h->steps + max_steps;
+    s.active = 0;
+    s.pending = 0;
+    s.last = 0;
+    s.grid0 = grid0;
+    s.ngrids = h->G;
+    s.dt_rule = h->prm.dt_rule;
+}
+
+// Tile extents: start from the whole grid and halve the longest extent (the highest axis on
+// ties, keeping axis 0 long for coalescing) until the tile has at most pmax points.
+void choose_tile(const int* n, int dim, int pmax, int* te) {
+    for (int k = 0; k < dim; ++k) te[k] = n[k];
+    for (;;) {
+        long long p = 1;
+        for (int k = 0; k < dim; ++k) p *= te[k];
+        if (p <= pmax) break;
+        int best = 0;
+        for (int k = 1; k < dim; ++k)
+            if (te[k] >= te[best]) best = k;
+        te[best] = (te[best] + 1) / 2;
+    }
+}
+
+int num_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n;
+}
+
+int stage_blocks_per_sm(const sg_ctx* h) {
+    return h->esize == 8 ? sg::Launch<double>::stage_blocks_per_sm(h->dim, h->ppt)
+                         : sg::Launch<float>::stage_blocks_per_sm(h->dim, h->ppt);
+}
+
+cudaError_t launch_stage(const sg_ctx* h, const StageArgs& a, int nblocks) {
+    return h->esize == 8 ? sg::Launch<double>::stage(h->dim, h->ppt, a, nblocks, h->stream)
+                         : sg::Launch<float>::stage(h->dim, h->ppt, a, nblocks, h->stream);
+}
+
+sg_status validate_params(const sg_params* p, int dim) {
+    if (p->struct_size != sizeof(sg_params)) return fail(SG_ERR_ARG, "sg_params.struct_size mismatch (use sg_params_init)");
+    for (int k = 0; k < dim; ++k) {
+        if (!(std::isfinite(p->lo[k]) && std::isfinite(p->hi[k]) && p->hi[k] > p->lo[k]))
+            return fail(SG_ERR_ARG, "domain axis %d: need finite lo < hi", k);
+        if (p->bc[k] != SG_BC_PERIODIC) return fail(SG_ERR_UNSUPPORTED, "only periodic boundaries are implemented");
+        if (!std::isfinite(p->adv_speed[k])) return fail(SG_ERR_ARG, "adv_speed[%d] not finite", k);
+    }
+    if (p->precision != SG_F64 && p->precision != SG_F32) return fail(SG_ERR_ARG, "precision");
+    if (p->exec != SG_PLAIN && p->exec != SG_BATCHED) return fail(SG_ERR_ARG, "exec");
+    if (p->scheme != SG_WENO5 && p->scheme != SG_LINEAR5) return fail(SG_ERR_ARG, "scheme");
+    if (p->prolong != SG_PROLONG_WENO5 && p->prolong != SG_PROLONG_LAGRANGE5) return fail(SG_ERR_ARG, "prolong");
+    if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return fail(SG_ERR_ARG, "eps must be > 0");
+    if (p->dt_rule != SG_DT_POW53 && p->dt_rule != SG_DT_CFL) return fail(SG_ERR_ARG, "dt_rule");
+    if (!(p->dt_coef > 0.0) || !(p->cfl > 0.0)) return fail(SG_ERR_ARG, "dt_coef and cfl must be > 0");
+    if (p->tile_points != 0 && p->tile_points != 256 && p->tile_points != 512 && p->tile_points != 1024)
+        return fail(SG_ERR_ARG, "tile_points must be 0, 256, 512 or 1024");
+    return SG_OK;
+}
+
+// Builds the device grid table and work queue of a single handle.
+sg_status build_tables(sg_ctx* h) {
+    const int pmax = 256 * h->ppt;
+    char* base = h->arena.as<char>();
+    const size_t region = (size_t)h->total_pts * h->esize;
+    h->hgrids.assign(h->G, GridDesc{});
+    h->hitems.clear();
+    for (int g = 0; g < h->G; ++g) {
+        GridDesc& d = h->hgrids[g];
+        d.u0 = base + (size_t)h->offset[g] * h->esize;
+        d.u1 = base + region + (size_t)h->offset[g] * h->esize;
+        d.u2 = base + 2 * region + (size_t)h->offset[g] * h->esize;
+        d.npts = h->npts[g];
+        int n[SG_MAXD] = {1, 1, 1, 1, 1, 1};
+        for (int k = 0; k < h->dim; ++k) n[k] = h->nr << h->levels[g][k];
+        choose_tile(n, h->dim, pmax, d.te);
+        int ntiles = 1;
+        for (int k = 0; k < SG_MAXD; ++k) {
+            if (k < h->dim) {
+                d.n[k] = n[k];
+                d.nt[k] = (n[k] + d.te[k] - 1) / d.te[k];
+                d.h[k] = (h->prm.hi[k] - h->prm.lo[k]) / (double)n[k];
+                d.rdx[k] = 1.0 / d.h[k];
+                d.lo[k] = h->prm.lo[k];
+                d.lev[k] = h->levels[g][k];
+                ntiles *= d.nt[k];
+            } else {
+                d.n[k] = 1;
+                d.te[k] = 1;
+                d.nt[k] = 1;
+                d.h[k] = 1.0;
+                d.rdx[k] = 1.0;
+                d.lo[k] = 0.0;
+                d.lev[k] = 0;
+            }
+        }
+        d.coeff = h->coeff[g];
+        d.inst = 0;
+        d.first_item = (int)h->hitems.size();
+        d.n_items = ntiles;
+        for (int t = 0; t < ntiles; ++t) h->hitems.push_back(WorkItem{g, t});
+    }
+    SG_TRY(h->dgrids.alloc(sizeof(GridDesc) * h->hgrids.size()));
+    SG_TRY(h->ditems.alloc(sizeof(WorkItem) * h->hitems.size()));
+    SG_CUDA(cudaMemcpy(h->dgrids.p, h->hgrids.data(), sizeof(GridDesc) * h->hgrids.size(), cudaMemcpyHostToDevice));
+    SG_CUDA(cudaMemcpy(h->ditems.p, h->hitems.data(), sizeof(WorkItem) * h->hitems.size(), cudaMemcpyHostToDevice));
+    return SG_OK;
+}
+
+sg_status alloc_step_buffers(sg_ctx* h, int ngrids_total, int ninst) {
+    SG_TRY(h->alpha.alloc(sizeof(unsigned long long) * 3 * (size_t)ngrids_total));
+    SG_TRY(h->flags.alloc(sizeof(int) * 4));
+    SG_TRY(h->dinst.alloc(sizeof(InstState) * (size_t)ninst));
+    SG_TRY(h->partial.alloc(sizeof(double) * 1032));
+    SG_TRY(h->hinst.alloc(ninst));
+    h->ninst = ninst;
+    SG_CUDA(cudaMemset(h->alpha.p, 0, h->alpha.bytes));
+    SG_CUDA(cudaMemset(h->flags.p, 0, h->flags.bytes));
+    const int bps = stage_blocks_per_sm(h);
+    if (bps < 1) return fail(SG_ERR_CUDA, "stage kernel cannot be resident (dim %d, %d points/thread)", h->dim, h->ppt);
+    h->blocks_total = bps * num_sms();
+    return SG_OK;
+}
+
+// Enqueues `nsteps` time steps (dt control + three RK stages each) on the handle's stream.
+sg_status enqueue_steps(sg_ctx* h, int nsteps, long long* kernels) {
+    const PhysParams ph = phys_of(h);
+    long long nk = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        SG_CUDA(sg::launch_dt(h->dinst.as<InstState>(), h->ninst, h->alpha.as<unsigned long long>(), ph, 0, h->stream));
+        ++nk;
+        for (int stage = 0; stage < 3; ++stage) {
+            StageArgs a{};
+            a.grids = h->dgrids.as<GridDesc>();
+            a.items = h->ditems.as<WorkItem>();
+            a.inst = h->dinst.as<InstState>();
+            a.alpha = h->alpha.as<unsigned long long>();
+            a.flags = h->flags.as<int>();
+            a.stage = stage;
+            a.phys = ph;
+            const bool batched = h->is_batch || h->prm.exec == SG_BATCHED;
+            if (batched) {
+                a.item_begin = 0;
+                a.item_end = (int)h->hitems.size();
+                SG_CUDA(launch_stage(h, a, std::min<int>(a.item_end, h->blocks_total)));
+                ++nk;
+            } else {
+                for (const GridDesc& d : h->hgrids) {
+                    a.item_begin = d.first_item;
+                    a.item_end = d.first_item + d.n_items;
+                    SG_CUDA(launch_stage(h, a, std::min<int>(d.n_items, h->blocks_total)));
+                    ++nk;
+                }
+            }
+        }
+    }
+    *kernels = nk;
+    return SG_OK;
+}
+
+sg_status ensure_graph(sg_ctx* h, int nsteps) {
+    if (h->graph && h->graph_nsteps == nsteps) return SG_OK;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    SG_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    long long nk = 0;
+    sg_status st = enqueue_steps(h, nsteps, &nk);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (st != SG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SG_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->graph = nullptr;
+        return fail(SG_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+    h->graph_nsteps = nsteps;
+    h->graph_kernels = nk;
+    return SG_OK;
+}
+
+// Would the next dt-control pass mark this instance inactive?  Mirrors sg_dt_kernel.
+bool finished(const InstState& s) {
+    if (!s.active) return true;
+    const double t = s.last ? s.t_end : s.t + s.dt;
+    const long long n = s.steps + 1;
+    return !(t < s.t_end && n < s.step_limit);
+}
+
+// Step loop shared by single handles and batches; h->hinst holds the members' states.
+sg_status run_steps(sg_ctx* h) {
+    SG_CUDA(cudaMemcpyAsync(h->dinst.p, h->hinst.p, sizeof(InstState) * h->ninst, cudaMemcpyHostToDevice, h->stream));
+    SG_CUDA(cudaMemsetAsync(h->alpha.p, 0, h->alpha.bytes, h->stream));
+    SG_CUDA(cudaMemsetAsync(h->flags.p, 0, h->flags.bytes, h->stream));
+    const int ng = (int)h->hgrids.size();
+    if (h->esize == 8)
+        SG_CUDA(sg::Launch<double>::alpha_init(h->dgrids.as<GridDesc>(), ng, h->max_grid_pts, h->alpha.as<unsigned long long>(), h->flags.as<int>(), h->stream));
+    else
+        SG_CUDA(sg::Launch<float>::alpha_init(h->dgrids.as<GridDesc>(), ng, h->max_grid_pts, h->alpha.as<unsigned long long>(), h->flags.as<int>(), h->stream));
+    h->launches += 1;
+    const int K = h->prm.graph_steps == 0 ? 16 : (h->prm.graph_steps < 0 ? 8 : h->prm.graph_steps);
+    const bool use_graph = h->prm.graph_steps >= 0;
+    if (use_graph) SG_TRY(ensure_graph(h, K));
+    for (;;) {
+        if (use_graph) {
+            SG_CUDA(cudaGraphLaunch(h->graph, h->stream));
+            h->launches += h->graph_kernels;
+        } else {
+            long long nk = 0;
+            SG_TRY(enqueue_steps(h, K, &nk));
+            h->launches += nk;
+        }
+        SG_CUDA(cudaMemcpyAsync(h->hinst.p, h->dinst.p, sizeof(InstState) * h->ninst, cudaMemcpyDeviceToHost, h->stream));
+        SG_CUDA(cudaStreamSynchronize(h->stream));
+        bool all = true;
+        for (int i = 0; i < h->ninst; ++i) all = all && finished(h->hinst.p[i]);
+        if (all) break;
+    }
+    SG_CUDA(sg::launch_dt(h->dinst.as<InstState>(), h->ninst, h->alpha.as<unsigned long long>(), phys_of(h), 1, h->stream));
+    h->launches += 1;
+    int hflags[4] = {0, 0, 0, 0};
+    SG_CUDA(cudaMemcpyAsync(h->hinst.p, h->dinst.p, sizeof(InstState) * h->ninst, cudaMemcpyDeviceToHost, h->stream));
+    SG_CUDA(cudaMemcpyAsync(hflags, h->flags.p, sizeof hflags, cudaMemcpyDeviceToHost, h->stream));
+    SG_CUDA(cudaStreamSynchronize(h->stream));
+    if (hflags[SG_FLAG_NONFINITE]) return fail(SG_ERR_NONFINITE, "a non-finite value appeared in the solution");
+    return SG_OK;
+}
+
+// Prolongation of every grid onto the finest grid and the combination sum (single handle).
+template <class T>
+sg_status prolong_combine_t(sg_ctx* h) {
+    const int d = h->dim;
+    const long long Nf = (long long)h->nr << h->nl;
+    // intermediate buffers: largest array produced by a non-final prolonged axis
+    long long need = 1;
+    for (int g = 0; g < h->G; ++g) {
+        long long m[SG_MAXD];
+        std::vector<int> axes;
+        for (int k = 0; k < d; ++k) {
+            m[k] = (long long)h->nr << h->levels[g][k];
+            if (h->levels[g][k] < h->nl) axes.push_back(k);
+        }
+        for (size_t a = 0; a + 1 < axes.size(); ++a) {
+            m[axes[a]] = Nf;
+            long long tot = 1;
+            for (int k = 0; k < d; ++k) tot *= m[k];
+            need = std::max(need, tot);
+        }
+    }
+    if (!h->uhat.p) SG_TRY(h->uhat.alloc(sizeof(double) * (size_t)h->fine_pts));
+    if (h->pro_a.bytes < sizeof(T) * (size_t)need) {
+        SG_TRY(h->pro_a.alloc(sizeof(T) * (size_t)need));
+        SG_TRY(h->pro_b.alloc(sizeof(T) * (size_t)need));
+    }
+    double* acc = h->uhat.as<double>();
+    SG_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)h->fine_pts, h->stream));
+    for (int g = 0; g < h->G; ++g) {
+        const GridDesc& gd = h->hgrids[g];
+        long long m[SG_MAXD];
+        std::vector<int> axes;
+        for (int k = 0; k < d; ++k) {
+            m[k] = gd.n[k];
+            if (gd.lev[k] < h->nl) axes.push_back(k);
+        }
+        const T* src = (const T*)gd.u0;
+        if (axes.empty()) {
+            SG_CUDA(sg::Launch<T>::accumulate(src, acc, gd.coeff, gd.npts, h->stream));
+            h->launches += 1;
+            continue;
+        }
+        T* bufs[2] = {h->pro_a.as<T>(), h->pro_b.as<T>()};
+        for (size_t a = 0; a < axes.size(); ++a) {
+            const int k = axes[a];
+            long long below = 1, above = 1;
+            for (int j = 0; j < k; ++j) below *= m[j];
+            for (int j = k + 1; j < d; ++j) above *= m[j];
+            const int r = 1 << (h->nl - gd.lev[k]);
+            const bool last = a + 1 == axes.size();
+            T* dst = last ? nullptr : bufs[a & 1];
+            SG_CUDA(sg::Launch<T>::prolong_axis(src, dst, last ? acc : nullptr, gd.coeff, below, (int)m[k],
+                                                (int)Nf, above, r, h->prm.eps, h->prm.prolong, h->stream));
+            h->launches += 1;
+            m[k] = Nf;
+            src = dst;
+        }
+    }
+    SG_CUDA(cudaStreamSynchronize(h->stream));
+    h->combined = true;
+    return SG_OK;
+}
+
+sg_status check_handle(sg_handle h) {
+    if (!h) return fail(SG_ERR_ARG, "NULL handle");
+    return SG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sg_status sg_params_init(sg_params* p) {
+    if (!p) return fail(SG_ERR_ARG, "NULL params");
+    std::memset(p, 0, sizeof *p);
+    p->struct_size = sizeof(sg_params);
+    for (int k = 0; k < SG_MAX_DIM; ++k) {
+        p->lo[k] = 0.0;
+        p->hi[k] = 4.0;
+        p->bc[k] = SG_BC_PERIODIC;
+        p->adv_speed[k] = 1.0;
+    }
+    p->precision = SG_F64;
+    p->exec = SG_PLAIN;
+    p->scheme = SG_WENO5;
+    p->prolong = SG_PROLONG_WENO5;
+    p->eps = 1e-3;
+    p->dt_rule = SG_DT_POW53;
+    p->dt_coef = 1.0;
+    p->cfl = 0.4;
+    p->cuda_stream = nullptr;
+    p->graph_steps = 0;
+    p->tile_points = 0;
+    return SG_OK;
+}
+
+sg_status sg_create(int dim, int root_cells, int level, int pde, const sg_params* params, sg_handle* out) {
+    if (!out) return fail(SG_ERR_ARG, "NULL output handle");
+    *out = nullptr;
+    if (dim < 1 || dim > SG_MAX_DIM) return fail(SG_ERR_ARG, "dim must be in [1, 6]");
+    if (root_cells < 5) return fail(SG_ERR_ARG, "root_cells must be >= 5 (five distinct stencil points)");
+    if (level < 0 || level > 16 || ((long long)root_cells << level) > (1LL << 20))
+        return fail(SG_ERR_ARG, "level must be in [0, 16] with root_cells * 2^level <= 2^20");
+    if (pde != SG_PDE_ADVECTION && pde != SG_PDE_BURGERS) return fail(SG_ERR_ARG, "pde");
+    sg_params prm;
+    if (params) prm = *params;
+    else sg_params_init(&prm);
+    SG_TRY(validate_params(&prm, dim));
+    try {
+        sg_ctx* h = new sg_ctx();
+        h->dim = dim;
+        h->nr = root_cells;
+        h->nl = level;
+        h->pde = pde;
+        h->prm = prm;
+        h->esize = prm.precision == SG_F64 ? 8 : 4;
+        h->ppt = prm.tile_points ? prm.tile_points / 256 : 2;
+        // grid set: |l| = N_L - q, q = 0..d-1, coefficient (-1)^q C(d-1, q)
+        for (int q = 0; q < dim && level - q >= 0; ++q) {
+            std::vector<std::array<int, SG_MAXD>> ls;
+            std::array<int, SG_MAXD> cur{};
+            compositions(dim, level, 0, level - q, cur, ls);
+            for (auto& l : ls) {
+                h->levels.push_back(l);
+                h->coeff.push_back((q % 2 ? -1.0 : 1.0) * (double)binom(dim - 1, q));
+            }
+        }
+        h->G = (int)h->levels.size();
+        h->total_pts = 0;
+        for (int g = 0; g < h->G; ++g) {
+            long long n = 1;
+            for (int k = 0; k < dim; ++k) n *= (long long)root_cells << h->levels[g][k];
+            h->npts.push_back(n);
+            h->offset.push_back(h->total_pts);
+            h->total_pts += n;
+            h->max_grid_pts = std::max(h->max_grid_pts, n);
+        }
+        h->fine_pts = 1;
+        for (int k = 0; k < dim; ++k) h->fine_pts *= (long long)root_cells << level;
+        if (prm.cuda_stream) {
+            h->stream = (cudaStream_t)prm.cuda_stream;
+        } else {
+            cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                delete h;
+                return fail(SG_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+            }
+            h->own_stream = true;
+        }
+        sg_status st = h->arena.alloc((size_t)h->total_pts * h->esize * 3);
+        if (st == SG_OK) st = build_tables(h);
+        if (st == SG_OK) st = alloc_step_buffers(h, h->G, 1);
+        if (st != SG_OK) {
+            delete h;
+            return st;
+        }
+        ++g_live_handles;
+        *out = h;
+        return SG_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(SG_ERR_NOMEM, "host allocation failed");
+    } catch (...) {
+        return fail(SG_ERR_CUDA, "unexpected exception in sg_create");
+    }
+}
+
+sg_status sg_init(sg_handle h, int ic_kind, const double* p, int n_params) {
+    SG_TRY(check_handle(h));
+    if (h->is_batch) return fail(SG_ERR_ARG, "sg_init applies to batch members, not to the batch");
+    if (ic_kind != SG_IC_SINE || n_params != 4 || !p) return fail(SG_ERR_ARG, "SG_IC_SINE takes 4 parameters");
+    for (int i = 0; i < 4; ++i)
+        if (!std::isfinite(p[i])) return fail(SG_ERR_ARG, "initial-condition parameter %d not finite", i);
+    for (int g = 0; g < h->G; ++g) {
+        if (h->esize == 8) SG_CUDA(sg::Launch<double>::restrict_sine(h->hgrids[g], h->dim, p, h->stream));
+        else SG_CUDA(sg::Launch<float>::restrict_sine(h->hgrids[g], h->dim, p, h->stream));
+        h->launches += 1;
+    }
+    SG_CUDA(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < 4; ++i) h->ic[i] = p[i];
+    h->ic_sine = true;
+    h->initialized = true;
+    h->combined = false;
+    h->t = 0.0;
+    h->steps = 0;
+    return SG_OK;
+}
+
+sg_status sg_init_grid(sg_handle h, int grid, const void* host_values, size_t bytes) {
+    SG_TRY(check_handle(h));
+    if (h->is_batch) return fail(SG_ERR_ARG, "sg_init_grid applies to batch members");
+    if (grid < 0 || grid >= h->G) return fail(SG_ERR_ARG, "grid index %d out of range [0, %d)", grid, h->G);
+    if (!host_values) return fail(SG_ERR_ARG, "NULL host buffer");
+    const size_t need = (size_t)h->npts[grid] * h->esize;
+    if (bytes != need) return fail(SG_ERR_ARG, "grid %d needs %zu bytes, got %zu", grid, need, bytes);
+    SG_CUDA(cudaMemcpyAsync(h->hgrids[grid].u0, host_values, need, cudaMemcpyHostToDevice, h->stream));
+    SG_CUDA(cudaStreamSynchronize(h->stream));
+    h->ic_sine = false;
+    h->initialized = true;
+    h->combined = false;
+    h->t = 0.0;
+    h->steps = 0;
+    return SG_OK;
+}
+
+sg_status sg_init_grids(sg_handle h, const void* host_values, size_t bytes) {
+    SG_TRY(check_handle(h));
+    if (h->is_batch) return fail(SG_ERR_ARG, "sg_init_grids applies to batch members");
+    if (!host_values) return fail(SG_ERR_ARG, "NULL host buffer");
+    const size_t need = (size_t)h->total_pts * h->esize;
+    if (bytes != need) return fail(SG_ERR_ARG, "all grids need %zu bytes, got %zu", need, bytes);
+    SG_CUDA(cudaMemcpyAsync(h->hgrids[0].u0, host_values, need, cudaMemcpyHostToDevice, h->stream));
+    SG_CUDA(cudaStreamSynchronize(h->stream));
+    h->ic_sine = false;
+    h->initialized = true;
+    h->combined = false;
+    h->t = 0.0;
+    h->steps = 0;
+    return SG_OK;
+}
+
+sg_status sg_step(sg_handle h, double t_end, long max_steps, double* t_reached) {
+    SG_TRY(check_handle(h));
+    if (!std::isfinite(t_end)) return fail(SG_ERR_ARG, "t_end must be finite");
+    if (max_steps < 0) return fail(SG_ERR_ARG, "max_steps must be >= 0");
+    try {
+        if (!h->is_batch) {
+            if (!h->initialized) return fail(SG_ERR_STATE, "sg_step before sg_init");
+            fill_inst(h, h->hinst.p[0], 0, t_end, max_steps);
+            sg_status st = run_steps(h);
+            h->t = h->hinst.p[0].t;
+            h->steps = h->hinst.p[0].steps;
+            h->combined = false;
+            if (t_reached) *t_reached = h->t;
+            return st;
+        }
+        int gbase = 0;
+        for (size_t i = 0; i < h->members.size(); ++i) {
+            sg_ctx* m = h->members[i];
+            if (!m->initialized) return fail(SG_ERR_STATE, "batch member %zu not initialised", i);
+            SG_CUDA(cudaStreamSynchronize(m->stream));
+            fill_inst(m, h->hinst.p[i], gbase, t_end, max_steps);
+            gbase += m->G;
+        }
+        sg_status st = run_steps(h);
+        double tmin = INFINITY;
+        for (size_t i = 0; i < h->members.size(); ++i) {
+            sg_ctx* m = h->members[i];
+            m->t = h->hinst.p[i].t;
+            m->steps = h->hinst.p[i].steps;
+            m->combined = false;
+            tmin = std::min(tmin, m->t);
+        }
+        if (t_reached) *t_reached = tmin;
+        return st;
+    } catch (const std::bad_alloc&) {
+        return fail(SG_ERR_NOMEM, "host allocation failed");
+    }
+}
+
+sg_status sg_prolong_combine(sg_handle h) {
+    SG_TRY(check_handle(h));
+    try {
+        if (h->is_batch) {
+            for (sg_ctx* m : h->members) SG_TRY(sg_prolong_combine(m));
+            return SG_OK;
+        }
+        if (!h->initialized) return fail(SG_ERR_STATE, "sg_prolong_combine before sg_init");
+        return h->esize == 8 ? prolong_combine_t<double>(h) : prolong_combine_t<float>(h);
+    } catch (const std::bad_alloc&) {
+        return fail(SG_ERR_NOMEM, "host allocation failed");
+    }
+}
+
+sg_status sg_read(sg_handle h, int which, void* host_dst, size_t dst_bytes) {
+    SG_TRY(check_handle(h));
+    if (h->is_batch) return fail(SG_ERR_ARG, "sg_read applies to batch members");
+    if (!host_dst) return fail(SG_ERR_ARG, "NULL destination");
+    const void* src;
+    size_t bytes;
+    if (which == SG_WHICH_COMBINED) {
+        if (!h->combined) return fail(SG_ERR_STATE, "no combined solution: call sg_prolong_combine first");
+        src = h->uhat.p;
+        bytes = sizeof(double) * (size_t)h->fine_pts;
+    } else if (which >= 0 && which < h->G) {
+        src = h->hgrids[which].u0;
+        bytes = (size_t)h->npts[which] * h->esize;
+    } else if (which == SG_WHICH_ALL_GRIDS) {
+        src = h->hgrids[0].u0;
+        bytes = (size_t)h->total_pts * h->esize;
+    } else {
+        return fail(SG_ERR_ARG, "which = %d out of range", which);
+    }
+    if (dst_bytes < bytes) return fail(SG_ERR_ARG, "destination holds %zu bytes, need %zu", dst_bytes, bytes);
+    SG_CUDA(cudaMemcpyAsync(host_dst, src, bytes, cudaMemcpyDeviceToHost, h->stream));
+    SG_CUDA(cudaStreamSynchronize(h->stream));
+    return SG_OK;
+}
+
+sg_status sg_reduce(sg_handle h, int which, int kind, double* out) {
+    SG_TRY(check_handle(h));
+    if (h->is_batch) return fail(SG_ERR_ARG, "sg_reduce applies to batch members");
+    if (!out) return fail(SG_ERR_ARG, "NULL output");
+    if (kind < SG_REDUCE_MASS || kind > SG_REDUCE_LINF_EXACT) return fail(SG_ERR_ARG, "unknown reduction %d", kind);
+    ExactSpec X{};
+    X.dim = h->dim;
+    X.pde = h->pde;
+    X.nf = (int)((long long)h->nr << h->nl);
+    for (int k = 0; k < SG_MAXD; ++k) {
+        X.lo[k] = k < h->dim ? h->prm.lo[k] : 0.0;
+        X.h[k] = k < h->dim ? fine_spacing(h, k) : 1.0;
+        X.adv[k] = k < h->dim ? h->prm.adv_speed[k] : 0.0;
+    }
+    X.b = h->ic[0];
+    X.a = h->ic[1];
+    X.w = h->ic[2];
+    X.phi = h->ic[3];
+    X.t = h->t;
+    const bool exact = kind == SG_REDUCE_L1_EXACT || kind == SG_REDUCE_LINF_EXACT;
+    double* dres = h->partial.as<double>() + 1024;
+    long long n;
+    double vol = 1.0;
+    if (which == SG_WHICH_COMBINED) {
+        if (!h->combined) return fail(SG_ERR_STATE, "no combined solution: call sg_prolong_combine first");
+        if (exact && !h->ic_sine) return fail(SG_ERR_STATE, "exact-solution norms need an SG_IC_SINE initial condition");
+        n = h->fine_pts;
+        for (int k = 0; k < h->dim; ++k) vol = vol * fine_spacing(h, k);
+        SG_CUDA(sg::Launch<double>::reduce(h->uhat.as<double>(), n, kind, X, h->partial.as<double>(), dres, h->stream));
+    } else if (which >= 0 && which < h->G) {
+        if (exact) return fail(SG_ERR_ARG, "exact-solution norms apply to the combined solution (which = -1)");
+        n = h->npts[which];
+        for (int k = 0; k < h->dim; ++k) vol = vol * h->hgrids[which].h[k];
+        if (h->esize == 8)
+            SG_CUDA(sg::Launch<double>::reduce((const double*)h->hgrids[which].u0, n, kind, X, h->partial.as<double>(), dres, h->stream));
+        else
+            SG_CUDA(sg::Launch<float>::reduce((const float*)h->hgrids[which].u0, n, kind, X, h->partial.as<double>(), dres, h->stream));
+    } else {
+        return fail(SG_ERR_ARG, "which = %d out of range", which);
+    }
+    h->launches += 2;
+    double r = 0.0;
+    SG_CUDA(cudaMemcpyAsync(&r, dres, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+    SG_CUDA(cudaStreamSynchronize(h->stream));
+    switch (kind) {
+        case SG_REDUCE_MASS:
+        case SG_REDUCE_ENERGY: r = r * vol; break;
+        case SG_REDUCE_L1_EXACT: r = r / (double)n; break;
+        default: break;
+    }
+    *out = r;
+    return SG_OK;
+}
+
+sg_status sg_num_grids(sg_handle h, int* n) {
+    SG_TRY(check_handle(h));
+    if (!n) return fail(SG_ERR_ARG, "NULL output");
+    *n = h->is_batch ? (int)h->hgrids.size() : h->G;
+    return SG_OK;
+}
+
+sg_status sg_grid_info(sg_handle h, int g, int* levels, long* shape, double* coeff) {
+    SG_TRY(check_handle(h));
+    if (h->is_batch) return fail(SG_ERR_ARG, "sg_grid_info applies to batch members");
+    if (g < 0 || g >= h->G) return fail(SG_ERR_ARG, "grid index %d out of range", g);
+    for (int k = 0; k < h->dim; ++k) {
+        if (levels) levels[k] = h->levels[g][k];
+        if (shape) shape[k] = (long)h->nr << h->levels[g][k];
+    }
+    if (coeff) *coeff = h->coeff[g];
+    return SG_OK;
+}
+
+sg_status sg_time(sg_handle h, double* t, long* steps) {
+    SG_TRY(check_handle(h));
+    if (t) *t = h->t;
+    if (steps) *steps = (long)h->steps;
+    return SG_OK;
+}
+
+sg_status sg_batch_create(const sg_handle* hs, int n, sg_handle* out) {
+    if (!out) return fail(SG_ERR_ARG, "NULL output handle");
+    *out = nullptr;
+    if (!hs || n < 1) return fail(SG_ERR_ARG, "need at least one member");
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i] || hs[i]->is_batch) return fail(SG_ERR_ARG, "member %d is NULL or a batch", i);
+        const sg_ctx* a = hs[0];
+        const sg_ctx* b = hs[i];
+        if (b->dim != a->dim || b->pde != a->pde || b->esize != a->esize || b->prm.scheme != a->prm.scheme ||
+            b->prm.eps != a->prm.eps || b->ppt != a->ppt)
+            return fail(SG_ERR_ARG, "member %d differs in dim, pde, precision, scheme, eps or tile size", i);
+        for (int k = 0; k < a->dim; ++k)
+            if (b->prm.adv_speed[k] != a->prm.adv_speed[k]) return fail(SG_ERR_ARG, "member %d differs in adv_speed", i);
+    }
+    try {
+        sg_ctx* h = new sg_ctx();
+        h->is_batch = true;
+        h->dim = hs[0]->dim;
+        h->pde = hs[0]->pde;
+        h->prm = hs[0]->prm;
+        h->prm.cuda_stream = nullptr;
+        h->esize = hs[0]->esize;
+        h->ppt = hs[0]->ppt;
+        h->nr = hs[0]->nr;
+        h->nl = hs[0]->nl;
+        for (int i = 0; i < n; ++i) {
+            sg_ctx* m = hs[i];
+            h->members.push_back(m);
+            const int gbase = (int)h->hgrids.size();
+            for (const GridDesc& d0 : m->hgrids) {
+                GridDesc d = d0;
+                d.inst = i;
+                d.first_item = (int)h->hitems.size();
+                const int g = (int)h->hgrids.size();
+                for (int t = 0; t < d.n_items; ++t) h->hitems.push_back(WorkItem{g, t});
+                h->hgrids.push_back(d);
+            }
+            (void)gbase;
+            h->max_grid_pts = std::max(h->max_grid_pts, m->max_grid_pts);
+        }
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return fail(SG_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        h->own_stream = true;
+        sg_status st = h->dgrids.alloc(sizeof(GridDesc) * h->hgrids.size());
+        if (st == SG_OK) st = h->ditems.alloc(sizeof(WorkItem) * h->hitems.size());
+        if (st == SG_OK) st = alloc_step_buffers(h, (int)h->hgrids.size(), n);
+        if (st == SG_OK) {
+            if (cudaMemcpy(h->dgrids.p, h->hgrids.data(), sizeof(GridDesc) * h->hgrids.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(h->ditems.p, h->hitems.data(), sizeof(WorkItem) * h->hitems.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+                cudaGetLastError();
+                st = fail(SG_ERR_CUDA, "uploading the batch tables failed");
+            }
+        }
+        if (st != SG_OK) {
+            delete h;
+            return st;
+        }
+        ++g_live_handles;
+        *out = h;
+        return SG_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(SG_ERR_NOMEM, "host allocation failed");
+    }
+}
+
+sg_status sg_destroy(sg_handle h) {
+    if (!h) return SG_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    delete h;
+    --g_live_handles;
+    return SG_OK;
+}
+
+const char* sg_last_error(void) { return g_err.c_str(); }
+
+sg_status sg_set_allocator(sg_alloc_fn alloc, sg_free_fn release, void* ctx) {
+    if ((alloc == nullptr) != (release == nullptr)) return fail(SG_ERR_ARG, "alloc and release must both be set or both NULL");
+    if (g_live_handles != 0) return fail(SG_ERR_STATE, "cannot change the allocator while handles exist");
+    g_alloc = alloc;
+    g_free = release;
+    g_alloc_ctx = ctx;
+    return SG_OK;
+}
+
+sg_status sg_launch_count(sg_handle h, long* n) {
+    SG_TRY(check_handle(h));
+    if (!n) return fail(SG_ERR_ARG, "NULL output");
+    *n = (long)h->launches;
+    return SG_OK;
+}
+
+}  // extern "C"

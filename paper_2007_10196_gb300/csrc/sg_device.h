@@ -1,0 +1,88 @@
+// sg_device.h -- plain-data structures shared by the host API (sg_api.cu) and the kernels.
+//
+// Layout in HBM (one problem = one "instance"; a batch concatenates instances):
+//   * every component grid owns three state arrays u0/u1/u2 of n_0*...*n_{d-1} elements
+//     (axis 0 fastest), each 256-byte aligned inside the instance's arena;
+//   * the work queue is an array of (grid, tile) items, grid-major, tiles in row-major
+//     order of the tile grid;
+//   * alpha slots: three per grid (the max |f'(u)| of the input of RK stage 0, 1, 2), kept
+//     as the bit pattern of a non-negative double so that atomicMax on the integer orders
+//     them like the values;
+//   * one InstState per instance carries its time, step size and step counters on the
+//     device, so that graph-captured steps need no host round trip.
+#pragma once
+#include <cstdint>
+
+#define SG_MAXD 6
+
+struct GridDesc {
+    void* u0;            // u^n, and u^{n+1} after stage 2 (written in place)
+    void* u1;            // u^{(1)}
+    void* u2;            // u^{(2)}
+    long long npts;
+    int n[SG_MAXD];      // nodes per axis
+    int te[SG_MAXD];     // tile extent per axis
+    int nt[SG_MAXD];     // tiles per axis
+    double h[SG_MAXD];   // node spacing (hi-lo)/n
+    double rdx[SG_MAXD]; // 1/h
+    double lo[SG_MAXD];
+    double coeff;        // combination coefficient (-1)^q C(d-1,q)
+    int lev[SG_MAXD];
+    int inst;            // instance (batch member) index
+    int first_item;      // index of this grid's first work item
+    int n_items;
+    int pad_;
+};
+
+struct WorkItem {
+    int grid;
+    int tile;
+};
+
+struct InstState {
+    double t;
+    double dt;
+    double t_end;
+    double dt_nom;          // dt of the h^{5/3} rule (host-computed)
+    double cfl;
+    double hf[SG_MAXD];     // finest-grid spacing per axis
+    long long steps;
+    long long step_limit;
+    int active;             // 1 while a step is being taken
+    int pending;            // dt set, step not yet added to t
+    int grid0;              // first grid of this instance in the grid table
+    int ngrids;
+    int dt_rule;            // 0: h^{5/3}, 1: CFL
+    int last;               // the pending step is the shortened last one (ends at t_end)
+};
+
+struct PhysParams {
+    int dim;
+    int pde;                 // 0 advection, 1 Burgers
+    int scheme;              // 0 WENO5, 1 linear
+    int prolong;             // 0 WENO5 interpolation, 1 Lagrange
+    double eps;
+    double adv[SG_MAXD];
+};
+
+struct StageArgs {
+    const GridDesc* grids;
+    const WorkItem* items;
+    InstState* inst;
+    unsigned long long* alpha;  // [grids][3]
+    int* flags;                 // [0]: non-finite seen
+    int item_begin;
+    int item_end;
+    int stage;                  // 0, 1, 2
+    int pad_;
+    PhysParams phys;
+};
+
+// Exact solution of u0 = b + a sin(w sum x + phi) on the finest grid (for error norms).
+struct ExactSpec {
+    int dim, pde, nf;
+    double lo[SG_MAXD], h[SG_MAXD], adv[SG_MAXD];
+    double b, a, w, phi, t;
+};
+
+enum { SG_FLAG_NONFINITE = 0 };

@@ -1,0 +1,18 @@
+// FP64 instantiation of the kernels.  Compiled with --fmad=false so that every double
+// expression is evaluated as written (no fused multiply-add): the FP64 path then performs
+// the same IEEE-754 operations, in the same order, as a plain sequential evaluation of the
+// paper's formulas.
+#include "sg_launch_impl.cuh"
+
+namespace sg {
+
+template struct Launch<double>;
+
+cudaError_t launch_dt(InstState* inst, int ninst, const unsigned long long* alpha,
+                      const PhysParams& ph, int commit_only, cudaStream_t s) {
+    if (ninst < 1) return cudaSuccess;
+    sg_dt_kernel<<<(ninst + 127) / 128, 128, 0, s>>>(inst, ninst, alpha, ph, commit_only);
+    return cudaGetLastError();
+}
+
+}  // namespace sg

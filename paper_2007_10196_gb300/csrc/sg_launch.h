@@ -1,0 +1,40 @@
+// sg_launch.h -- host-side launchers of the kernels in sg_kernels.cuh.  Each precision is
+// compiled in its own translation unit (sg_kernels_f64.cu without FMA contraction,
+// sg_kernels_f32.cu with it); the API (sg_api.cu) sees only these declarations.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "sg_device.h"
+
+namespace sg {
+
+template <class T>
+struct Launch {
+    // Dynamic shared memory of the stage kernel for `ppt` points per thread.
+    static size_t stage_smem(int ppt);
+    // Resident blocks per SM of the stage kernel (occupancy), 0 if unsupported.
+    static int stage_blocks_per_sm(int dim, int ppt);
+    // One RK stage over work items [a.item_begin, a.item_end) with `nblocks` blocks.
+    static cudaError_t stage(int dim, int ppt, const StageArgs& a, int nblocks, cudaStream_t s);
+    // alpha slot 0 of every grid <- max |u0| (slots must be zero); flags non-finite values.
+    static cudaError_t alpha_init(const GridDesc* grids, int ngrids, long long max_pts,
+                                  unsigned long long* alpha, int* flags, cudaStream_t s);
+    // u0 of one grid <- p0 + p1 sin(p2 sum x + p3).
+    static cudaError_t restrict_sine(const GridDesc& g, int dim, const double* p, cudaStream_t s);
+    // One prolongation axis; acc != nullptr fuses "acc += coeff * result".
+    static cudaError_t prolong_axis(const T* in, T* out, double* acc, double coeff, long long below,
+                                    int min_, int nf, long long above, int r, double eps,
+                                    int lagrange, cudaStream_t s);
+    static cudaError_t accumulate(const T* u, double* acc, double coeff, long long n, cudaStream_t s);
+    // FP64 reduction of n values (kind as in sg_kernels.cuh); partial holds >= 1024 doubles.
+    static cudaError_t reduce(const T* u, long long n, int kind, const ExactSpec& X, double* partial,
+                              double* out, cudaStream_t s);
+};
+
+extern template struct Launch<double>;
+extern template struct Launch<float>;
+
+cudaError_t launch_dt(InstState* inst, int ninst, const unsigned long long* alpha,
+                      const PhysParams& ph, int commit_only, cudaStream_t s);
+
+}  // namespace sg

@@ -128,7 +128,7 @@ def _march(lmb, T, dt):
     while t < T:
         d = min(dt, T - t)
         A *= _rk3_amplification(d * lmb)
-        t = t + d
+        t = T if d == T - t else t + d
         n += 1
     return A, n
 
