@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""Benchmark of the sparse-grid WENO5 hot path on one GB300 (or N, one process each).
+
+Workload: an uneven batch of 256 independent 3-D Burgers problems u_t + sum_k (u^2/2)_{x_k} = 0
+on [0, 4]^3, u0 = 0.5 + a sin(pi (x+y+z)/2), a ~ U[0.5, 1], root cells N_r in {8, 12, 16},
+finest level N_L in {3, 4, 5} (seeded draws), all advanced to t = 0.3 with CFL 0.4, FP32 state,
+one persistent launch per RK stage over all members' grids, CUDA-graph replay.
+
+One benchmark step = one pass of the whole path over the batch: on-device restriction of the
+initial condition (Step 1), time marching to t = 0.3 (Step 2), WENO5 prolongation and signed
+combination in FP64 for every member (Step 3), FP64 min/max of every combined solution.
+
+Metric: grid-point updates per second (one point advanced one full RK3 step), whole job.
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2007_10196_gb300 import inputs  # noqa: E402  (seeded workload draws only)
+
+METRIC = "WENO5 grid-point updates/s and HBM GB/s fraction, FP32 batched vs FP64 plain at equal L1"
+UNIT = "grid-point updates/s"
+WORKLOAD = "burgers3d_batch256_t0.3_cfl0.4_f32_batched"
+
+# Algorithmic work of the FP32 stage kernel per grid point per RK stage for 3-D Burgers (FLOPs,
+# an FMA counts 2): per axis the LF split of the point (6), one interface flux with two
+# one-sided WENO5 reconstructions (2 x 54) and their combination (7), the flux difference (3);
+# plus the RK update (4 on average over the three stages).
+FLOPS_PER_POINT_STAGE_3D = 3 * (6 + 2 * 54 + 7 + 3) + 4
+# Algorithmic HBM bytes per point per full RK step (FP32): stage 1 reads u^n and writes u1,
+# stages 2 and 3 read the stage input and u^n and write the result: 8 + 12 + 12.
+BYTES_PER_POINT_STEP = 32
+FP32_LANES_PER_SM = 128
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+N_MEMBERS = 256
+
+
+def _members(rank):
+    return inputs.burgers3d_batch(256, seed=2007 + rank)[:N_MEMBERS]
+
+
+def _batch_points(members):
+    """Grid counts and points per member (sparse-grid combination of Section 2.2)."""
+    out = []
+    for m in members:
+        tot, grids = 0, 0
+        for q in range(3):
+            s = m.nl - q
+            for l0 in range(s + 1):
+                for l1 in range(s - l0 + 1):
+                    l2 = s - l0 - l1
+                    tot += (m.nr << l0) * (m.nr << l1) * (m.nr << l2)
+                    grids += 1
+        out.append((grids, tot))
+    return out
+
+
+# ------------------------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and --impl reference)
+# ------------------------------------------------------------------------------------------
+def _oracle_member(args):
+    nr, nl, a, nsteps = args
+    import oracle
+    p = oracle.problem(3, nr, nl, pde=oracle.BURGERS, eps=1e-3, lo=0.0, hi=4.0)
+    lev, co = oracle.grid_set(3, nl)
+    grids = [oracle.restrict_sine(p, l, 0.5, a, math.pi / 2) for l in lev]
+    t0 = time.perf_counter()
+    out, steps, t = oracle.solve(p, lev, grids, inputs.BATCH_T_END, max_steps=nsteps, rule=oracle.DT_CFL,
+                                 cfl=inputs.BATCH_CFL)
+    dt = time.perf_counter() - t0
+    return sum(g.size for g in out) * steps, dt
+
+
+def oracle_sample(members, pool, cores, nsteps=1):
+    """Runs the oracle on every member for `nsteps` time steps in a process pool; returns
+    (point-updates, wall seconds)."""
+    import oracle
+    oracle.build()
+    jobs = [(m.nr, m.nl, m.a, nsteps) for m in members]
+    jobs.sort(key=lambda j: -(j[0] << j[1]))  # largest first for balance
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_member, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    return sum(r[0] for r in res), wall
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.f:
+            return None
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _stage_traffic(points_per_launch):
+    """DRAM bytes per stage launch from the committed ncu summary, scaled by the points one
+    launch processes, if the kernel source still matches the one profiled; else None."""
+    path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        src = open(os.path.join(ROOT, "paper_2007_10196_gb300", "csrc", "sg_kernels.cuh"), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec["kernel_sha256"]:
+            return None
+        return rec["dram_bytes_per_point_stage"] * points_per_launch
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2007_10196_gb300 as P
+
+    pool = None
+    cores = 0
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = min(os.cpu_count() or 1, 64)
+        pool = mp.get_context("spawn").Pool(cores)
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    stream = torch.cuda.Stream()
+    members = _members(rank)
+    info = _batch_points(members)
+    P.build()
+    hs = []
+    with torch.cuda.stream(stream):
+        for m in members:
+            h = P.create(3, m.nr, m.nl, P.SG_PDE_BURGERS, precision=P.SG_F32, exec=P.SG_BATCHED,
+                         dt_rule=P.SG_DT_CFL, cfl=inputs.BATCH_CFL, cuda_stream=stream.cuda_stream)
+            hs.append(h)
+        batch = P.sg_batch_create(hs)
+    ics = [(0.5, m.a, math.pi / 2, 0.0) for m in members]
+    all_h = hs + [batch]
+
+    def one_pass(host_in=None, host_out=None):
+        if host_in is None:
+            for h, ic in zip(hs, ics):
+                P.sg_init(h, P.SG_IC_SINE, ic)
+        else:
+            for h, buf in zip(hs, host_in):
+                P.sg_init_grids(h, buf)
+        ev_step0.record(stream)
+        P.sg_step(batch, inputs.BATCH_T_END)
+        ev_step1.record(stream)
+        ext = []
+        for h in hs:
+            P.sg_prolong_combine(h)
+            ext.append((P.sg_reduce(h, -1, P.SG_REDUCE_MIN), P.sg_reduce(h, -1, P.SG_REDUCE_MAX)))
+        if host_out is not None:
+            for h, buf in zip(hs, host_out):
+                P.sg_read(h, P.SG_WHICH_ALL_GRIDS, out=buf)
+        return ext
+
+    def updates():
+        return sum(P.sg_time(h)[1] * n for h, (_, n) in zip(hs, info))
+
+    ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev_step0, ev_step1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_pass()
+        upd_per_pass = updates()
+        P.sg_set_profiling(batch, True)
+        launches0 = sum(P.sg_launch_count(h) for h in all_h)
+        step_ms = []
+        times = []
+        barrier()
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        smi_id = vis.split(",")[local_rank].strip() if vis else str(local_rank)
+        with ClockSampler(smi_id) as clk:
+            for _ in range(args.steps):
+                ev_a.record(stream)
+                ext = one_pass()
+                ev_b.record(stream)
+                ev_b.synchronize()
+                times.append(ev_a.elapsed_time(ev_b))
+                step_ms.append(ev_step0.elapsed_time(ev_step1))
+        barrier()
+        launches = sum(P.sg_launch_count(h) for h in all_h) - launches0
+        stage_ms, stage_launches = P.sg_profile(batch)
+        P.sg_set_profiling(batch, False)
+        assert updates() == upd_per_pass
+        # shock-capturing bound of the combined solutions (report, not tuned): u0 in [0.5-a, 0.5+a]
+        over = max(max(0.0, (0.5 - m.a) - lo, hi - (0.5 + m.a)) for m, (lo, hi) in zip(members, ext))
+
+        # end to end through the C ABI from pinned host buffers, results read back to host
+        e2e = None
+        if not args.no_e2e:
+            host_in, host_out = [], []
+            for h, (_, n) in zip(hs, info):
+                P.sg_init(h, P.SG_IC_SINE, ics[len(host_in)])
+                pin = torch.empty(n, dtype=torch.float32, pin_memory=True).numpy()
+                P.sg_read(h, P.SG_WHICH_ALL_GRIDS, out=pin)
+                host_in.append(pin)
+                host_out.append(torch.empty(n, dtype=torch.float32, pin_memory=True).numpy())
+            one_pass(host_in, host_out)  # warm
+            barrier()
+            et = []
+            for _ in range(max(1, args.steps // 2)):
+                ev_a.record(stream)
+                one_pass(host_in, host_out)
+                ev_b.record(stream)
+                ev_b.synchronize()
+                et.append(ev_a.elapsed_time(ev_b))
+            barrier()
+            nbytes = sum(n for _, n in info) * 4
+            e2e_ms = statistics.mean(et)
+            e2e = {"value": upd_per_pass / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                   "d2h_bytes_per_step": nbytes + 16 * len(hs), "ms_per_step": e2e_ms,
+                   "api": "sg_init_grids (pinned host) + sg_step + sg_prolong_combine + sg_reduce + sg_read"}
+
+    mean_ms = statistics.mean(times)
+    local = {"upd": upd_per_pass * args.steps, "ms": sum(times)}
+    if dist is not None:
+        t = torch.tensor([local["ms"], local["upd"]], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        total_ms, total_upd = float(mx[0]), float(sm[1])
+    else:
+        total_ms, total_upd = local["ms"], float(local["upd"])
+
+    for h in [batch] + hs:
+        P.sg_destroy(h)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks, src = _peaks()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    point_stages = 3 * upd_per_pass * args.steps
+    achieved = point_stages * FLOPS_PER_POINT_STAGE_3D / (stage_ms / 1e3) / 1e12
+    hbm_gbs = upd_per_pass * args.steps * BYTES_PER_POINT_STEP / (stage_ms / 1e3) / 1e9
+    traffic = _stage_traffic(point_stages / max(stage_launches, 1))
+    clocks = clk.summary()
+    cpu = None
+    if pool is not None:
+        upd_c, wall_c = oracle_sample(members, pool, cores, nsteps=1)
+        pool.close()
+        cpu = {"value": upd_c / wall_c, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "all %d members, first time step each (FP64 C oracle, one process per core)" % len(members),
+               "seconds": wall_c}
+    line = {
+        "metric": METRIC, "value": total_upd / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "members": len(members), "seed": 2007, "domain": "[0,4]^3",
+                   "grids": sum(g for g, _ in info), "points": sum(n for _, n in info),
+                   "pt_updates_per_step": upd_per_pass, "t_end": inputs.BATCH_T_END, "cfl": inputs.BATCH_CFL,
+                   "exec": "one persistent launch per RK stage over all members, graph replay",
+                   "l2": "inputs larger than L2 (3 FP32 state arrays of %.2f GB)" % (sum(n for _, n in info) * 4 / 1e9),
+                   "parallelism": "replicas" if world == 1 else "dp%d" % world},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": traffic,
+                     "kernel": "sg_stage_kernel<float,3,2>",
+                     "peak_source": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (%s SM clock)" % (nsm, FP32_LANES_PER_SM, sm_max, src)},
+        "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
+                "frac": hbm_gbs / float(peaks.get("hbm_gbs", 6800.0)), "peak_source": src,
+                "bytes_per_point_step": BYTES_PER_POINT_STEP},
+        "breakdown_ms": {"step_to_t_end": statistics.mean(step_ms), "stage_kernels": stage_ms / args.steps,
+                         "stage_launches": stage_launches // args.steps},
+        "stepping_rate": upd_per_pass / (statistics.mean(step_ms) / 1e3),
+        "bound_overshoot": over,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank, world):
+    """The FP64 C oracle on the host cores, each step a bounded sample of the workload."""
+    if rank != 0:
+        return
+    members = _members(0)
+    cores = min(os.cpu_count() or 1, 64)
+    pool = mp.get_context("spawn").Pool(cores)
+    for _ in range(args.warmup):
+        oracle_sample(members[:cores], pool, cores, nsteps=1)
+    upd, wall = 0, 0.0
+    for _ in range(args.steps):
+        u, w = oracle_sample(members, pool, cores, nsteps=1)
+        upd += u
+        wall += w
+    pool.close()
+    v = upd / wall
+    sample = "all %d members, first time step each (FP64 C oracle, one process per core)" % len(members)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "members": len(members), "seed": 2007},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--members", type=int, default=256,
+                    help="first M members of the batch only (small cases for profiling)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least three untimed passes
+    global N_MEMBERS
+    N_MEMBERS = max(1, min(256, args.members))
+    rank, world, local_rank = _env_rank()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -187,6 +187,16 @@ sg_status sg_set_allocator(sg_alloc_fn alloc, sg_free_fn release, void *ctx);
  * number of kernels this handle launched since creation. */
 sg_status sg_launch_count(sg_handle h, long *n_launches);
 
+/* Profiling.  With profiling on, every RK-stage launch of sg_step is bracketed by CUDA
+ * events recorded on the handle's stream (captured into the step graph), and their elapsed
+ * times are accumulated after each graph replay.  sg_profile(kind = SG_PROF_STAGE) returns
+ * the accumulated milliseconds and the number of stage kernel launches since profiling was
+ * switched on (a plain handle counts one launch per grid per stage; the events then bracket
+ * the group).  Switching profiling on or off re-captures the graph at the next sg_step. */
+enum { SG_PROF_STAGE = 0 };
+sg_status sg_set_profiling(sg_handle h, int on);
+sg_status sg_profile(sg_handle h, int kind, double *ms, long *launches);
+
 #ifdef __cplusplus
 }
 #endif

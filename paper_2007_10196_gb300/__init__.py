@@ -37,7 +37,9 @@ EXPORTED = [
     "sg_params_init", "sg_create", "sg_init", "sg_init_grid", "sg_init_grids", "sg_step",
     "sg_prolong_combine", "sg_read", "sg_reduce", "sg_num_grids", "sg_grid_info", "sg_time",
     "sg_batch_create", "sg_destroy", "sg_last_error", "sg_set_allocator", "sg_launch_count",
+    "sg_set_profiling", "sg_profile",
 ]
+SG_PROF_STAGE = 0
 
 
 class SgError(RuntimeError):
@@ -64,8 +66,9 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    from . import build as _b
-    return _b.build(force=force)
+    """Compiles libsgweno.so in-tree if any source is newer (paper_2007_10196_gb300/build.py)."""
+    import importlib
+    return importlib.import_module(__name__ + ".build").build(force=force)
 
 
 def lib():
@@ -96,6 +99,8 @@ def lib():
         "sg_last_error": (C.c_char_p, []),
         "sg_set_allocator": (st, [ALLOC_FN, FREE_FN, C.c_void_p]),
         "sg_launch_count": (st, [H, C.POINTER(C.c_long)]),
+        "sg_set_profiling": (st, [H, C.c_int]),
+        "sg_profile": (st, [H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -233,6 +238,17 @@ def sg_launch_count(h) -> int:
     n = C.c_long()
     _check(lib().sg_launch_count(h, C.byref(n)))
     return n.value
+
+
+def sg_set_profiling(h, on: bool = True):
+    _check(lib().sg_set_profiling(h, int(bool(on))))
+
+
+def sg_profile(h, kind: int = SG_PROF_STAGE):
+    """(milliseconds, launches) of the stage kernel since profiling was switched on."""
+    ms, n = C.c_double(), C.c_long()
+    _check(lib().sg_profile(h, kind, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
 
 
 _alloc_refs = None

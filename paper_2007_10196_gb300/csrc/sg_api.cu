@@ -139,7 +139,9 @@ struct sg_ctx {
     std::vector<long long> npts;
     std::vector<long long> offset;  // element offset of each grid inside a state region
     long long total_pts = 0;
-    DevBuf arena;  // [U0 region][U1 region][U2 region]
+    DevBuf arena;  // state regions u0, u1, u2 (and u3 = C for FP32), each all grids concatenated
+    long long box_elems = 0;  // stage kernel: elements of one padded box (d <= 3)
+    size_t smem = 0;          // stage kernel: dynamic shared memory per block
     // device tables (single handle or batch)
     std::vector<GridDesc> hgrids;
     std::vector<WorkItem> hitems;
@@ -153,6 +155,13 @@ struct sg_ctx {
     cudaGraphExec_t graph = nullptr;
     int graph_nsteps = 0;
     long long graph_kernels = 0;
+    bool graph_profiled = false;
+    // profiling: event pairs around each stage launch (group) of one graph replay
+    bool profile = false;
+    std::vector<cudaEvent_t> ev;
+    int ev_pairs_used = 0;
+    double prof_ms = 0.0;
+    long long prof_launches = 0;
     // state
     bool initialized = false;
     bool combined = false;
@@ -169,6 +178,7 @@ struct sg_ctx {
 
     ~sg_ctx() {
         if (graph) cudaGraphExecDestroy(graph);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -205,6 +215,7 @@ void fill_inst(const sg_ctx* h, InstState& s, int grid0, double t_end, long long
     s.cfl = h->prm.cfl;
     for (int k = 0; k < SG_MAXD; ++k) s.hf[k] = k < h->dim ? fine_spacing(h, k) : 1.0;
     s.steps = h->steps;
+    s.step0 = h->steps;
     s.step_limit = max_steps > (1LL << 62) - h->steps ? (1LL << 62) : h->steps + max_steps;
     s.active = 0;
     s.pending = 0;
@@ -238,14 +249,36 @@ int num_sms() {
     return n;
 }
 
+// Shared memory of the stage kernel for the largest tile among the given grids.
+void stage_footprint(sg_ctx* h) {
+    long long box = 1, flux = 1;
+    for (const GridDesc& d : h->hgrids) {
+        long long b, f;
+        sg::box_footprint(h->dim, d.te, &b, &f);
+        box = std::max(box, b);
+        flux = std::max(flux, f);
+    }
+    h->box_elems = box;
+    h->smem = h->esize == 8 ? sg::Launch<double>::stage_smem(h->dim, h->ppt, box, flux)
+                            : sg::Launch<float>::stage_smem(h->dim, h->ppt, box, flux);
+}
+
 int stage_blocks_per_sm(const sg_ctx* h) {
-    return h->esize == 8 ? sg::Launch<double>::stage_blocks_per_sm(h->dim, h->ppt)
-                         : sg::Launch<float>::stage_blocks_per_sm(h->dim, h->ppt);
+    return h->esize == 8 ? sg::Launch<double>::stage_prepare(h->dim, h->ppt, h->smem)
+                         : sg::Launch<float>::stage_prepare(h->dim, h->ppt, h->smem);
 }
 
 cudaError_t launch_stage(const sg_ctx* h, const StageArgs& a, int nblocks) {
-    return h->esize == 8 ? sg::Launch<double>::stage(h->dim, h->ppt, a, nblocks, h->stream)
-                         : sg::Launch<float>::stage(h->dim, h->ppt, a, nblocks, h->stream);
+    return h->esize == 8 ? sg::Launch<double>::stage(h->dim, h->ppt, a, nblocks, h->smem, h->stream)
+                         : sg::Launch<float>::stage(h->dim, h->ppt, a, nblocks, h->smem, h->stream);
+}
+
+// FP32 state: after a call in which instance i took an odd number of steps, U sits in the
+// second buffer of the ping-pong pair; swap the pair in the grid tables so that u0 holds U
+// again between calls.  `grids` are the instance's entries (a member's own table, or a slice
+// of a batch table).
+void swap_pair(GridDesc* grids, int n) {
+    for (int g = 0; g < n; ++g) std::swap(grids[g].u0, grids[g].u1);
 }
 
 sg_status validate_params(const sg_params* p, int dim) {
@@ -280,6 +313,7 @@ sg_status build_tables(sg_ctx* h) {
         d.u0 = base + (size_t)h->offset[g] * h->esize;
         d.u1 = base + region + (size_t)h->offset[g] * h->esize;
         d.u2 = base + 2 * region + (size_t)h->offset[g] * h->esize;
+        d.u3 = h->esize == 4 ? base + 3 * region + (size_t)h->offset[g] * h->esize : nullptr;
         d.npts = h->npts[g];
         int n[SG_MAXD] = {1, 1, 1, 1, 1, 1};
         for (int k = 0; k < h->dim; ++k) n[k] = h->nr << h->levels[g][k];
@@ -326,16 +360,29 @@ sg_status alloc_step_buffers(sg_ctx* h, int ngrids_total, int ninst) {
     h->ninst = ninst;
     SG_CUDA(cudaMemset(h->alpha.p, 0, h->alpha.bytes));
     SG_CUDA(cudaMemset(h->flags.p, 0, h->flags.bytes));
+    stage_footprint(h);
     const int bps = stage_blocks_per_sm(h);
     if (bps < 1) return fail(SG_ERR_CUDA, "stage kernel cannot be resident (dim %d, %d points/thread)", h->dim, h->ppt);
     h->blocks_total = bps * num_sms();
     return SG_OK;
 }
 
+sg_status ensure_events(sg_ctx* h, int pairs) {
+    while ((int)h->ev.size() < 2 * pairs) {
+        cudaEvent_t e;
+        SG_CUDA(cudaEventCreate(&e));
+        h->ev.push_back(e);
+    }
+    return SG_OK;
+}
+
 // Enqueues `nsteps` time steps (dt control + three RK stages each) on the handle's stream.
+// With profiling on, each stage launch (or per-grid launch group) is bracketed by an event pair.
 sg_status enqueue_steps(sg_ctx* h, int nsteps, long long* kernels) {
     const PhysParams ph = phys_of(h);
     long long nk = 0;
+    if (h->profile) SG_TRY(ensure_events(h, 3 * nsteps));
+    h->ev_pairs_used = h->profile ? 3 * nsteps : 0;
     for (int s = 0; s < nsteps; ++s) {
         SG_CUDA(sg::launch_dt(h->dinst.as<InstState>(), h->ninst, h->alpha.as<unsigned long long>(), ph, 0, h->stream));
         ++nk;
@@ -348,6 +395,9 @@ sg_status enqueue_steps(sg_ctx* h, int nsteps, long long* kernels) {
             a.flags = h->flags.as<int>();
             a.stage = stage;
             a.phys = ph;
+            a.box_elems = (int)h->box_elems;
+            const int pair = 3 * s + stage;
+            if (h->profile) SG_CUDA(cudaEventRecordWithFlags(h->ev[2 * pair], h->stream, cudaEventRecordExternal));
             const bool batched = h->is_batch || h->prm.exec == SG_BATCHED;
             if (batched) {
                 a.item_begin = 0;
@@ -362,14 +412,31 @@ sg_status enqueue_steps(sg_ctx* h, int nsteps, long long* kernels) {
                     ++nk;
                 }
             }
+            if (h->profile) SG_CUDA(cudaEventRecordWithFlags(h->ev[2 * pair + 1], h->stream, cudaEventRecordExternal));
         }
     }
     *kernels = nk;
     return SG_OK;
 }
 
+// After the enqueued steps completed: add the stage-launch times to the profile.
+sg_status collect_profile(sg_ctx* h) {
+    if (!h->profile) return SG_OK;
+    const bool batched = h->is_batch || h->prm.exec == SG_BATCHED;
+    for (int j = 0; j < h->ev_pairs_used; ++j) {
+        float ms = 0.f;
+        SG_CUDA(cudaEventElapsedTime(&ms, h->ev[2 * j], h->ev[2 * j + 1]));
+        h->prof_ms += ms;
+        h->prof_launches += batched ? 1 : (long long)h->hgrids.size();
+    }
+    return SG_OK;
+}
+
 sg_status ensure_graph(sg_ctx* h, int nsteps) {
-    if (h->graph && h->graph_nsteps == nsteps) return SG_OK;
+    if (h->graph && h->graph_nsteps == nsteps && h->graph_profiled == h->profile) {
+        h->ev_pairs_used = h->profile ? 3 * nsteps : 0;
+        return SG_OK;
+    }
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
@@ -396,6 +463,7 @@ sg_status ensure_graph(sg_ctx* h, int nsteps) {
     }
     h->graph_nsteps = nsteps;
     h->graph_kernels = nk;
+    h->graph_profiled = h->profile;
     return SG_OK;
 }
 
@@ -432,6 +500,7 @@ sg_status run_steps(sg_ctx* h) {
         }
         SG_CUDA(cudaMemcpyAsync(h->hinst.p, h->dinst.p, sizeof(InstState) * h->ninst, cudaMemcpyDeviceToHost, h->stream));
         SG_CUDA(cudaStreamSynchronize(h->stream));
+        SG_TRY(collect_profile(h));
         bool all = true;
         for (int i = 0; i < h->ninst; ++i) all = all && finished(h->hinst.p[i]);
         if (all) break;
@@ -596,7 +665,7 @@ sg_status sg_create(int dim, int root_cells, int level, int pde, const sg_params
             }
             h->own_stream = true;
         }
-        sg_status st = h->arena.alloc((size_t)h->total_pts * h->esize * 3);
+        sg_status st = h->arena.alloc((size_t)h->total_pts * h->esize * (h->esize == 4 ? 4 : 3));
         if (st == SG_OK) st = build_tables(h);
         if (st == SG_OK) st = alloc_step_buffers(h, h->G, 1);
         if (st != SG_OK) {
@@ -642,6 +711,7 @@ sg_status sg_init_grid(sg_handle h, int grid, const void* host_values, size_t by
     const size_t need = (size_t)h->npts[grid] * h->esize;
     if (bytes != need) return fail(SG_ERR_ARG, "grid %d needs %zu bytes, got %zu", grid, need, bytes);
     SG_CUDA(cudaMemcpyAsync(h->hgrids[grid].u0, host_values, need, cudaMemcpyHostToDevice, h->stream));
+    if (h->hgrids[grid].u3) SG_CUDA(cudaMemsetAsync(h->hgrids[grid].u3, 0, need, h->stream));
     SG_CUDA(cudaStreamSynchronize(h->stream));
     h->ic_sine = false;
     h->initialized = true;
@@ -658,6 +728,7 @@ sg_status sg_init_grids(sg_handle h, const void* host_values, size_t bytes) {
     const size_t need = (size_t)h->total_pts * h->esize;
     if (bytes != need) return fail(SG_ERR_ARG, "all grids need %zu bytes, got %zu", need, bytes);
     SG_CUDA(cudaMemcpyAsync(h->hgrids[0].u0, host_values, need, cudaMemcpyHostToDevice, h->stream));
+    if (h->hgrids[0].u3) SG_CUDA(cudaMemsetAsync(h->hgrids[0].u3, 0, need, h->stream));
     SG_CUDA(cudaStreamSynchronize(h->stream));
     h->ic_sine = false;
     h->initialized = true;
@@ -676,8 +747,13 @@ sg_status sg_step(sg_handle h, double t_end, long max_steps, double* t_reached) 
             if (!h->initialized) return fail(SG_ERR_STATE, "sg_step before sg_init");
             fill_inst(h, h->hinst.p[0], 0, t_end, max_steps);
             sg_status st = run_steps(h);
-            h->t = h->hinst.p[0].t;
-            h->steps = h->hinst.p[0].steps;
+            const InstState& s = h->hinst.p[0];
+            if (h->esize == 4 && ((s.steps - s.step0) & 1)) {
+                swap_pair(h->hgrids.data(), h->G);
+                SG_CUDA(cudaMemcpy(h->dgrids.p, h->hgrids.data(), sizeof(GridDesc) * h->hgrids.size(), cudaMemcpyHostToDevice));
+            }
+            h->t = s.t;
+            h->steps = s.steps;
             h->combined = false;
             if (t_reached) *t_reached = h->t;
             return st;
@@ -688,17 +764,32 @@ sg_status sg_step(sg_handle h, double t_end, long max_steps, double* t_reached) 
             if (!m->initialized) return fail(SG_ERR_STATE, "batch member %zu not initialised", i);
             SG_CUDA(cudaStreamSynchronize(m->stream));
             fill_inst(m, h->hinst.p[i], gbase, t_end, max_steps);
+            for (int g = 0; g < m->G; ++g) {  // members may have been stepped on their own
+                h->hgrids[gbase + g].u0 = m->hgrids[g].u0;
+                h->hgrids[gbase + g].u1 = m->hgrids[g].u1;
+            }
             gbase += m->G;
         }
+        SG_CUDA(cudaMemcpy(h->dgrids.p, h->hgrids.data(), sizeof(GridDesc) * h->hgrids.size(), cudaMemcpyHostToDevice));
         sg_status st = run_steps(h);
         double tmin = INFINITY;
+        bool swapped = false;
         for (size_t i = 0; i < h->members.size(); ++i) {
             sg_ctx* m = h->members[i];
-            m->t = h->hinst.p[i].t;
-            m->steps = h->hinst.p[i].steps;
+            const InstState& s = h->hinst.p[i];
+            if (m->esize == 4 && ((s.steps - s.step0) & 1)) {
+                swap_pair(m->hgrids.data(), m->G);
+                swap_pair(h->hgrids.data() + s.grid0, m->G);
+                SG_CUDA(cudaMemcpy(m->dgrids.p, m->hgrids.data(), sizeof(GridDesc) * m->hgrids.size(), cudaMemcpyHostToDevice));
+                swapped = true;
+            }
+            m->t = s.t;
+            m->steps = s.steps;
             m->combined = false;
             tmin = std::min(tmin, m->t);
         }
+        if (swapped)
+            SG_CUDA(cudaMemcpy(h->dgrids.p, h->hgrids.data(), sizeof(GridDesc) * h->hgrids.size(), cudaMemcpyHostToDevice));
         if (t_reached) *t_reached = tmin;
         return st;
     } catch (const std::bad_alloc&) {
@@ -773,15 +864,15 @@ sg_status sg_reduce(sg_handle h, int which, int kind, double* out) {
         if (exact && !h->ic_sine) return fail(SG_ERR_STATE, "exact-solution norms need an SG_IC_SINE initial condition");
         n = h->fine_pts;
         for (int k = 0; k < h->dim; ++k) vol = vol * fine_spacing(h, k);
-        SG_CUDA(sg::Launch<double>::reduce(h->uhat.as<double>(), n, kind, X, h->partial.as<double>(), dres, h->stream));
+        SG_CUDA(sg::Launch<double>::reduce(h->uhat.as<double>(), nullptr, n, kind, X, h->partial.as<double>(), dres, h->stream));
     } else if (which >= 0 && which < h->G) {
         if (exact) return fail(SG_ERR_ARG, "exact-solution norms apply to the combined solution (which = -1)");
         n = h->npts[which];
         for (int k = 0; k < h->dim; ++k) vol = vol * h->hgrids[which].h[k];
         if (h->esize == 8)
-            SG_CUDA(sg::Launch<double>::reduce((const double*)h->hgrids[which].u0, n, kind, X, h->partial.as<double>(), dres, h->stream));
-        else
-            SG_CUDA(sg::Launch<float>::reduce((const float*)h->hgrids[which].u0, n, kind, X, h->partial.as<double>(), dres, h->stream));
+            SG_CUDA(sg::Launch<double>::reduce((const double*)h->hgrids[which].u0, nullptr, n, kind, X, h->partial.as<double>(), dres, h->stream));
+        else  // FP32 state is the float pair U + C
+            SG_CUDA(sg::Launch<float>::reduce((const float*)h->hgrids[which].u0, (const float*)h->hgrids[which].u3, n, kind, X, h->partial.as<double>(), dres, h->stream));
     } else {
         return fail(SG_ERR_ARG, "which = %d out of range", which);
     }
@@ -865,13 +956,22 @@ sg_status sg_batch_create(const sg_handle* hs, int n, sg_handle* out) {
             (void)gbase;
             h->max_grid_pts = std::max(h->max_grid_pts, m->max_grid_pts);
         }
-        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            delete h;
-            return fail(SG_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        // members that all run on one caller-provided stream: the batch uses it too, so that
+        // the caller's stream orders every operation; otherwise the batch owns a stream
+        bool shared = !hs[0]->own_stream;
+        for (int i = 1; i < n && shared; ++i) shared = !hs[i]->own_stream && hs[i]->stream == hs[0]->stream;
+        if (shared) {
+            h->stream = hs[0]->stream;
+            h->own_stream = false;
+        } else {
+            cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                delete h;
+                return fail(SG_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+            }
+            h->own_stream = true;
         }
-        h->own_stream = true;
         sg_status st = h->dgrids.alloc(sizeof(GridDesc) * h->hgrids.size());
         if (st == SG_OK) st = h->ditems.alloc(sizeof(WorkItem) * h->hitems.size());
         if (st == SG_OK) st = alloc_step_buffers(h, (int)h->hgrids.size(), n);
@@ -917,6 +1017,22 @@ sg_status sg_launch_count(sg_handle h, long* n) {
     SG_TRY(check_handle(h));
     if (!n) return fail(SG_ERR_ARG, "NULL output");
     *n = (long)h->launches;
+    return SG_OK;
+}
+
+sg_status sg_set_profiling(sg_handle h, int on) {
+    SG_TRY(check_handle(h));
+    h->profile = on != 0;
+    h->prof_ms = 0.0;
+    h->prof_launches = 0;
+    return SG_OK;
+}
+
+sg_status sg_profile(sg_handle h, int kind, double* ms, long* launches) {
+    SG_TRY(check_handle(h));
+    if (kind != SG_PROF_STAGE) return fail(SG_ERR_ARG, "unknown profile kind %d", kind);
+    if (ms) *ms = h->prof_ms;
+    if (launches) *launches = (long)h->prof_launches;
     return SG_OK;
 }
 

@@ -16,9 +16,14 @@
 #define SG_MAXD 6
 
 struct GridDesc {
-    void* u0;            // u^n, and u^{n+1} after stage 2 (written in place)
-    void* u1;            // u^{(1)}
-    void* u2;            // u^{(2)}
+    // FP64: u0 = u^n (u^{n+1} written in place by the last stage), u1 = u^{(1)}, u2 = u^{(2)}.
+    // FP32: (u0, u1) = ping-pong pair holding U (the float head of u^n) and the first stage
+    // increment, u2 = second-stage increment, u3 = C (the float tail: u^n = U + C).
+    // Between calls u0 always holds U.
+    void* u0;
+    void* u1;
+    void* u2;
+    void* u3;
     long long npts;
     int n[SG_MAXD];      // nodes per axis
     int te[SG_MAXD];     // tile extent per axis
@@ -47,6 +52,7 @@ struct InstState {
     double cfl;
     double hf[SG_MAXD];     // finest-grid spacing per axis
     long long steps;
+    long long step0;        // steps at the start of the current sg_step call (FP32 ping-pong parity)
     long long step_limit;
     int active;             // 1 while a step is being taken
     int pending;            // dt set, step not yet added to t
@@ -74,7 +80,7 @@ struct StageArgs {
     int item_begin;
     int item_end;
     int stage;                  // 0, 1, 2
-    int pad_;
+    int box_elems;              // box kernel: elements of one padded box in shared memory
     PhysParams phys;
 };
 

@@ -1,636 +1,13 @@
-// sg_kernels.cuh -- CUDA kernels of the sparse-grid WENO5 hot path, templated on the state
-// precision T (double or float) and the dimension D.
+// sg_kernels.cuh -- all CUDA kernels of the sparse-grid WENO5 hot path, templated on the state
+// precision T (double or float) and the dimension.
 //
 // Instantiated twice:
-//   sg_kernels_f64.cu, compiled with --fmad=false: every double expression below is then a
-//     fixed sequence of IEEE-754 operations in the order the paper prints the formula, so
-//     the FP64 path reproduces a plain sequential evaluation bit for bit;
+//   sg_kernels_f64.cu, compiled with --fmad=false: every double expression is then a fixed
+//     sequence of IEEE-754 operations in the order the paper prints the formula, so the FP64
+//     path reproduces a plain sequential evaluation bit for bit;
 //   sg_kernels_f32.cu, with contraction on: the float path uses an algebraically equivalent
-//     reformulation with fewer operations (first differences, one reciprocal per interface).
+//     reformulation with fewer operations and a compensated state.
 #pragma once
-#include <cuda_runtime.h>
-#include <stdint.h>
-
-#include "sg_device.h"
-
-#define SG_NT 256  // threads per block of the stage kernel
-
-// ------------------------------------------------------------------------------------
-// Small helpers
-// ------------------------------------------------------------------------------------
-
-// Exact unsigned division by a run-time divisor d <= 2^16 for x < 2^16 (multiply-high by
-// ceil(2^32 / d)).  x (d - 1) < 2^32 guarantees floor(x m / 2^32) = floor(x / d).
-struct FDiv {
-    unsigned m, d;
-    __device__ __forceinline__ void init(unsigned dd) {
-        d = dd;
-        m = dd <= 1u ? 0u : (unsigned)((0x100000000ull + dd - 1ull) / (unsigned long long)dd);
-    }
-    __device__ __forceinline__ unsigned div(unsigned x) const { return d <= 1u ? x : __umulhi(x, m); }
-};
-
-__device__ __forceinline__ unsigned long long dbits(double v) {
-    return (unsigned long long)__double_as_longlong(v);
-}
-__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
-
-template <class T>
-__device__ __forceinline__ T sg_abs(T v) { return v < T(0) ? -v : v; }
-
-__device__ __forceinline__ bool sg_isfinite(double v) { return isfinite(v); }
-__device__ __forceinline__ bool sg_isfinite(float v) { return isfinite(v); }
-
-__device__ __forceinline__ double block_max(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    }
-    __syncthreads();
-    return v;  // valid in thread 0
-}
-
-// ------------------------------------------------------------------------------------
-// Numerical flux at one interface x_{i+1/2} from u_{i-2} .. u_{i+3}:
-// Lax-Friedrichs split f^{+-} = (f +- alpha u)/2 (Eq. 7), WENO5 on f^+ with the stencil
-// i-2..i+2 and on f^- with its mirror image i+3..i-1 (Section 2.1), fhat = fhat^+ + fhat^-.
-// ------------------------------------------------------------------------------------
-template <class T>
-struct Weno;
-
-// FP64: Eqs. (3)-(6) evaluated literally; must be compiled without contraction.
-template <>
-struct Weno<double> {
-    static __device__ __forceinline__ double side(double a, double b, double c, double d, double e,
-                                                  double eps, int linear) {
-        const double q0 = (1.0 / 3.0) * a - (7.0 / 6.0) * b + (11.0 / 6.0) * c;
-        const double q1 = -(1.0 / 6.0) * b + (5.0 / 6.0) * c + (1.0 / 3.0) * d;
-        const double q2 = (1.0 / 3.0) * c + (5.0 / 6.0) * d - (1.0 / 6.0) * e;
-        double w0 = 0.1, w1 = 0.6, w2 = 0.3;
-        if (!linear) {
-            const double r0 = a - 2.0 * b + c, g0 = a - 4.0 * b + 3.0 * c;
-            const double r1 = b - 2.0 * c + d, g1 = b - d;
-            const double r2 = c - 2.0 * d + e, g2 = 3.0 * c - 4.0 * d + e;
-            const double b0 = (13.0 / 12.0) * (r0 * r0) + 0.25 * (g0 * g0);
-            const double b1 = (13.0 / 12.0) * (r1 * r1) + 0.25 * (g1 * g1);
-            const double b2 = (13.0 / 12.0) * (r2 * r2) + 0.25 * (g2 * g2);
-            w0 = 0.1 / ((eps + b0) * (eps + b0));
-            w1 = 0.6 / ((eps + b1) * (eps + b1));
-            w2 = 0.3 / ((eps + b2) * (eps + b2));
-        }
-        return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
-    }
-
-    static __device__ __forceinline__ double interface(const double* v, double alpha, double ak,
-                                                       const PhysParams& ph) {
-        double fp[6], fm[6];
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            const double u = v[j];
-            const double f = ph.pde == 1 ? (0.5 * u) * u : ak * u;
-            fp[j] = 0.5 * (f + alpha * u);
-            fm[j] = 0.5 * (f - alpha * u);
-        }
-        const double fplus = side(fp[0], fp[1], fp[2], fp[3], fp[4], ph.eps, ph.scheme);
-        const double fminus = side(fm[5], fm[4], fm[3], fm[2], fm[1], ph.eps, ph.scheme);
-        return fplus + fminus;
-    }
-
-    // WENO5 / Lagrange interpolation at x_i + s h, Eqs. (8)-(11), literal order.
-    static __device__ __forceinline__ double interp(double a, double b, double c, double d, double e,
-                                                    double s, double eps, int lagrange) {
-        if (s == 0.0) return c;
-        const double g0 = 0.5 * (a - 4.0 * b + 3.0 * c), k0 = 0.5 * (a - 2.0 * b + c);
-        const double g1 = 0.5 * (d - b), k1 = 0.5 * (b - 2.0 * c + d);
-        const double g2 = 0.5 * (-3.0 * c + 4.0 * d - e), k2 = 0.5 * (c - 2.0 * d + e);
-        const double P0 = c + s * (g0 + s * k0);
-        const double P1 = c + s * (g1 + s * k1);
-        const double P2 = c + s * (g2 + s * k2);
-        const double C0 = ((s - 1.0) * (s - 2.0)) / 12.0;
-        const double C1 = (4.0 - s * s) / 6.0;
-        const double C2 = ((s + 1.0) * (s + 2.0)) / 12.0;
-        if (lagrange) return C0 * P0 + C1 * P1 + C2 * P2;
-        const double r0 = a - 2.0 * b + c, g0s = a - 4.0 * b + 3.0 * c;
-        const double r1 = b - 2.0 * c + d, g1s = b - d;
-        const double r2 = c - 2.0 * d + e, g2s = 3.0 * c - 4.0 * d + e;
-        const double b0 = (13.0 / 12.0) * (r0 * r0) + 0.25 * (g0s * g0s);
-        const double b1 = (13.0 / 12.0) * (r1 * r1) + 0.25 * (g1s * g1s);
-        const double b2 = (13.0 / 12.0) * (r2 * r2) + 0.25 * (g2s * g2s);
-        const double w0 = C0 / ((eps + b0) * (eps + b0));
-        const double w1 = C1 / ((eps + b1) * (eps + b1));
-        const double w2 = C2 / ((eps + b2) * (eps + b2));
-        return (w0 * P0 + w1 * P1 + w2 * P2) / (w0 + w1 + w2);
-    }
-};
-
-// FP32: the same mathematics in first differences d_j = f_j - f_{j-1}:
-//   q_r - f_i : (5/6 d2 - 1/3 d1, 1/6 d2 + 1/3 d3, 2/3 d3 - 1/6 d4)
-//   12 (eps + beta_r) = 13 t_r^2 + 3 s_r^2 + 12 eps, t = second differences,
-//   s = (3 d2 - d1, d2 + d3, 3 d3 - d4)
-//   alpha_r / alpha_1 = (d_r/d_1) prod_{j != r} E_j / prod_{j != 1} E_j, E_r = (12(eps+beta_r))^2
-// so one side costs no division; the two sides share one reciprocal.
-template <>
-struct Weno<float> {
-    static __device__ __forceinline__ void side(float a, float b, float c, float d, float e,
-                                                float eps12, int linear, float& num, float& den) {
-        const float d1 = b - a, d2 = c - b, d3 = d - c, d4 = e - d;
-        const float p0 = fmaf(5.f / 6.f, d2, (-1.f / 3.f) * d1);
-        const float p1 = fmaf(1.f / 6.f, d2, (1.f / 3.f) * d3);
-        const float p2 = fmaf(2.f / 3.f, d3, (-1.f / 6.f) * d4);
-        float a0, a1, a2;
-        if (linear) {
-            a0 = 0.1f;
-            a1 = 0.6f;
-            a2 = 0.3f;
-        } else {
-            const float t0 = d2 - d1, t1 = d3 - d2, t2 = d4 - d3;
-            const float s0 = fmaf(3.f, d2, -d1), s1 = d2 + d3, s2 = fmaf(3.f, d3, -d4);
-            const float e0 = fmaf(13.f * t0, t0, fmaf(3.f * s0, s0, eps12));
-            const float e1 = fmaf(13.f * t1, t1, fmaf(3.f * s1, s1, eps12));
-            const float e2 = fmaf(13.f * t2, t2, fmaf(3.f * s2, s2, eps12));
-            const float E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
-            a0 = (1.f / 6.f) * (E1 * E2);
-            a1 = E0 * E2;
-            a2 = 0.5f * (E0 * E1);
-        }
-        num = fmaf(a0, p0, fmaf(a1, p1, a2 * p2));
-        den = a0 + a1 + a2;
-    }
-
-    static __device__ __forceinline__ float interface(const float* v, float alpha, float ak,
-                                                      const PhysParams& ph, float eps12) {
-        float fp[6], fm[6];
-        if (ph.pde == 1) {
-            const float ha = 0.5f * alpha;
-#pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                fp[j] = v[j] * fmaf(0.25f, v[j], ha);
-                fm[j] = v[j] * fmaf(0.25f, v[j], -ha);
-            }
-        } else {
-            const float cp = 0.5f * (ak + alpha), cm = 0.5f * (ak - alpha);
-#pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                fp[j] = cp * v[j];
-                fm[j] = cm * v[j];
-            }
-        }
-        float np, dp, nm, dm;
-        side(fp[0], fp[1], fp[2], fp[3], fp[4], eps12, ph.scheme, np, dp);
-        side(fm[5], fm[4], fm[3], fm[2], fm[1], eps12, ph.scheme, nm, dm);
-        return (fp[2] + fm[3]) + __fdividef(fmaf(np, dm, nm * dp), dp * dm);
-    }
-
-    static __device__ __forceinline__ float interp(float a, float b, float c, float d, float e,
-                                                   float s, float eps12, int lagrange) {
-        if (s == 0.f) return c;
-        const float d1 = b - a, d2 = c - b, d3 = d - c, d4 = e - d;
-        const float t0 = d2 - d1, t1 = d3 - d2, t2 = d4 - d3;
-        const float s0 = fmaf(3.f, d2, -d1), s1 = d2 + d3, s2 = fmaf(3.f, d3, -d4);
-        // P_k(s) - c = (s/2) (s_k + s t_k)
-        const float p0 = fmaf(s, t0, s0), p1 = fmaf(s, t1, s1), p2 = fmaf(s, t2, s2);
-        const float C0 = (s - 1.f) * (s - 2.f) * (1.f / 12.f);
-        const float C1 = fmaf(-s, s, 4.f) * (1.f / 6.f);
-        const float C2 = (s + 1.f) * (s + 2.f) * (1.f / 12.f);
-        float w0 = C0, w1 = C1, w2 = C2;
-        if (!lagrange) {
-            const float e0 = fmaf(13.f * t0, t0, fmaf(3.f * s0, s0, eps12));
-            const float e1 = fmaf(13.f * t1, t1, fmaf(3.f * s1, s1, eps12));
-            const float e2 = fmaf(13.f * t2, t2, fmaf(3.f * s2, s2, eps12));
-            const float E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
-            w0 = C0 * (E1 * E2);
-            w1 = C1 * (E0 * E2);
-            w2 = C2 * (E0 * E1);
-        }
-        const float num = fmaf(w0, p0, fmaf(w1, p1, w2 * p2));
-        return fmaf(0.5f * s, __fdividef(num, w0 + w1 + w2), c);
-    }
-};
-
-// ------------------------------------------------------------------------------------
-// RK3 stage kernel.  One persistent block walks work items (grid, tile) of
-// [item_begin, item_end).  Per item: for each axis k, the tile's lines along k plus a
-// 3-point periodic halo are staged in shared memory, every interface flux of the tile is
-// computed once into shared memory, and each thread subtracts (F_{i+1/2} - F_{i-1/2})/h_k
-// for the points it owns.  Then the Shu-Osher stage update is applied, the result written,
-// and max |u| of the result reduced into the alpha slot of the next stage (Burgers).
-// ------------------------------------------------------------------------------------
-template <int PPT>
-struct StageSmem {
-    // worst case over tile shapes with P <= SG_NT*PPT points and extents >= 1:
-    // line buffer (ek + 7) * P / ek <= 8 P; flux buffer (ek + 2) * P / ek <= 3 P
-    static constexpr int P = SG_NT * PPT;
-    static constexpr int LB = 8 * P;
-    static constexpr int FB = 3 * P;
-};
-
-template <class T, int D, int PPT>
-__global__ void __launch_bounds__(SG_NT) sg_stage_kernel(const StageArgs A) {
-    extern __shared__ __align__(16) unsigned char sg_smem_raw[];
-    T* lb = reinterpret_cast<T*>(sg_smem_raw);
-    T* fb = lb + StageSmem<PPT>::LB;
-    __shared__ double red[SG_NT / 32];
-
-    const int tid = threadIdx.x;
-    const int stage = A.stage;
-    const PhysParams& ph = A.phys;
-
-    for (int it = A.item_begin + blockIdx.x; it < A.item_end; it += gridDim.x) {
-        const WorkItem w = A.items[it];
-        const GridDesc* G = A.grids + w.grid;
-        const InstState* S = A.inst + G->inst;
-        if (!S->active) continue;  // uniform: the state is not written during this kernel
-        const double dt = S->dt;
-
-        int org[D], ext[D], nn[D];
-        long long gstr[D];
-        FDiv fd[D];
-        int P = 1;
-        {
-            unsigned tt = (unsigned)w.tile;
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const unsigned nt = (unsigned)G->nt[k];
-                const unsigned tc = tt % nt;
-                tt /= nt;
-                nn[k] = G->n[k];
-                org[k] = (int)tc * G->te[k];
-                ext[k] = min(G->te[k], nn[k] - org[k]);
-                gstr[k] = k == 0 ? 1LL : gstr[k - 1] * (long long)nn[k - 1];
-                fd[k].init((unsigned)ext[k]);
-                P *= ext[k];
-            }
-        }
-        const T* uin = (const T*)(stage == 0 ? G->u0 : stage == 1 ? G->u1 : G->u2);
-        T* uout = (T*)(stage == 0 ? G->u1 : stage == 1 ? G->u2 : G->u0);
-        const T* un = (const T*)G->u0;
-        const double alpha_slot = bitsd(A.alpha[w.grid * 3 + stage]);
-
-        // owned points: tile-local coordinates
-        int cp[PPT][D];
-        bool own[PPT];
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-            const int p = tid + q * SG_NT;
-            own[q] = p < P;
-            unsigned r = (unsigned)(own[q] ? p : 0);
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const unsigned qq = fd[k].div(r);
-                cp[q][k] = (int)(r - qq * (unsigned)ext[k]);
-                r = qq;
-            }
-        }
-        T acc[PPT];
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) acc[q] = T(0);
-
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-            const int ek = ext[k];
-            const int lines = P / ek;
-            const int ls = (ek + 6) | 1;  // odd strides avoid bank conflicts
-            const int fs = (ek + 1) | 1;
-            const T alpha = ph.pde == 1 ? (T)alpha_slot : (T)sg_abs(ph.adv[k]);
-            const T ak = (T)ph.adv[k];
-            FDiv fl, fr, ff;
-            fl.init((unsigned)lines);
-            fr.init((unsigned)(ek + 6));
-            ff.init((unsigned)(ek + 1));
-
-            // 1) stage lines (with periodic halo of 3) in shared memory
-            const int NL = lines * (ek + 6);
-            for (int e = tid; e < NL; e += SG_NT) {
-                int line, i;
-                if (k == 0) {
-                    line = (int)fr.div((unsigned)e);
-                    i = e - line * (ek + 6);
-                } else {
-                    i = (int)fl.div((unsigned)e);
-                    line = e - i * lines;
-                }
-                long long g = 0;
-                unsigned rem = (unsigned)line;
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    if (j == k) continue;
-                    const unsigned qq = fd[j].div(rem);
-                    const int cj = (int)(rem - qq * (unsigned)ext[j]);
-                    rem = qq;
-                    g += (long long)(org[j] + cj) * gstr[j];
-                }
-                int ck = org[k] + i - 3;
-                if (ck < 0) ck += nn[k];
-                else if (ck >= nn[k]) ck -= nn[k];
-                g += (long long)ck * gstr[k];
-                lb[line * ls + i] = uin[g];
-            }
-            __syncthreads();
-
-            // 2) interface fluxes F[line][i] at x_{org+i-1/2}, i = 0..ek
-            const int NF = lines * (ek + 1);
-            for (int e = tid; e < NF; e += SG_NT) {
-                const int line = (int)ff.div((unsigned)e);
-                const int i = e - line * (ek + 1);
-                const T* v = lb + line * ls + i;
-                if constexpr (sizeof(T) == 8) {
-                    fb[line * fs + i] = Weno<double>::interface((const double*)v, (double)alpha, (double)ak, ph);
-                } else {
-                    fb[line * fs + i] = Weno<float>::interface((const float*)v, (float)alpha, (float)ak, ph,
-                                                               (float)(12.0 * ph.eps));
-                }
-            }
-            __syncthreads();
-
-            // 3) flux difference for owned points
-            const T rdx = (T)G->rdx[k];
-#pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                if (!own[q]) continue;
-                int line = 0, mul = 1;
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    if (j == k) continue;
-                    line += cp[q][j] * mul;
-                    mul *= ext[j];
-                }
-                const int i = cp[q][k];
-                const T* F = fb + line * fs + i;
-                acc[q] = acc[q] - (F[1] - F[0]) * rdx;
-            }
-            __syncthreads();
-        }
-
-        // 4) TVD-RK3 (Shu-Osher) stage update, alpha reduction of the result
-        double mx = 0.0;
-        bool bad = false;
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-            if (!own[q]) continue;
-            long long g = 0;
-#pragma unroll
-            for (int k = 0; k < D; ++k) g += (long long)(org[k] + cp[q][k]) * gstr[k];
-            const T us = uin[g];
-            const T L = acc[q];
-            T o;
-            if constexpr (sizeof(T) == 8) {
-                const double dtt = dt;
-                if (stage == 0) o = us + dtt * L;
-                else if (stage == 1) o = 0.75 * un[g] + 0.25 * (us + dtt * L);
-                else o = (1.0 / 3.0) * un[g] + (2.0 / 3.0) * (us + dtt * L);
-            } else {
-                const float dtf = (float)dt;
-                if (stage == 0) o = fmaf(dtf, L, us);
-                else if (stage == 1) o = fmaf(0.75f, un[g], 0.25f * fmaf(dtf, L, us));
-                else o = fmaf(1.f / 3.f, un[g], (2.f / 3.f) * fmaf(dtf, L, us));
-            }
-            uout[g] = o;
-            if (!sg_isfinite(o)) bad = true;
-            mx = fmax(mx, (double)sg_abs(o));
-        }
-        if (__syncthreads_or(bad) && tid == 0) atomicOr(A.flags + SG_FLAG_NONFINITE, 1);
-        if (ph.pde == 1) {
-            const double m = block_max(mx, red);
-            if (tid == 0) atomicMax(A.alpha + w.grid * 3 + (stage + 1) % 3, dbits(m));
-        }
-        if (tid == 0 && it == G->first_item) A.alpha[w.grid * 3 + (stage + 2) % 3] = 0ull;
-    }
-}
-
-// max |u| of the stage-0 input over every tile of the queue -> alpha slot 0 (the slots of
-// stages 1 and 2 are cleared by the caller); also flags non-finite values.
-template <class T>
-__global__ void __launch_bounds__(SG_NT) sg_alpha_init_kernel(const GridDesc* grids, int ngrids,
-                                                               unsigned long long* alpha, int* flags) {
-    __shared__ double red[SG_NT / 32];
-    for (int g = blockIdx.y; g < ngrids; g += gridDim.y) {
-        const GridDesc* G = grids + g;
-        const T* u = (const T*)G->u0;
-        double mx = 0.0;
-        bool bad = false;
-        for (long long p = blockIdx.x * (long long)SG_NT + threadIdx.x; p < G->npts;
-             p += (long long)gridDim.x * SG_NT) {
-            const T v = u[p];
-            if (!sg_isfinite(v)) bad = true;
-            mx = fmax(mx, (double)sg_abs(v));
-        }
-        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags + SG_FLAG_NONFINITE, 1);
-        const double m = block_max(mx, red);
-        if (threadIdx.x == 0) atomicMax(alpha + g * 3, dbits(m));
-    }
-}
-
-// Per-instance time-step control, one thread per instance.  commit_only = 0 at the start of
-// a step: adds the previous (pending) step to t, then sets dt for the next step or marks the
-// instance inactive.  commit_only = 1 after the last step: only adds the pending step.
-static __global__ void sg_dt_kernel(InstState* inst, int ninst, const unsigned long long* alpha,
-                             PhysParams ph, int commit_only) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ninst) return;
-    InstState s = inst[i];
-    if (s.pending) {
-        s.t = s.last ? s.t_end : s.t + s.dt;
-        s.steps += 1;
-        s.pending = 0;
-    }
-    s.active = 0;
-    if (!commit_only && s.t < s.t_end && s.steps < s.step_limit) {
-        double dt;
-        if (s.dt_rule == 0) {
-            dt = s.dt_nom;
-        } else {
-            double sum = 0.0;
-            for (int k = 0; k < ph.dim; ++k) {
-                double a = 0.0;
-                if (ph.pde == 1) {
-                    for (int g = s.grid0; g < s.grid0 + s.ngrids; ++g) a = fmax(a, bitsd(alpha[g * 3]));
-                } else {
-                    a = ph.adv[k] < 0.0 ? -ph.adv[k] : ph.adv[k];
-                }
-                sum = sum + a / s.hf[k];
-            }
-            dt = s.cfl / sum;
-        }
-        s.last = 0;
-        if (dt >= s.t_end - s.t) {  // shortened last step: the run ends exactly at t_end
-            dt = s.t_end - s.t;
-            s.last = 1;
-        }
-        s.dt = dt;
-        s.pending = 1;
-        s.active = 1;
-    }
-    inst[i] = s;
-}
-
-// ------------------------------------------------------------------------------------
-// Step 1: restriction of u0 = p0 + p1 sin(p2 sum_k x_k + p3), x_k = lo_k + j_k h_k.
-// ------------------------------------------------------------------------------------
-template <class T>
-__global__ void sg_restrict_sine_kernel(GridDesc G, int dim, double p0, double p1, double p2,
-                                        double p3) {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < G.npts;
-         p += (long long)gridDim.x * blockDim.x) {
-        long long r = p;
-        double S = 0.0;
-        for (int k = 0; k < dim; ++k) {
-            const long long j = r % G.n[k];
-            r /= G.n[k];
-            S = S + (G.lo[k] + (double)j * G.h[k]);
-        }
-        ((T*)G.u0)[p] = (T)(p0 + p1 * sin(p2 * S + p3));
-    }
-}
-
-// ------------------------------------------------------------------------------------
-// Prolongation of one axis (Section 2.2.1): in has shape (below, m_in, above) in the
-// axis-0-fastest sense, out has (below, Nf, above).  Fine node jf on an axis refined by
-// r = 2^{N_L - l}: centre i = floor(jf/r + 1/2), s = jf/r - i in [-1/2, 1/2).
-// If acc != nullptr the result is added, times coeff, into the FP64 accumulator instead
-// (the last prolonged axis, fused with the combination sum of Eq. 13).
-// ------------------------------------------------------------------------------------
-template <class T>
-__device__ __forceinline__ void fine_to_coarse(int jf, int r, int& ic, T& s) {
-    const int i = jf / r, m = jf - i * r;
-    if (2 * m < r) {
-        ic = i;
-        s = (T)m / (T)r;
-    } else {
-        ic = i + 1;
-        s = (T)(m - r) / (T)r;
-    }
-}
-
-template <class T>
-__global__ void sg_prolong_axis_kernel(const T* __restrict__ in, T* __restrict__ out,
-                                       double* __restrict__ acc, double coeff, long long below,
-                                       int min_, int nf, long long above, int r, double eps,
-                                       int lagrange) {
-    const long long tot = below * nf * above;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long lo = idx % below;
-        const long long rest = idx / below;
-        const int jf = (int)(rest % nf);
-        const long long hi = rest / nf;
-        int ic;
-        T s;
-        fine_to_coarse<T>(jf, r, ic, s);
-        const T* line = in + lo + hi * below * min_;
-        T v[5];
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            int c = ic - 2 + m;
-            c %= min_;
-            if (c < 0) c += min_;
-            v[m] = line[(long long)c * below];
-        }
-        T res;
-        if constexpr (sizeof(T) == 8) {
-            res = Weno<double>::interp(v[0], v[1], v[2], v[3], v[4], s, eps, lagrange);
-        } else {
-            res = Weno<float>::interp(v[0], v[1], v[2], v[3], v[4], s, (float)(12.0 * eps), lagrange);
-        }
-        if (acc) acc[idx] = acc[idx] + coeff * (double)res;
-        else out[idx] = res;
-    }
-}
-
-// uhat += coeff * u for a grid that is already the finest grid.
-template <class T>
-__global__ void sg_accumulate_kernel(const T* __restrict__ u, double* __restrict__ acc, double coeff,
-                                     long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        acc[i] = acc[i] + coeff * (double)u[i];
-}
-
-// ------------------------------------------------------------------------------------
-// FP64 reductions, deterministic two-pass (fixed grid, fixed order).
-// kind: 0 sum u, 1 sum u^2, 2 min, 3 max, 4 sum |u - exact|, 5 max |u - exact|
-// ------------------------------------------------------------------------------------
-
-
-__device__ __forceinline__ double sg_exact(const ExactSpec& X, long long p) {
-    double S = 0.0, St = 0.0;
-    long long r = p;
-    for (int k = 0; k < X.dim; ++k) {
-        const long long j = r % X.nf;
-        r /= X.nf;
-        const double x = X.lo[k] + (double)j * X.h[k];
-        S = S + x;
-        St = St + (x - X.adv[k] * X.t);
-    }
-    if (X.pde == 0) return X.b + X.a * sin(X.w * St + X.phi);
-    const double d = (double)X.dim;
-    double u = X.b + X.a * sin(X.w * S + X.phi);
-    for (int it = 0; it < 100; ++it) {
-        const double arg = X.w * (S - d * u * X.t) + X.phi;
-        const double F = u - X.b - X.a * sin(arg);
-        const double dF = 1.0 + X.a * X.w * d * X.t * cos(arg);
-        const double du = F / dF;
-        u = u - du;
-        if (fabs(du) <= 1e-16 * (1.0 + fabs(u))) break;
-    }
-    return u;
-}
-
-template <class T>
-__global__ void __launch_bounds__(256) sg_reduce_pass1(const T* __restrict__ u, long long n, int kind,
-                                                       ExactSpec X, double* partial) {
-    __shared__ double sh[256];
-    double v;
-    const bool is_min = kind == 2, is_max = kind == 3 || kind == 5;
-    v = is_min ? INFINITY : (is_max ? -INFINITY : 0.0);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const double x = (double)u[i];
-        double y;
-        switch (kind) {
-            case 0: y = x; break;
-            case 1: y = x * x; break;
-            case 4:
-            case 5: y = fabs(x - sg_exact(X, i)); break;
-            default: y = x; break;
-        }
-        if (is_min) v = fmin(v, y);
-        else if (is_max) v = fmax(v, y);
-        else v = v + y;
-    }
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            const double o = sh[threadIdx.x + s];
-            double& m = sh[threadIdx.x];
-            m = is_min ? fmin(m, o) : (is_max ? fmax(m, o) : m + o);
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
-}
-
-static __global__ void __launch_bounds__(256) sg_reduce_pass2(const double* partial, int np, int kind, double* out) {
-    __shared__ double sh[256];
-    const bool is_min = kind == 2, is_max = kind == 3 || kind == 5;
-    double v = is_min ? INFINITY : (is_max ? -INFINITY : 0.0);
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        const double y = partial[i];
-        v = is_min ? fmin(v, y) : (is_max ? fmax(v, y) : v + y);
-    }
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            const double o = sh[threadIdx.x + s];
-            double& m = sh[threadIdx.x];
-            m = is_min ? fmin(m, o) : (is_max ? fmax(m, o) : m + o);
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = sh[0];
-}
+#include "sg_weno.cuh"
+#include "sg_stage.cuh"
+#include "sg_aux.cuh"

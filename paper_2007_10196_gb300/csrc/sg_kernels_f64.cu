@@ -1,7 +1,7 @@
 // FP64 instantiation of the kernels.  Compiled with --fmad=false so that every double
 // expression is evaluated as written (no fused multiply-add): the FP64 path then performs
 // the same IEEE-754 operations, in the same order, as a plain sequential evaluation of the
-// paper's formulas.
+// paper's formulas.  Also holds the precision-independent launchers.
 #include "sg_launch_impl.cuh"
 
 namespace sg {
@@ -13,6 +13,18 @@ cudaError_t launch_dt(InstState* inst, int ninst, const unsigned long long* alph
     if (ninst < 1) return cudaSuccess;
     sg_dt_kernel<<<(ninst + 127) / 128, 128, 0, s>>>(inst, ninst, alpha, ph, commit_only);
     return cudaGetLastError();
+}
+
+void box_footprint(int d, const int* te, long long* box, long long* flux) {
+    long long b = 1, p = 1;
+    for (int k = 0; k < d; ++k) {
+        b *= te[k] + 6;
+        p *= te[k];
+    }
+    long long f = 0;
+    for (int k = 0; k < d; ++k) f += p / te[k] * (te[k] + 1);
+    *box = b;
+    *flux = f;
 }
 
 }  // namespace sg

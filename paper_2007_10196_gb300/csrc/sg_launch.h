@@ -8,27 +8,33 @@
 
 namespace sg {
 
+// Shared-memory footprint (elements) of the d <= 3 stage kernel for tile extents te[0..d-1]:
+// two padded boxes (box) and the flux arrays of all axes (flux).
+void box_footprint(int d, const int* te, long long* box, long long* flux);
+
 template <class T>
 struct Launch {
-    // Dynamic shared memory of the stage kernel for `ppt` points per thread.
-    static size_t stage_smem(int ppt);
-    // Resident blocks per SM of the stage kernel (occupancy), 0 if unsupported.
-    static int stage_blocks_per_sm(int dim, int ppt);
+    // Dynamic shared memory (bytes) of the stage kernel: d <= 3 uses the padded-box kernel
+    // (2 box + flux elements), d >= 4 the line-buffer kernel (fixed by ppt).
+    static size_t stage_smem(int dim, int ppt, long long box, long long flux);
+    // Raises the kernel's shared-memory limit and returns resident blocks per SM (0 if the
+    // configuration cannot run).
+    static int stage_prepare(int dim, int ppt, size_t smem);
     // One RK stage over work items [a.item_begin, a.item_end) with `nblocks` blocks.
-    static cudaError_t stage(int dim, int ppt, const StageArgs& a, int nblocks, cudaStream_t s);
+    static cudaError_t stage(int dim, int ppt, const StageArgs& a, int nblocks, size_t smem, cudaStream_t s);
     // alpha slot 0 of every grid <- max |u0| (slots must be zero); flags non-finite values.
     static cudaError_t alpha_init(const GridDesc* grids, int ngrids, long long max_pts,
                                   unsigned long long* alpha, int* flags, cudaStream_t s);
-    // u0 of one grid <- p0 + p1 sin(p2 sum x + p3).
+    // u0 of one grid <- p0 + p1 sin(p2 sum x + p3) (FP32: also the compensation term u3).
     static cudaError_t restrict_sine(const GridDesc& g, int dim, const double* p, cudaStream_t s);
     // One prolongation axis; acc != nullptr fuses "acc += coeff * result".
     static cudaError_t prolong_axis(const T* in, T* out, double* acc, double coeff, long long below,
                                     int min_, int nf, long long above, int r, double eps,
                                     int lagrange, cudaStream_t s);
     static cudaError_t accumulate(const T* u, double* acc, double coeff, long long n, cudaStream_t s);
-    // FP64 reduction of n values (kind as in sg_kernels.cuh); partial holds >= 1024 doubles.
-    static cudaError_t reduce(const T* u, long long n, int kind, const ExactSpec& X, double* partial,
-                              double* out, cudaStream_t s);
+    // FP64 reduction of n values u (+ comp if non-null); partial holds >= 1024 doubles.
+    static cudaError_t reduce(const T* u, const T* comp, long long n, int kind, const ExactSpec& X,
+                              double* partial, double* out, cudaStream_t s);
 };
 
 extern template struct Launch<double>;

@@ -9,41 +9,53 @@ namespace sg {
 namespace detail {
 
 template <class T, int D, int PPT>
-cudaError_t stage_one(const StageArgs& a, int nblocks, cudaStream_t s) {
-    auto kern = sg_stage_kernel<T, D, PPT>;
-    const size_t smem = sizeof(T) * (size_t)(StageSmem<PPT>::LB + StageSmem<PPT>::FB);
-    // the dynamic shared-memory limit was raised by occupancy_one() when the handle was created
-    kern<<<nblocks, SG_NT, smem, s>>>(a);
+struct StageKernel {
+    static constexpr bool box = D <= 3;
+    static void* fn() {
+        if constexpr (D <= 3) return (void*)sg_stage_box_kernel<T, D, PPT>;
+        else return (void*)sg_stage_line_kernel<T, D, PPT>;
+    }
+};
+
+template <class T, int D, int PPT>
+cudaError_t stage_one(const StageArgs& a, int nblocks, size_t smem, cudaStream_t s) {
+    // the dynamic shared-memory limit was raised by stage_prepare() when the handle was created
+    if constexpr (D <= 3) sg_stage_box_kernel<T, D, PPT><<<nblocks, SG_NT, smem, s>>>(a);
+    else sg_stage_line_kernel<T, D, PPT><<<nblocks, SG_NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <class T, int D, int PPT>
-int occupancy_one() {
-    auto kern = sg_stage_kernel<T, D, PPT>;
-    const size_t smem = sizeof(T) * (size_t)(StageSmem<PPT>::LB + StageSmem<PPT>::FB);
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+int prepare_one(size_t smem) {
+    const void* kern = StageKernel<T, D, PPT>::fn();
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
         return 0;
+    }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, SG_NT, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, SG_NT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     return nb;
 }
 
 template <class T, int D>
-cudaError_t stage_d(int ppt, const StageArgs& a, int nblocks, cudaStream_t s) {
+cudaError_t stage_d(int ppt, const StageArgs& a, int nblocks, size_t smem, cudaStream_t s) {
     switch (ppt) {
-        case 1: return stage_one<T, D, 1>(a, nblocks, s);
-        case 2: return stage_one<T, D, 2>(a, nblocks, s);
-        case 4: return stage_one<T, D, 4>(a, nblocks, s);
+        case 1: return stage_one<T, D, 1>(a, nblocks, smem, s);
+        case 2: return stage_one<T, D, 2>(a, nblocks, smem, s);
+        case 4: return stage_one<T, D, 4>(a, nblocks, smem, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <class T, int D>
-int occ_d(int ppt) {
+int prepare_d(int ppt, size_t smem) {
     switch (ppt) {
-        case 1: return occupancy_one<T, D, 1>();
-        case 2: return occupancy_one<T, D, 2>();
-        case 4: return occupancy_one<T, D, 4>();
+        case 1: return prepare_one<T, D, 1>(smem);
+        case 2: return prepare_one<T, D, 2>(smem);
+        case 4: return prepare_one<T, D, 4>(smem);
         default: return 0;
     }
 }
@@ -58,33 +70,34 @@ inline int grid_for(long long n, int threads) {
 }  // namespace detail
 
 template <class T>
-size_t Launch<T>::stage_smem(int ppt) {
-    return sizeof(T) * (size_t)(8 + 3) * SG_NT * (size_t)ppt;
+size_t Launch<T>::stage_smem(int dim, int ppt, long long box, long long flux) {
+    if (dim <= 3) return sizeof(T) * (size_t)(2 * box + flux);
+    return sizeof(T) * (size_t)(LineSmem<1>::LB + LineSmem<1>::FB) * (size_t)ppt;
 }
 
 template <class T>
-int Launch<T>::stage_blocks_per_sm(int dim, int ppt) {
+int Launch<T>::stage_prepare(int dim, int ppt, size_t smem) {
     switch (dim) {
-        case 1: return detail::occ_d<T, 1>(ppt);
-        case 2: return detail::occ_d<T, 2>(ppt);
-        case 3: return detail::occ_d<T, 3>(ppt);
-        case 4: return detail::occ_d<T, 4>(ppt);
-        case 5: return detail::occ_d<T, 5>(ppt);
-        case 6: return detail::occ_d<T, 6>(ppt);
+        case 1: return detail::prepare_d<T, 1>(ppt, smem);
+        case 2: return detail::prepare_d<T, 2>(ppt, smem);
+        case 3: return detail::prepare_d<T, 3>(ppt, smem);
+        case 4: return detail::prepare_d<T, 4>(ppt, smem);
+        case 5: return detail::prepare_d<T, 5>(ppt, smem);
+        case 6: return detail::prepare_d<T, 6>(ppt, smem);
         default: return 0;
     }
 }
 
 template <class T>
-cudaError_t Launch<T>::stage(int dim, int ppt, const StageArgs& a, int nblocks, cudaStream_t s) {
+cudaError_t Launch<T>::stage(int dim, int ppt, const StageArgs& a, int nblocks, size_t smem, cudaStream_t s) {
     if (nblocks < 1) return cudaSuccess;
     switch (dim) {
-        case 1: return detail::stage_d<T, 1>(ppt, a, nblocks, s);
-        case 2: return detail::stage_d<T, 2>(ppt, a, nblocks, s);
-        case 3: return detail::stage_d<T, 3>(ppt, a, nblocks, s);
-        case 4: return detail::stage_d<T, 4>(ppt, a, nblocks, s);
-        case 5: return detail::stage_d<T, 5>(ppt, a, nblocks, s);
-        case 6: return detail::stage_d<T, 6>(ppt, a, nblocks, s);
+        case 1: return detail::stage_d<T, 1>(ppt, a, nblocks, smem, s);
+        case 2: return detail::stage_d<T, 2>(ppt, a, nblocks, smem, s);
+        case 3: return detail::stage_d<T, 3>(ppt, a, nblocks, smem, s);
+        case 4: return detail::stage_d<T, 4>(ppt, a, nblocks, smem, s);
+        case 5: return detail::stage_d<T, 5>(ppt, a, nblocks, smem, s);
+        case 6: return detail::stage_d<T, 6>(ppt, a, nblocks, smem, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -123,12 +136,12 @@ cudaError_t Launch<T>::accumulate(const T* u, double* acc, double coeff, long lo
 }
 
 template <class T>
-cudaError_t Launch<T>::reduce(const T* u, long long n, int kind, const ExactSpec& X, double* partial,
-                              double* out, cudaStream_t s) {
+cudaError_t Launch<T>::reduce(const T* u, const T* comp, long long n, int kind, const ExactSpec& X,
+                              double* partial, double* out, cudaStream_t s) {
     int nb = (int)((n + 255) / 256);
     if (nb > 1024) nb = 1024;
     if (nb < 1) nb = 1;
-    sg_reduce_pass1<T><<<nb, 256, 0, s>>>(u, n, kind, X, partial);
+    sg_reduce_pass1<T><<<nb, 256, 0, s>>>(u, comp, n, kind, X, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     sg_reduce_pass2<<<1, 256, 0, s>>>(partial, nb, kind, out);

@@ -1,0 +1,239 @@
+// sg_weno.cuh -- device arithmetic of the method: the Lax-Friedrichs split (Eq. 7), the
+// one-sided WENO5 reconstruction (Eqs. 3-6) and the WENO5 / Lagrange interpolation
+// (Eqs. 8-11), plus small device helpers.
+//
+// Weno<double> evaluates the paper's formulas literally; the translation unit that
+// instantiates it is compiled with --fmad=false so each expression is a fixed sequence of
+// IEEE-754 operations.  Weno<float> evaluates the same mathematics in first differences with
+// one reciprocal per interface (see the comment above it).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sg_device.h"
+
+#define SG_NT 256  // threads per block of the stage kernels
+
+// Exact unsigned division by a run-time divisor d <= 2^16 for x < 2^16 (multiply-high by
+// ceil(2^32 / d)).  x (d - 1) < 2^32 guarantees floor(x m / 2^32) = floor(x / d).
+struct FDiv {
+    unsigned m, d;
+    __device__ __forceinline__ void init(unsigned dd) {
+        d = dd;
+        m = dd <= 1u ? 0u : (unsigned)((0x100000000ull + dd - 1ull) / (unsigned long long)dd);
+    }
+    __device__ __forceinline__ unsigned div(unsigned x) const { return d <= 1u ? x : __umulhi(x, m); }
+};
+
+__device__ __forceinline__ unsigned long long dbits(double v) {
+    return (unsigned long long)__double_as_longlong(v);
+}
+__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+template <class T>
+__device__ __forceinline__ T sg_abs(T v) { return v < T(0) ? -v : v; }
+
+__device__ __forceinline__ bool sg_isfinite(double v) { return isfinite(v); }
+__device__ __forceinline__ bool sg_isfinite(float v) { return isfinite(v); }
+
+// Block-wide max of non-negative values; the result is valid in thread 0.  Contains two
+// barriers, so every thread of the block must call it.
+__device__ __forceinline__ double block_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    __syncthreads();
+    return v;
+}
+
+template <class T>
+struct Weno;
+
+// ------------------------------------------------------------------------------------
+// FP64: Eqs. (3)-(7) and (8)-(11) evaluated literally; compile without contraction.
+// ------------------------------------------------------------------------------------
+template <>
+struct Weno<double> {
+    // fhat_{i+1/2} from (a..e) = (f_{i-2}, ..., f_{i+2}) (positive wind), Eqs. (3)-(6).
+    static __device__ __forceinline__ double side(double a, double b, double c, double d, double e,
+                                                  double eps, int linear) {
+        const double q0 = (1.0 / 3.0) * a - (7.0 / 6.0) * b + (11.0 / 6.0) * c;
+        const double q1 = -(1.0 / 6.0) * b + (5.0 / 6.0) * c + (1.0 / 3.0) * d;
+        const double q2 = (1.0 / 3.0) * c + (5.0 / 6.0) * d - (1.0 / 6.0) * e;
+        double w0 = 0.1, w1 = 0.6, w2 = 0.3;
+        if (!linear) {
+            const double r0 = a - 2.0 * b + c, g0 = a - 4.0 * b + 3.0 * c;
+            const double r1 = b - 2.0 * c + d, g1 = b - d;
+            const double r2 = c - 2.0 * d + e, g2 = 3.0 * c - 4.0 * d + e;
+            const double b0 = (13.0 / 12.0) * (r0 * r0) + 0.25 * (g0 * g0);
+            const double b1 = (13.0 / 12.0) * (r1 * r1) + 0.25 * (g1 * g1);
+            const double b2 = (13.0 / 12.0) * (r2 * r2) + 0.25 * (g2 * g2);
+            w0 = 0.1 / ((eps + b0) * (eps + b0));
+            w1 = 0.6 / ((eps + b1) * (eps + b1));
+            w2 = 0.3 / ((eps + b2) * (eps + b2));
+        }
+        return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+    }
+
+    // Lax-Friedrichs split of one value, Eq. (7): f^{+-} = (f +- alpha u)/2.
+    static __device__ __forceinline__ void split(double u, double alpha, double ak, int pde, double& fp,
+                                                 double& fm) {
+        const double f = pde == 1 ? (0.5 * u) * u : ak * u;
+        fp = 0.5 * (f + alpha * u);
+        fm = 0.5 * (f - alpha * u);
+    }
+
+    // fhat = fhat^+ + fhat^- at x_{L+1/2} from split values at L-2 .. L+3 (stride S):
+    // fhat^+ on (L-2..L+2), fhat^- on the mirror image (L+3..L-1).
+    static __device__ __forceinline__ double interface_split(const double* p, const double* m, int S,
+                                                             const PhysParams& ph) {
+        const double fplus = side(p[0], p[S], p[2 * S], p[3 * S], p[4 * S], ph.eps, ph.scheme);
+        const double fminus = side(m[5 * S], m[4 * S], m[3 * S], m[2 * S], m[S], ph.eps, ph.scheme);
+        return fplus + fminus;
+    }
+
+    // Same from raw values u_{L-2} .. u_{L+3} (stride S).
+    static __device__ __forceinline__ double interface(const double* v, int S, double alpha, double ak,
+                                                       const PhysParams& ph) {
+        double fp[6], fm[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) split(v[j * S], alpha, ak, ph.pde, fp[j], fm[j]);
+        const double fplus = side(fp[0], fp[1], fp[2], fp[3], fp[4], ph.eps, ph.scheme);
+        const double fminus = side(fm[5], fm[4], fm[3], fm[2], fm[1], ph.eps, ph.scheme);
+        return fplus + fminus;
+    }
+
+    // WENO5 / Lagrange interpolation at x_i + s h, Eqs. (8)-(11), literal order.
+    static __device__ __forceinline__ double interp(double a, double b, double c, double d, double e,
+                                                    double s, double eps, int lagrange) {
+        if (s == 0.0) return c;
+        const double g0 = 0.5 * (a - 4.0 * b + 3.0 * c), k0 = 0.5 * (a - 2.0 * b + c);
+        const double g1 = 0.5 * (d - b), k1 = 0.5 * (b - 2.0 * c + d);
+        const double g2 = 0.5 * (-3.0 * c + 4.0 * d - e), k2 = 0.5 * (c - 2.0 * d + e);
+        const double P0 = c + s * (g0 + s * k0);
+        const double P1 = c + s * (g1 + s * k1);
+        const double P2 = c + s * (g2 + s * k2);
+        const double C0 = ((s - 1.0) * (s - 2.0)) / 12.0;
+        const double C1 = (4.0 - s * s) / 6.0;
+        const double C2 = ((s + 1.0) * (s + 2.0)) / 12.0;
+        if (lagrange) return C0 * P0 + C1 * P1 + C2 * P2;
+        const double r0 = a - 2.0 * b + c, g0s = a - 4.0 * b + 3.0 * c;
+        const double r1 = b - 2.0 * c + d, g1s = b - d;
+        const double r2 = c - 2.0 * d + e, g2s = 3.0 * c - 4.0 * d + e;
+        const double b0 = (13.0 / 12.0) * (r0 * r0) + 0.25 * (g0s * g0s);
+        const double b1 = (13.0 / 12.0) * (r1 * r1) + 0.25 * (g1s * g1s);
+        const double b2 = (13.0 / 12.0) * (r2 * r2) + 0.25 * (g2s * g2s);
+        const double w0 = C0 / ((eps + b0) * (eps + b0));
+        const double w1 = C1 / ((eps + b1) * (eps + b1));
+        const double w2 = C2 / ((eps + b2) * (eps + b2));
+        return (w0 * P0 + w1 * P1 + w2 * P2) / (w0 + w1 + w2);
+    }
+};
+
+// ------------------------------------------------------------------------------------
+// FP32: the same mathematics in first differences d_j = f_j - f_{j-1}:
+//   q_r - f_i = (5/6 d2 - 1/3 d1, 1/6 d2 + 1/3 d3, 2/3 d3 - 1/6 d4)
+//   12 (eps + beta_r) = 13 t_r^2 + 3 s_r^2 + 12 eps, t = second differences,
+//   s = (3 d2 - d1, d2 + d3, 3 d3 - d4)
+//   alpha_r / alpha_1 = (d_r / d_1) prod_{j != r} E_j / prod_{j != 1} E_j, E_r = (12(eps+beta_r))^2
+// so one side needs no division and the two sides of an interface share one reciprocal.
+// (The products stay in float range for |f| differences below ~1e4 when eps >= 1e-8.)
+// ------------------------------------------------------------------------------------
+template <>
+struct Weno<float> {
+    static __device__ __forceinline__ void side(float a, float b, float c, float d, float e,
+                                                float eps12, int linear, float& num, float& den) {
+        const float d1 = b - a, d2 = c - b, d3 = d - c, d4 = e - d;
+        const float p0 = fmaf(5.f / 6.f, d2, (-1.f / 3.f) * d1);
+        const float p1 = fmaf(1.f / 6.f, d2, (1.f / 3.f) * d3);
+        const float p2 = fmaf(2.f / 3.f, d3, (-1.f / 6.f) * d4);
+        float a0, a1, a2;
+        if (linear) {
+            a0 = 0.1f;
+            a1 = 0.6f;
+            a2 = 0.3f;
+        } else {
+            const float t0 = d2 - d1, t1 = d3 - d2, t2 = d4 - d3;
+            const float s0 = fmaf(3.f, d2, -d1), s1 = d2 + d3, s2 = fmaf(3.f, d3, -d4);
+            const float e0 = fmaf(13.f * t0, t0, fmaf(3.f * s0, s0, eps12));
+            const float e1 = fmaf(13.f * t1, t1, fmaf(3.f * s1, s1, eps12));
+            const float e2 = fmaf(13.f * t2, t2, fmaf(3.f * s2, s2, eps12));
+            const float E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
+            a0 = (1.f / 6.f) * (E1 * E2);
+            a1 = E0 * E2;
+            a2 = 0.5f * (E0 * E1);
+        }
+        num = fmaf(a0, p0, fmaf(a1, p1, a2 * p2));
+        den = a0 + a1 + a2;
+    }
+
+    // Burgers split, Eq. (7): f^{+-} = u (u/4 +- alpha/2).
+    static __device__ __forceinline__ void split_burgers(float u, float half_alpha, float& fp, float& fm) {
+        fp = u * fmaf(0.25f, u, half_alpha);
+        fm = u * fmaf(0.25f, u, -half_alpha);
+    }
+
+    static __device__ __forceinline__ float combine(float cp, float cm, float np, float dp, float nm, float dm) {
+        return (cp + cm) + __fdividef(fmaf(np, dm, nm * dp), dp * dm);
+    }
+
+    static __device__ __forceinline__ float interface_split(const float* p, const float* m, int S, float eps12,
+                                                            int linear) {
+        float np, dp, nm, dm;
+        side(p[0], p[S], p[2 * S], p[3 * S], p[4 * S], eps12, linear, np, dp);
+        side(m[5 * S], m[4 * S], m[3 * S], m[2 * S], m[S], eps12, linear, nm, dm);
+        return combine(p[2 * S], m[3 * S], np, dp, nm, dm);
+    }
+
+    // raw values u_{L-2} .. u_{L+3} (stride S)
+    static __device__ __forceinline__ float interface(const float* v, int S, float alpha, float ak,
+                                                      const PhysParams& ph, float eps12) {
+        float fp[6], fm[6];
+        if (ph.pde == 1) {
+            const float ha = 0.5f * alpha;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) split_burgers(v[j * S], ha, fp[j], fm[j]);
+        } else {
+            const float cp = 0.5f * (ak + alpha), cm = 0.5f * (ak - alpha);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                fp[j] = cp * v[j * S];
+                fm[j] = cm * v[j * S];
+            }
+        }
+        float np, dp, nm, dm;
+        side(fp[0], fp[1], fp[2], fp[3], fp[4], eps12, ph.scheme, np, dp);
+        side(fm[5], fm[4], fm[3], fm[2], fm[1], eps12, ph.scheme, nm, dm);
+        return combine(fp[2], fm[3], np, dp, nm, dm);
+    }
+
+    static __device__ __forceinline__ float interp(float a, float b, float c, float d, float e,
+                                                   float s, float eps12, int lagrange) {
+        if (s == 0.f) return c;
+        const float d1 = b - a, d2 = c - b, d3 = d - c, d4 = e - d;
+        const float t0 = d2 - d1, t1 = d3 - d2, t2 = d4 - d3;
+        const float s0 = fmaf(3.f, d2, -d1), s1 = d2 + d3, s2 = fmaf(3.f, d3, -d4);
+        // P_k(s) - c = (s/2) (s_k + s t_k)
+        const float p0 = fmaf(s, t0, s0), p1 = fmaf(s, t1, s1), p2 = fmaf(s, t2, s2);
+        const float C0 = (s - 1.f) * (s - 2.f) * (1.f / 12.f);
+        const float C1 = fmaf(-s, s, 4.f) * (1.f / 6.f);
+        const float C2 = (s + 1.f) * (s + 2.f) * (1.f / 12.f);
+        float w0 = C0, w1 = C1, w2 = C2;
+        if (!lagrange) {
+            const float e0 = fmaf(13.f * t0, t0, fmaf(3.f * s0, s0, eps12));
+            const float e1 = fmaf(13.f * t1, t1, fmaf(3.f * s1, s1, eps12));
+            const float e2 = fmaf(13.f * t2, t2, fmaf(3.f * s2, s2, eps12));
+            const float E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
+            w0 = C0 * (E1 * E2);
+            w1 = C1 * (E0 * E2);
+            w2 = C2 * (E0 * E1);
+        }
+        const float num = fmaf(w0, p0, fmaf(w1, p1, w2 * p2));
+        return fmaf(0.5f * s, __fdividef(num, w0 + w1 + w2), c);
+    }
+};
