@@ -406,7 +406,7 @@ def test_fp32_mass_conserved_by_float_pair(sg):
         P.sg_init(h, P.SG_IC_SINE, (0.5, 0.9, math.pi / 2, 0.0))
         G = P.sg_num_grids(h)
         m0 = [P.sg_reduce(h, g, P.SG_REDUCE_MASS) for g in range(G)]
-        P.sg_step(h, 0.25)
+        P.sg_step(h, 0.5)  # about 32 steps, through the shock (t_s = 0.24)
         steps = P.sg_time(h)[1]
         m1 = [P.sg_reduce(h, g, P.SG_REDUCE_MASS) for g in range(G)]
     finally:
@@ -416,3 +416,34 @@ def test_fp32_mass_conserved_by_float_pair(sg):
         # the flux differences telescope; each step adds at most one float rounding of the
         # increment per point to the pair
         assert abs(a - b) <= 1e-6 * 64.0, (a, b)
+
+
+def test_shocked_member_fp64_bitwise(sg, orc):
+    """A benchmark-batch member past its shock time (3-D Burgers, N_r = 8, N_L = 3, a = 1,
+    t = 0.3, CFL 0.4): the FP64 path equals the oracle bit for bit through the shock and the
+    combination, including the combined solution's overshoot of the initial bounds — the
+    overshoot is the combination technique at this root resolution, not the implementation."""
+    nr, nl, a = 8, 3, 1.0
+    ic = (0.5, a, math.pi / 2, 0.0)
+    p = orc.problem(3, nr, nl, pde=1, eps=1e-3)
+    lev, co = orc.grid_set(3, nl)
+    g0 = [sine_grid(nr, l, 0.0, 4.0, ic) for l in lev]
+    ref, osteps, ot = orc.solve(p, lev, g0, 0.3, rule=1, cfl=0.4)
+    refhat = orc.combine(p, lev, co, ref)
+    h = make(3, nr, nl, P.SG_PDE_BURGERS, exec=P.SG_BATCHED, dt_rule=P.SG_DT_CFL)
+    try:
+        P.sg_init_grids(h, np.concatenate(g0))
+        P.sg_step(h, 0.3)
+        t, steps = P.sg_time(h)
+        got = read_grids(h, [len(g) for g in g0])
+        P.sg_prolong_combine(h)
+        uhat = P.sg_read(h, -1, count=refhat.size)
+        lo, hi = P.sg_reduce(h, -1, P.SG_REDUCE_MIN), P.sg_reduce(h, -1, P.SG_REDUCE_MAX)
+    finally:
+        P.sg_destroy(h)
+    assert steps == osteps and t == ot == 0.3
+    assert all(np.array_equal(g, r) for g, r in zip(got, ref))
+    assert np.array_equal(uhat, refhat)
+    assert lo == refhat.min() and hi == refhat.max()
+    assert max(g.max() for g in ref) <= 0.5 + a and min(g.min() for g in ref) >= 0.5 - a  # grids stay bounded
+    assert lo < 0.5 - a - 0.1  # the combination overshoots
