@@ -197,6 +197,36 @@ enum { SG_PROF_STAGE = 0 };
 sg_status sg_set_profiling(sg_handle h, int on);
 sg_status sg_profile(sg_handle h, int kind, double *ms, long *launches);
 
+/* One RK3 step of one grid without any device allocation.  The paper has no counterpart:
+ * this is a library convenience.  It serves callers that cannot call cudaMalloc -- code
+ * running inside a framework that owns all of the device memory, or a loop with real-time
+ * constraints where an allocation (and the synchronisation that cudaMalloc/cudaFree can
+ * bring) is not allowed.  The caller passes the grid in and gets the stepped grid back; all
+ * scratch (the two intermediate RK stages, the grid descriptor, the work queue, the
+ * Lax-Friedrichs alpha slots and the flags) lives in one static device array of the library,
+ * sized for SG_NOALLOC_MAX_POINTS points (about 16.5 MB), which every GPU that loads the
+ * library holds until the process exits.
+ *
+ * It advances one periodic FP64 grid by one TVD-RK3 step of the WENO5 / Lax-Friedrichs
+ * scheme with the same stage kernel and tiles as sg_step, so the result equals that of a
+ * level-0 handle stepped with the same dt, bit for bit.
+ *   dim: 1..3 (SG_ERR_UNSUPPORTED otherwise); shape[k] >= 5 and prod shape[k] <=
+ *   SG_NOALLOC_MAX_POINTS (SG_ERR_ARG otherwise, with a message in sg_last_error);
+ *   lo, hi: the domain (node spacing (hi_k - lo_k)/shape[k]); pde, scheme, eps as in
+ *   sg_create / sg_params; adv_speed: a_k for advection (NULL = all 1);
+ *   u_in, u_out: device pointers to prod shape[k] doubles, axis 0 fastest (they may be the
+ *   same pointer); dt: the step; cuda_stream: the cudaStream_t to run on (NULL = default).
+ * The call is asynchronous on that stream and calls no cudaMalloc, cudaFree or allocating
+ * library routine.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  Every call uses the same scratch array and leaves its last contents there: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race and corrupt each
+ * other's result.  Non-finite values are not reported (sg_step reports them). */
+#define SG_NOALLOC_MAX_POINTS 1048576
+sg_status sg_step_grid_noalloc(int dim, const long *shape, const double *lo, const double *hi, int pde,
+                               const double *adv_speed, int scheme, double eps, const double *u_in,
+                               double *u_out, double dt, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,8 +37,9 @@ EXPORTED = [
     "sg_params_init", "sg_create", "sg_init", "sg_init_grid", "sg_init_grids", "sg_step",
     "sg_prolong_combine", "sg_read", "sg_reduce", "sg_num_grids", "sg_grid_info", "sg_time",
     "sg_batch_create", "sg_destroy", "sg_last_error", "sg_set_allocator", "sg_launch_count",
-    "sg_set_profiling", "sg_profile",
+    "sg_set_profiling", "sg_profile", "sg_step_grid_noalloc",
 ]
+SG_NOALLOC_MAX_POINTS = 1048576
 SG_PROF_STAGE = 0
 
 
@@ -99,6 +100,9 @@ def lib():
         "sg_last_error": (C.c_char_p, []),
         "sg_set_allocator": (st, [ALLOC_FN, FREE_FN, C.c_void_p]),
         "sg_launch_count": (st, [H, C.POINTER(C.c_long)]),
+        "sg_step_grid_noalloc": (st, [C.c_int, C.POINTER(C.c_long), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double), C.c_int,
+                                      C.c_double, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
         "sg_set_profiling": (st, [H, C.c_int]),
         "sg_profile": (st, [H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
     }
@@ -238,6 +242,19 @@ def sg_launch_count(h) -> int:
     n = C.c_long()
     _check(lib().sg_launch_count(h, C.byref(n)))
     return n.value
+
+
+def sg_step_grid_noalloc(shape, lo, hi, pde, u_in_ptr: int, u_out_ptr: int, dt: float,
+                         adv_speed=None, scheme: int = SG_WENO5, eps: float = 1e-3, stream: int = 0):
+    """One RK3 step of one periodic FP64 grid in caller device memory (pointers as ints, e.g.
+    a CUDA tensor's data_ptr()) without any device allocation; see include/sgweno.h."""
+    dim = len(shape)
+    shp = (C.c_long * dim)(*[int(x) for x in shape])
+    lo_ = (C.c_double * dim)(*np.broadcast_to(np.asarray(lo, float), (dim,)))
+    hi_ = (C.c_double * dim)(*np.broadcast_to(np.asarray(hi, float), (dim,)))
+    adv = None if adv_speed is None else (C.c_double * dim)(*[float(a) for a in adv_speed])
+    _check(lib().sg_step_grid_noalloc(dim, shp, lo_, hi_, pde, adv, scheme, float(eps), C.c_void_p(u_in_ptr),
+                                      C.c_void_p(u_out_ptr), float(dt), C.c_void_p(stream)))
 
 
 def sg_set_profiling(h, on: bool = True):

@@ -1,10 +1,11 @@
 """Builds libsgweno.so (the CUDA library behind include/sgweno.h) in-tree for sm_103a.
 
-Three translation units are compiled in parallel with nvcc and linked into
+Four translation units are compiled in parallel with nvcc and linked into
 paper_2007_10196_gb300/libsgweno.so:
   sg_kernels_f64.cu  -- FP64 kernels, --fmad=false (no contraction: literal evaluation order)
   sg_kernels_f32.cu  -- FP32 kernels
   sg_api.cu          -- the C ABI
+  sg_noalloc.cu      -- sg_step_grid_noalloc and its static scratch, --fmad=false
 """
 from __future__ import annotations
 
@@ -24,6 +25,7 @@ UNITS = {
     "sg_kernels_f64.cu": ["--fmad=false"],
     "sg_kernels_f32.cu": [],
     "sg_api.cu": [],
+    "sg_noalloc.cu": ["--fmad=false"],
 }
 
 

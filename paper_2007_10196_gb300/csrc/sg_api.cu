@@ -1004,6 +1004,12 @@ sg_status sg_destroy(sg_handle h) {
 
 const char* sg_last_error(void) { return g_err.c_str(); }
 
+}  // extern "C"
+
+void sg::set_last_error(const char* msg) { g_err = msg; }
+
+extern "C" {
+
 sg_status sg_set_allocator(sg_alloc_fn alloc, sg_free_fn release, void* ctx) {
     if ((alloc == nullptr) != (release == nullptr)) return fail(SG_ERR_ARG, "alloc and release must both be set or both NULL");
     if (g_live_handles != 0) return fail(SG_ERR_STATE, "cannot change the allocator while handles exist");

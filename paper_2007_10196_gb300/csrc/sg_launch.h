@@ -43,4 +43,7 @@ extern template struct Launch<float>;
 cudaError_t launch_dt(InstState* inst, int ninst, const unsigned long long* alpha,
                       const PhysParams& ph, int commit_only, cudaStream_t s);
 
+// Sets the calling thread's message returned by sg_last_error (defined in sg_api.cu).
+void set_last_error(const char* msg);
+
 }  // namespace sg
