@@ -183,6 +183,21 @@ def _stage_traffic(points_per_launch):
         return None
 
 
+def aggregate(local_ms, local_updates, dist=None, device="cpu"):
+    """Whole-job figures over ranks: (max elapsed ms over ranks, sum of point-updates).  The
+    members of every rank are independent problems, so nothing but these two scalars is
+    exchanged (weak scaling)."""
+    if dist is None:
+        return float(local_ms), float(local_updates)
+    import torch
+    t = torch.tensor([float(local_ms), float(local_updates)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 # ------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------
@@ -225,10 +240,8 @@ def run_ours(args, rank, world, local_rank):
         ev_step0.record(stream)
         P.sg_step(batch, inputs.BATCH_T_END)
         ev_step1.record(stream)
-        ext = []
-        for h in hs:
-            P.sg_prolong_combine(h)
-            ext.append((P.sg_reduce(h, -1, P.SG_REDUCE_MIN), P.sg_reduce(h, -1, P.SG_REDUCE_MAX)))
+        P.sg_prolong_combine(batch)  # every member, sharing the batch's intermediates
+        ext = [(P.sg_reduce(h, -1, P.SG_REDUCE_MIN), P.sg_reduce(h, -1, P.SG_REDUCE_MAX)) for h in hs]
         if host_out is not None:
             for h, buf in zip(hs, host_out):
                 P.sg_read(h, P.SG_WHICH_ALL_GRIDS, out=buf)
@@ -300,16 +313,7 @@ def run_ours(args, rank, world, local_rank):
                    "api": "sg_init_grids (pinned host) + sg_step + sg_prolong_combine + sg_reduce + sg_read"}
 
     mean_ms = statistics.mean(times)
-    local = {"upd": upd_per_pass * args.steps, "ms": sum(times)}
-    if dist is not None:
-        t = torch.tensor([local["ms"], local["upd"]], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        total_ms, total_upd = float(mx[0]), float(sm[1])
-    else:
-        total_ms, total_upd = local["ms"], float(local["upd"])
+    total_ms, total_upd = aggregate(sum(times), upd_per_pass * args.steps, dist, "cuda")
 
     for h in [batch] + hs:
         P.sg_destroy(h)

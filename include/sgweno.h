@@ -67,6 +67,16 @@ enum { SG_PROLONG_WENO5 = 0, SG_PROLONG_LAGRANGE5 = 1 };
  *              max |f_k'(u)| at the start of the step.
  * Either way the last step is shortened so that the run ends exactly at t_end. */
 enum { SG_DT_POW53 = 0, SG_DT_CFL = 1 };
+/* Stage kernel (an implementation choice; every choice computes the same values, bit for bit
+ * in FP64):
+ * SG_STAGE_AUTO:  tile_points = 0 lets the autotuner pick the kernel and the tile at the
+ *                 first sg_step (see sg_stage_config); tile_points > 0 selects SG_STAGE_TILED
+ *                 with that tile;
+ * SG_STAGE_TILED: the tiled kernel of the dimension (d <= 3 padded box, d >= 4 line buffer),
+ *                 tiles of tile_points points (0 = 512);
+ * SG_STAGE_SWEEP: d = 3 only -- one thread per grid line of an 8 x 8 x 8 tile, sweeping it
+ *                 with a register window; tile_points is ignored. */
+enum { SG_STAGE_AUTO = 0, SG_STAGE_TILED = 1, SG_STAGE_SWEEP = 2 };
 /* Initial condition kinds for sg_init. SG_IC_SINE: u_0(x) = p0 + p1 sin(p2 (x_0+...+x_{d-1}) + p3). */
 enum { SG_IC_SINE = 0 };
 /* Reductions (FP64).  MASS = sum u prod h, ENERGY = sum u^2 prod h, MIN/MAX of the values;
@@ -101,7 +111,11 @@ typedef struct {
     double cfl;                  /* default 0.4 */
     void *cuda_stream;           /* cudaStream_t to run on; NULL = a stream the handle owns */
     int graph_steps;             /* time steps per captured CUDA graph; 0 = default (16), <0 = no graph */
-    int tile_points;             /* points per work-queue tile; 0 = autotune */
+    int tile_points;             /* points per work-queue tile: 0 (default), 256, 512 or 1024 */
+    double combine_budget_gb;    /* device memory (GB) the one-pass prolongation + combination may
+                                    use for intermediates; above it (or if < 0) uhat is accumulated
+                                    grid by grid instead.  0 = default (8 GB) */
+    int stage_kernel;            /* SG_STAGE_AUTO (default), SG_STAGE_TILED or SG_STAGE_SWEEP */
 } sg_params;
 
 /* Fills *p with the defaults listed above.  SG_ERR_ARG if p is NULL. */
@@ -196,6 +210,19 @@ sg_status sg_launch_count(sg_handle h, long *n_launches);
 enum { SG_PROF_STAGE = 0 };
 sg_status sg_set_profiling(sg_handle h, int on);
 sg_status sg_profile(sg_handle h, int kind, double *ms, long *launches);
+
+/* The stage-kernel configuration the handle (or batch) steps with: *kernel receives
+ * SG_STAGE_TILED or SG_STAGE_SWEEP, *tile_points the largest tile in points, *tune_ms the
+ * measured time of one RK-stage launch of the chosen configuration when the autotuner picked
+ * it (0 otherwise).  Under SG_STAGE_AUTO with tile_points = 0 the autotuner runs at the first
+ * sg_step: it times one stage-0 launch with dt = 0 (which leaves the solution untouched) of
+ * each candidate -- the tiled kernel with 256-, 512- and 1024-point tiles and, for d = 3, the
+ * sweep kernel -- keeps the fastest and remembers it, for the life of the process, per
+ * dimension, precision, PDE, scheme, execution mode and size class (total points rounded up
+ * to a power of two).  Before that first step the query reports the starting configuration.
+ * A batch puts all of its members on one configuration (the first member's at creation, the
+ * tuned one after its first sg_step); any output pointer may be NULL. */
+sg_status sg_stage_config(sg_handle h, int *kernel, int *tile_points, double *tune_ms);
 
 /* One RK3 step of one grid without any device allocation.  The paper has no counterpart:
  * this is a library convenience.  It serves callers that cannot call cudaMalloc -- code

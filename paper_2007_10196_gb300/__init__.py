@@ -28,6 +28,7 @@ SG_PLAIN, SG_BATCHED = 0, 1
 SG_WENO5, SG_LINEAR5 = 0, 1
 SG_PROLONG_WENO5, SG_PROLONG_LAGRANGE5 = 0, 1
 SG_DT_POW53, SG_DT_CFL = 0, 1
+SG_STAGE_AUTO, SG_STAGE_TILED, SG_STAGE_SWEEP = 0, 1, 2
 SG_IC_SINE = 0
 SG_REDUCE_MASS, SG_REDUCE_ENERGY, SG_REDUCE_MIN, SG_REDUCE_MAX = 0, 1, 2, 3
 SG_REDUCE_L1_EXACT, SG_REDUCE_LINF_EXACT = 4, 5
@@ -37,7 +38,7 @@ EXPORTED = [
     "sg_params_init", "sg_create", "sg_init", "sg_init_grid", "sg_init_grids", "sg_step",
     "sg_prolong_combine", "sg_read", "sg_reduce", "sg_num_grids", "sg_grid_info", "sg_time",
     "sg_batch_create", "sg_destroy", "sg_last_error", "sg_set_allocator", "sg_launch_count",
-    "sg_set_profiling", "sg_profile", "sg_step_grid_noalloc",
+    "sg_set_profiling", "sg_profile", "sg_step_grid_noalloc", "sg_stage_config",
 ]
 SG_NOALLOC_MAX_POINTS = 1048576
 SG_PROF_STAGE = 0
@@ -57,6 +58,7 @@ class sg_params(C.Structure):
         ("precision", C.c_int), ("exec", C.c_int), ("scheme", C.c_int), ("prolong", C.c_int),
         ("eps", C.c_double), ("dt_rule", C.c_int), ("dt_coef", C.c_double), ("cfl", C.c_double),
         ("cuda_stream", C.c_void_p), ("graph_steps", C.c_int), ("tile_points", C.c_int),
+        ("combine_budget_gb", C.c_double), ("stage_kernel", C.c_int),
     ]
 
 
@@ -105,6 +107,7 @@ def lib():
                                       C.c_double, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
         "sg_set_profiling": (st, [H, C.c_int]),
         "sg_profile": (st, [H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
+        "sg_stage_config": (st, [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -266,6 +269,13 @@ def sg_profile(h, kind: int = SG_PROF_STAGE):
     ms, n = C.c_double(), C.c_long()
     _check(lib().sg_profile(h, kind, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def sg_stage_config(h):
+    """(kernel, tile_points, tune_ms): the stage-kernel configuration the handle steps with."""
+    k, tp, ms = C.c_int(), C.c_int(), C.c_double()
+    _check(lib().sg_stage_config(h, C.byref(k), C.byref(tp), C.byref(ms)))
+    return k.value, tp.value, ms.value
 
 
 _alloc_refs = None

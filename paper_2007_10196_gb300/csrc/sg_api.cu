@@ -9,6 +9,9 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "sg_device.h"
@@ -83,6 +86,11 @@ struct DevBuf {
     T* as() const { return static_cast<T*>(p); }
 };
 
+// Intermediates of the fused prolongation + combination.
+struct CombineBuffers {
+    DevBuf pool, pa, pb, tab;
+};
+
 struct PinnedInst {
     InstState* p = nullptr;
     int n = 0;
@@ -131,7 +139,10 @@ struct sg_ctx {
     int dim = 0, nr = 0, nl = 0, pde = 0;
     sg_params prm{};
     int esize = 8;
-    int ppt = 2;
+    int ppt = 2;       // points per thread of the stage kernel (tile = 256 ppt points)
+    int variant = 0;   // stage kernel: 0 = default of the dimension, 1 = padded box (d = 3)
+    bool tuned = false;
+    double tune_ms = 0.0;  // time of one stage launch of the chosen configuration
     // grids (single handle)
     int G = 0;
     std::vector<std::array<int, SG_MAXD>> levels;
@@ -172,6 +183,7 @@ struct sg_ctx {
     long long launches = 0;
     // combination
     DevBuf uhat, pro_a, pro_b;
+    CombineBuffers comb;  // fused form's intermediates (a batch's are shared by its members)
     long long fine_pts = 0;
     // batch
     std::vector<sg_ctx*> members;
@@ -193,6 +205,7 @@ PhysParams phys_of(const sg_ctx* h) {
     ph.prolong = h->prm.prolong;
     ph.eps = h->prm.eps;
     for (int k = 0; k < SG_MAXD; ++k) ph.adv[k] = k < h->dim ? h->prm.adv_speed[k] : 0.0;
+    ph.alpha_f32 = h->esize == 4;
     return ph;
 }
 
@@ -210,6 +223,7 @@ double dt_pow53(const sg_ctx* h) {
 void fill_inst(const sg_ctx* h, InstState& s, int grid0, double t_end, long long max_steps) {
     s.t = h->t;
     s.dt = 0.0;
+    s.dtf = 0.0f;
     s.t_end = t_end;
     s.dt_nom = dt_pow53(h);
     s.cfl = h->prm.cfl;
@@ -254,7 +268,8 @@ void stage_footprint(sg_ctx* h) {
     long long box = 1, flux = 1;
     for (const GridDesc& d : h->hgrids) {
         long long b, f;
-        sg::box_footprint(h->dim, d.te, &b, &f);
+        if (h->dim == 3 && h->variant == 0) sg::sweep_footprint(d.te, &b, &f);
+        else sg::box_footprint(h->dim, d.te, &b, &f);
         box = std::max(box, b);
         flux = std::max(flux, f);
     }
@@ -264,13 +279,13 @@ void stage_footprint(sg_ctx* h) {
 }
 
 int stage_blocks_per_sm(const sg_ctx* h) {
-    return h->esize == 8 ? sg::Launch<double>::stage_prepare(h->dim, h->ppt, h->smem)
-                         : sg::Launch<float>::stage_prepare(h->dim, h->ppt, h->smem);
+    return h->esize == 8 ? sg::Launch<double>::stage_prepare(h->dim, h->ppt, h->smem, h->variant)
+                         : sg::Launch<float>::stage_prepare(h->dim, h->ppt, h->smem, h->variant);
 }
 
 cudaError_t launch_stage(const sg_ctx* h, const StageArgs& a, int nblocks) {
-    return h->esize == 8 ? sg::Launch<double>::stage(h->dim, h->ppt, a, nblocks, h->smem, h->stream)
-                         : sg::Launch<float>::stage(h->dim, h->ppt, a, nblocks, h->smem, h->stream);
+    return h->esize == 8 ? sg::Launch<double>::stage(h->dim, h->ppt, a, nblocks, h->smem, h->stream, h->variant)
+                         : sg::Launch<float>::stage(h->dim, h->ppt, a, nblocks, h->smem, h->stream, h->variant);
 }
 
 // FP32 state: after a call in which instance i took an odd number of steps, U sits in the
@@ -298,6 +313,10 @@ sg_status validate_params(const sg_params* p, int dim) {
     if (!(p->dt_coef > 0.0) || !(p->cfl > 0.0)) return fail(SG_ERR_ARG, "dt_coef and cfl must be > 0");
     if (p->tile_points != 0 && p->tile_points != 256 && p->tile_points != 512 && p->tile_points != 1024)
         return fail(SG_ERR_ARG, "tile_points must be 0, 256, 512 or 1024");
+    if (p->stage_kernel != SG_STAGE_AUTO && p->stage_kernel != SG_STAGE_TILED && p->stage_kernel != SG_STAGE_SWEEP)
+        return fail(SG_ERR_ARG, "stage_kernel");
+    if (p->stage_kernel == SG_STAGE_SWEEP && dim != 3)
+        return fail(SG_ERR_UNSUPPORTED, "the sweep stage kernel is implemented for d = 3 only");
     return SG_OK;
 }
 
@@ -306,18 +325,24 @@ sg_status build_tables(sg_ctx* h) {
     const int pmax = 256 * h->ppt;
     char* base = h->arena.as<char>();
     const size_t region = (size_t)h->total_pts * h->esize;
+    // a rebuild (reconfiguration) keeps the state buffers where they are: an FP32 handle's
+    // ping-pong pair may be swapped
+    std::vector<std::pair<void*, void*>> keep;
+    if ((int)h->hgrids.size() == h->G)
+        for (const GridDesc& d : h->hgrids) keep.emplace_back(d.u0, d.u1);
     h->hgrids.assign(h->G, GridDesc{});
     h->hitems.clear();
     for (int g = 0; g < h->G; ++g) {
         GridDesc& d = h->hgrids[g];
-        d.u0 = base + (size_t)h->offset[g] * h->esize;
-        d.u1 = base + region + (size_t)h->offset[g] * h->esize;
+        d.u0 = keep.empty() ? base + (size_t)h->offset[g] * h->esize : keep[g].first;
+        d.u1 = keep.empty() ? base + region + (size_t)h->offset[g] * h->esize : keep[g].second;
         d.u2 = base + 2 * region + (size_t)h->offset[g] * h->esize;
         d.u3 = h->esize == 4 ? base + 3 * region + (size_t)h->offset[g] * h->esize : nullptr;
         d.npts = h->npts[g];
         int n[SG_MAXD] = {1, 1, 1, 1, 1, 1};
         for (int k = 0; k < h->dim; ++k) n[k] = h->nr << h->levels[g][k];
-        choose_tile(n, h->dim, pmax, d.te);
+        if (h->dim == 3 && h->variant == 0) sg::sweep_tile(n, d.te);
+        else choose_tile(n, h->dim, pmax, d.te);
         int ntiles = 1;
         for (int k = 0; k < SG_MAXD; ++k) {
             if (k < h->dim) {
@@ -325,6 +350,7 @@ sg_status build_tables(sg_ctx* h) {
                 d.nt[k] = (n[k] + d.te[k] - 1) / d.te[k];
                 d.h[k] = (h->prm.hi[k] - h->prm.lo[k]) / (double)n[k];
                 d.rdx[k] = 1.0 / d.h[k];
+                d.rdxf[k] = (float)d.rdx[k];
                 d.lo[k] = h->prm.lo[k];
                 d.lev[k] = h->levels[g][k];
                 ntiles *= d.nt[k];
@@ -334,6 +360,7 @@ sg_status build_tables(sg_ctx* h) {
                 d.nt[k] = 1;
                 d.h[k] = 1.0;
                 d.rdx[k] = 1.0;
+                d.rdxf[k] = 1.0f;
                 d.lo[k] = 0.0;
                 d.lev[k] = 0;
             }
@@ -467,6 +494,177 @@ sg_status ensure_graph(sg_ctx* h, int nsteps) {
     return SG_OK;
 }
 
+// A batch's grid table and work queue: its members' tables concatenated, grid g of member i
+// owned by instance i.  Uploaded to the device.
+sg_status build_batch_tables(sg_ctx* h) {
+    h->hgrids.clear();
+    h->hitems.clear();
+    h->max_grid_pts = 0;
+    for (size_t i = 0; i < h->members.size(); ++i) {
+        const sg_ctx* m = h->members[i];
+        for (const GridDesc& d0 : m->hgrids) {
+            GridDesc d = d0;
+            d.inst = (int)i;
+            d.first_item = (int)h->hitems.size();
+            const int g = (int)h->hgrids.size();
+            for (int t = 0; t < d.n_items; ++t) h->hitems.push_back(WorkItem{g, t});
+            h->hgrids.push_back(d);
+        }
+        h->max_grid_pts = std::max(h->max_grid_pts, m->max_grid_pts);
+    }
+    if (h->dgrids.bytes < sizeof(GridDesc) * h->hgrids.size()) SG_TRY(h->dgrids.alloc(sizeof(GridDesc) * h->hgrids.size()));
+    if (h->ditems.bytes < sizeof(WorkItem) * h->hitems.size()) SG_TRY(h->ditems.alloc(sizeof(WorkItem) * h->hitems.size()));
+    SG_CUDA(cudaMemcpy(h->dgrids.p, h->hgrids.data(), sizeof(GridDesc) * h->hgrids.size(), cudaMemcpyHostToDevice));
+    SG_CUDA(cudaMemcpy(h->ditems.p, h->hitems.data(), sizeof(WorkItem) * h->hitems.size(), cudaMemcpyHostToDevice));
+    return SG_OK;
+}
+
+void drop_graph(sg_ctx* h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_nsteps = 0;
+}
+
+// Stage-kernel configuration: kernel variant and points per thread (tile size); rebuilds the
+// tiles and work queues (of every member, for a batch) and drops the captured graph.
+sg_status configure(sg_ctx* h, int variant, int ppt) {
+    if (h->is_batch) {
+        for (sg_ctx* m : h->members) {
+            m->variant = variant;
+            m->ppt = ppt;
+            SG_TRY(build_tables(m));
+            stage_footprint(m);
+            m->tuned = true;
+            drop_graph(m);
+        }
+        SG_TRY(build_batch_tables(h));
+    }
+    h->variant = variant;
+    h->ppt = ppt;
+    if (!h->is_batch) SG_TRY(build_tables(h));
+    if (h->is_batch) {
+        for (sg_ctx* m : h->members) {  // members keep a runnable configuration of their own
+            const int b = stage_blocks_per_sm(m);
+            if (b < 1) return fail(SG_ERR_CUDA, "stage kernel cannot be resident");
+            m->blocks_total = b * num_sms();
+        }
+    }
+    stage_footprint(h);
+    const int bps = stage_blocks_per_sm(h);
+    if (bps < 1) return fail(SG_ERR_CUDA, "stage kernel cannot be resident (dim %d, variant %d, %d points/thread)",
+                             h->dim, variant, ppt);
+    h->blocks_total = bps * num_sms();
+    drop_graph(h);
+    return SG_OK;
+}
+
+// Autotuner (SG_STAGE_AUTO with tile_points = 0): the first sg_step of a handle or batch
+// times one RK-stage launch of each candidate configuration (stage 0 with dt = 0: it writes
+// only the first-stage buffer and an alpha slot, both of which the step itself rewrites) and
+// keeps the fastest.  Candidates: the tiled kernel with 256-, 512- and 1024-point tiles, and
+// for d = 3 the sweep kernel in place of the 256-point tile.  Choices are cached per
+// (dimension, precision, pde, scheme, batch or not, size class) for the life of the process.
+struct TuneKey {
+    int dim, esize, pde, scheme, batched, size_class;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(dim, esize, pde, scheme, batched, size_class) <
+               std::tie(o.dim, o.esize, o.pde, o.scheme, o.batched, o.size_class);
+    }
+};
+std::map<TuneKey, std::tuple<int, int, double>> g_tuned;  // variant, ppt, ms
+std::mutex g_tune_mutex;
+
+sg_status time_stage0(sg_ctx* h, double* ms) {
+    for (int i = 0; i < h->ninst; ++i) {
+        InstState& s = h->hinst.p[i];
+        s.active = 1;
+        s.dt = 0.0;
+        s.dtf = 0.0f;
+        s.steps = s.step0 = 0;
+    }
+    SG_CUDA(cudaMemcpyAsync(h->dinst.p, h->hinst.p, sizeof(InstState) * h->ninst, cudaMemcpyHostToDevice, h->stream));
+    SG_CUDA(cudaMemsetAsync(h->alpha.p, 0, h->alpha.bytes, h->stream));
+    cudaEvent_t e0, e1;
+    SG_CUDA(cudaEventCreate(&e0));
+    SG_CUDA(cudaEventCreate(&e1));
+    StageArgs a{};
+    a.grids = h->dgrids.as<GridDesc>();
+    a.items = h->ditems.as<WorkItem>();
+    a.inst = h->dinst.as<InstState>();
+    a.alpha = h->alpha.as<unsigned long long>();
+    a.flags = h->flags.as<int>();
+    a.stage = 0;
+    a.phys = phys_of(h);
+    a.box_elems = (int)h->box_elems;
+    const bool batched = h->is_batch || h->prm.exec == SG_BATCHED;
+    cudaError_t err = cudaSuccess;
+    for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {  // one warm-up, three timed
+        if (rep == 1) err = cudaEventRecord(e0, h->stream);
+        if (batched) {
+            a.item_begin = 0;
+            a.item_end = (int)h->hitems.size();
+            if (err == cudaSuccess) err = launch_stage(h, a, std::min<int>(a.item_end, h->blocks_total));
+        } else {
+            for (const GridDesc& d : h->hgrids) {
+                a.item_begin = d.first_item;
+                a.item_end = d.first_item + d.n_items;
+                if (err == cudaSuccess) err = launch_stage(h, a, std::min<int>(d.n_items, h->blocks_total));
+            }
+        }
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SG_CUDA(err);
+    SG_CUDA(cudaMemsetAsync(h->flags.p, 0, h->flags.bytes, h->stream));
+    *ms = t / 3.0;
+    return SG_OK;
+}
+
+sg_status autotune(sg_ctx* h) {
+    if (h->tuned) return SG_OK;
+    long long pts = 0;
+    for (const GridDesc& d : h->hgrids) pts += d.npts;
+    int size_class = 0;
+    while ((1LL << size_class) < pts) ++size_class;
+    const TuneKey key{h->dim, h->esize, h->pde, h->prm.scheme, (int)(h->is_batch || h->prm.exec == SG_BATCHED),
+                      size_class};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto f = g_tuned.find(key);
+        if (f != g_tuned.end()) {
+            SG_TRY(configure(h, std::get<0>(f->second), std::get<1>(f->second)));
+            h->tuned = true;
+            h->tune_ms = std::get<2>(f->second);
+            return SG_OK;
+        }
+    }
+    std::vector<std::pair<int, int>> cand;
+    if (h->dim == 3) cand = {{0, 2}, {1, 2}, {1, 4}};
+    else cand = {{0, 1}, {0, 2}, {0, 4}};
+    double best = INFINITY;
+    std::pair<int, int> pick = cand[0];
+    for (const auto& c : cand) {
+        sg_status st = configure(h, c.first, c.second);
+        if (st != SG_OK) continue;  // a candidate that cannot run is skipped
+        double ms = INFINITY;
+        if (time_stage0(h, &ms) != SG_OK) continue;
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    SG_TRY(configure(h, pick.first, pick.second));
+    h->tuned = true;
+    h->tune_ms = std::isfinite(best) ? best : 0.0;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[key] = std::make_tuple(pick.first, pick.second, h->tune_ms);
+    return SG_OK;
+}
+
 // Would the next dt-control pass mark this instance inactive?  Mirrors sg_dt_kernel.
 bool finished(const InstState& s) {
     if (!s.active) return true;
@@ -515,9 +713,11 @@ sg_status run_steps(sg_ctx* h) {
     return SG_OK;
 }
 
-// Prolongation of every grid onto the finest grid and the combination sum (single handle).
+// Prolongation of every grid onto the finest grid and the combination sum, one grid at a time:
+// the last prolonged axis of each grid adds c_g times its values into uhat (a read-modify-write
+// of uhat per grid).  Used when the fused form's intermediates exceed the memory budget.
 template <class T>
-sg_status prolong_combine_t(sg_ctx* h) {
+sg_status prolong_combine_rmw_t(sg_ctx* h) {
     const int d = h->dim;
     const long long Nf = (long long)h->nr << h->nl;
     // intermediate buffers: largest array produced by a non-final prolonged axis
@@ -578,6 +778,92 @@ sg_status prolong_combine_t(sg_ctx* h) {
     return SG_OK;
 }
 
+// Fused form (Step 3): phase 1 prolongs every grid over axes 0..d-2 into a pool slot (the
+// grid itself if none of those axes is coarse); phase 2 prolongs the last axis of all grids
+// and forms sum_g c_g P U_g in one pass that writes uhat once.  Buffers come from `cb` (the
+// handle's own, or a batch's, shared by its members).  Returns SG_ERR_UNSUPPORTED (without
+// touching anything) when the pool would exceed the budget.
+template <class T>
+sg_status prolong_combine_fused_t(sg_ctx* h, CombineBuffers& cb) {
+    const int d = h->dim;
+    const long long Nf = (long long)h->nr << h->nl;
+    long long below = 1;
+    for (int k = 0; k + 1 < d; ++k) below *= Nf;
+    // sizes: pool slots and the ping-pong buffers of phase 1
+    long long pool = 0, need = 1;
+    std::vector<long long> slot(h->G, -1);
+    for (int g = 0; g < h->G; ++g) {
+        const GridDesc& gd = h->hgrids[g];
+        long long m[SG_MAXD];
+        std::vector<int> axes;
+        for (int k = 0; k < d; ++k) {
+            m[k] = gd.n[k];
+            if (k + 1 < d && gd.lev[k] < h->nl) axes.push_back(k);
+        }
+        if (axes.empty()) continue;
+        slot[g] = pool;
+        pool += below * m[d - 1];
+        for (size_t a = 0; a + 1 < axes.size(); ++a) {
+            m[axes[a]] = Nf;
+            long long tot = 1;
+            for (int k = 0; k < d; ++k) tot *= m[k];
+            need = std::max(need, tot);
+        }
+    }
+    // bytes of intermediates the fused form may hold
+    const double budget = h->prm.combine_budget_gb == 0.0 ? 8.0e9 : h->prm.combine_budget_gb * 1e9;
+    if (budget < 0.0 || (double)(pool + 2 * need) * sizeof(T) > budget) return SG_ERR_UNSUPPORTED;
+    if (!h->uhat.p) SG_TRY(h->uhat.alloc(sizeof(double) * (size_t)h->fine_pts));
+    if (cb.pool.bytes < sizeof(T) * (size_t)std::max(pool, 1LL)) SG_TRY(cb.pool.alloc(sizeof(T) * (size_t)std::max(pool, 1LL)));
+    if (cb.pa.bytes < sizeof(T) * (size_t)need) {
+        SG_TRY(cb.pa.alloc(sizeof(T) * (size_t)need));
+        SG_TRY(cb.pb.alloc(sizeof(T) * (size_t)need));
+    }
+    if (cb.tab.bytes < sizeof(CombineGrid) * (size_t)h->G) SG_TRY(cb.tab.alloc(sizeof(CombineGrid) * (size_t)h->G));
+    std::vector<CombineGrid> tab(h->G);
+    T* bufs[2] = {cb.pa.as<T>(), cb.pb.as<T>()};
+    for (int g = 0; g < h->G; ++g) {
+        const GridDesc& gd = h->hgrids[g];
+        long long m[SG_MAXD];
+        std::vector<int> axes;
+        for (int k = 0; k < d; ++k) {
+            m[k] = gd.n[k];
+            if (k + 1 < d && gd.lev[k] < h->nl) axes.push_back(k);
+        }
+        const T* src = (const T*)gd.u0;
+        for (size_t a = 0; a < axes.size(); ++a) {
+            const int k = axes[a];
+            long long lo = 1, hi = 1;
+            for (int j = 0; j < k; ++j) lo *= m[j];
+            for (int j = k + 1; j < d; ++j) hi *= m[j];
+            T* dst = a + 1 == axes.size() ? cb.pool.as<T>() + slot[g] : bufs[a & 1];
+            SG_CUDA(sg::Launch<T>::prolong_axis2(src, dst, lo, (int)m[k], (int)Nf, hi, 1 << (h->nl - gd.lev[k]),
+                                                 h->prm.eps, h->prm.prolong, h->stream));
+            h->launches += 1;
+            m[k] = Nf;
+            src = dst;
+        }
+        tab[g].src = src;
+        tab[g].n = gd.n[d - 1];
+        tab[g].r = 1 << (h->nl - gd.lev[d - 1]);
+        tab[g].coeff = gd.coeff;
+    }
+    SG_CUDA(cudaMemcpyAsync(cb.tab.p, tab.data(), sizeof(CombineGrid) * tab.size(), cudaMemcpyHostToDevice, h->stream));
+    SG_CUDA(sg::Launch<T>::combine_last_axis(cb.tab.as<CombineGrid>(), h->G, h->uhat.as<double>(), below, (int)Nf,
+                                             h->prm.eps, h->prm.prolong, h->stream));
+    h->launches += 1;
+    SG_CUDA(cudaStreamSynchronize(h->stream));
+    h->combined = true;
+    return SG_OK;
+}
+
+template <class T>
+sg_status prolong_combine_t(sg_ctx* h, CombineBuffers& cb) {
+    const sg_status st = prolong_combine_fused_t<T>(h, cb);
+    if (st != SG_ERR_UNSUPPORTED) return st;
+    return prolong_combine_rmw_t<T>(h);
+}
+
 sg_status check_handle(sg_handle h) {
     if (!h) return fail(SG_ERR_ARG, "NULL handle");
     return SG_OK;
@@ -608,6 +894,8 @@ sg_status sg_params_init(sg_params* p) {
     p->cuda_stream = nullptr;
     p->graph_steps = 0;
     p->tile_points = 0;
+    p->combine_budget_gb = 0.0;
+    p->stage_kernel = SG_STAGE_AUTO;
     return SG_OK;
 }
 
@@ -632,6 +920,10 @@ sg_status sg_create(int dim, int root_cells, int level, int pde, const sg_params
         h->prm = prm;
         h->esize = prm.precision == SG_F64 ? 8 : 4;
         h->ppt = prm.tile_points ? prm.tile_points / 256 : 2;
+        // d = 3: variant 0 is the sweep kernel, 1 the padded box; other dimensions have one
+        const bool autotuned = prm.stage_kernel == SG_STAGE_AUTO && prm.tile_points == 0;
+        h->variant = dim == 3 && (autotuned || prm.stage_kernel == SG_STAGE_SWEEP) ? 0 : (dim == 3 ? 1 : 0);
+        h->tuned = !autotuned;
         // grid set: |l| = N_L - q, q = 0..d-1, coefficient (-1)^q C(d-1, q)
         for (int q = 0; q < dim && level - q >= 0; ++q) {
             std::vector<std::array<int, SG_MAXD>> ls;
@@ -745,6 +1037,7 @@ sg_status sg_step(sg_handle h, double t_end, long max_steps, double* t_reached) 
     try {
         if (!h->is_batch) {
             if (!h->initialized) return fail(SG_ERR_STATE, "sg_step before sg_init");
+            SG_TRY(autotune(h));
             fill_inst(h, h->hinst.p[0], 0, t_end, max_steps);
             sg_status st = run_steps(h);
             const InstState& s = h->hinst.p[0];
@@ -758,11 +1051,14 @@ sg_status sg_step(sg_handle h, double t_end, long max_steps, double* t_reached) 
             if (t_reached) *t_reached = h->t;
             return st;
         }
+        for (size_t i = 0; i < h->members.size(); ++i) {
+            if (!h->members[i]->initialized) return fail(SG_ERR_STATE, "batch member %zu not initialised", i);
+            SG_CUDA(cudaStreamSynchronize(h->members[i]->stream));
+        }
+        SG_TRY(autotune(h));
         int gbase = 0;
         for (size_t i = 0; i < h->members.size(); ++i) {
             sg_ctx* m = h->members[i];
-            if (!m->initialized) return fail(SG_ERR_STATE, "batch member %zu not initialised", i);
-            SG_CUDA(cudaStreamSynchronize(m->stream));
             fill_inst(m, h->hinst.p[i], gbase, t_end, max_steps);
             for (int g = 0; g < m->G; ++g) {  // members may have been stepped on their own
                 h->hgrids[gbase + g].u0 = m->hgrids[g].u0;
@@ -800,12 +1096,15 @@ sg_status sg_step(sg_handle h, double t_end, long max_steps, double* t_reached) 
 sg_status sg_prolong_combine(sg_handle h) {
     SG_TRY(check_handle(h));
     try {
-        if (h->is_batch) {
-            for (sg_ctx* m : h->members) SG_TRY(sg_prolong_combine(m));
+        if (h->is_batch) {  // members one after another, sharing the batch's intermediates
+            for (sg_ctx* m : h->members) {
+                if (!m->initialized) return fail(SG_ERR_STATE, "sg_prolong_combine before sg_init");
+                SG_TRY(m->esize == 8 ? prolong_combine_t<double>(m, h->comb) : prolong_combine_t<float>(m, h->comb));
+            }
             return SG_OK;
         }
         if (!h->initialized) return fail(SG_ERR_STATE, "sg_prolong_combine before sg_init");
-        return h->esize == 8 ? prolong_combine_t<double>(h) : prolong_combine_t<float>(h);
+        return h->esize == 8 ? prolong_combine_t<double>(h, h->comb) : prolong_combine_t<float>(h, h->comb);
     } catch (const std::bad_alloc&) {
         return fail(SG_ERR_NOMEM, "host allocation failed");
     }
@@ -925,8 +1224,9 @@ sg_status sg_batch_create(const sg_handle* hs, int n, sg_handle* out) {
         const sg_ctx* a = hs[0];
         const sg_ctx* b = hs[i];
         if (b->dim != a->dim || b->pde != a->pde || b->esize != a->esize || b->prm.scheme != a->prm.scheme ||
-            b->prm.eps != a->prm.eps || b->ppt != a->ppt)
-            return fail(SG_ERR_ARG, "member %d differs in dim, pde, precision, scheme, eps or tile size", i);
+            b->prm.eps != a->prm.eps || b->prm.tile_points != a->prm.tile_points ||
+            b->prm.stage_kernel != a->prm.stage_kernel)
+            return fail(SG_ERR_ARG, "member %d differs in dim, pde, precision, scheme, eps or stage kernel", i);
         for (int k = 0; k < a->dim; ++k)
             if (b->prm.adv_speed[k] != a->prm.adv_speed[k]) return fail(SG_ERR_ARG, "member %d differs in adv_speed", i);
     }
@@ -939,23 +1239,10 @@ sg_status sg_batch_create(const sg_handle* hs, int n, sg_handle* out) {
         h->prm.cuda_stream = nullptr;
         h->esize = hs[0]->esize;
         h->ppt = hs[0]->ppt;
+        h->variant = hs[0]->variant;
         h->nr = hs[0]->nr;
         h->nl = hs[0]->nl;
-        for (int i = 0; i < n; ++i) {
-            sg_ctx* m = hs[i];
-            h->members.push_back(m);
-            const int gbase = (int)h->hgrids.size();
-            for (const GridDesc& d0 : m->hgrids) {
-                GridDesc d = d0;
-                d.inst = i;
-                d.first_item = (int)h->hitems.size();
-                const int g = (int)h->hgrids.size();
-                for (int t = 0; t < d.n_items; ++t) h->hitems.push_back(WorkItem{g, t});
-                h->hgrids.push_back(d);
-            }
-            (void)gbase;
-            h->max_grid_pts = std::max(h->max_grid_pts, m->max_grid_pts);
-        }
+        for (int i = 0; i < n; ++i) h->members.push_back(hs[i]);
         // members that all run on one caller-provided stream: the batch uses it too, so that
         // the caller's stream orders every operation; otherwise the batch owns a stream
         bool shared = !hs[0]->own_stream;
@@ -972,16 +1259,12 @@ sg_status sg_batch_create(const sg_handle* hs, int n, sg_handle* out) {
             }
             h->own_stream = true;
         }
-        sg_status st = h->dgrids.alloc(sizeof(GridDesc) * h->hgrids.size());
-        if (st == SG_OK) st = h->ditems.alloc(sizeof(WorkItem) * h->hitems.size());
+        // every member on the first member's configuration, so one kernel fits every tile
+        sg_status st = build_batch_tables(h);
         if (st == SG_OK) st = alloc_step_buffers(h, (int)h->hgrids.size(), n);
-        if (st == SG_OK) {
-            if (cudaMemcpy(h->dgrids.p, h->hgrids.data(), sizeof(GridDesc) * h->hgrids.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-                cudaMemcpy(h->ditems.p, h->hitems.data(), sizeof(WorkItem) * h->hitems.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-                cudaGetLastError();
-                st = fail(SG_ERR_CUDA, "uploading the batch tables failed");
-            }
-        }
+        if (st == SG_OK) st = configure(h, h->variant, h->ppt);
+        // a batch of autotuned members tunes itself (the batched launch is another workload)
+        if (st == SG_OK) h->tuned = !(h->prm.stage_kernel == SG_STAGE_AUTO && h->prm.tile_points == 0);
         if (st != SG_OK) {
             delete h;
             return st;
@@ -1003,6 +1286,15 @@ sg_status sg_destroy(sg_handle h) {
 }
 
 const char* sg_last_error(void) { return g_err.c_str(); }
+
+sg_status sg_stage_config(sg_handle h, int* kernel, int* tile_points, double* tune_ms) {
+    SG_TRY(check_handle(h));
+    const bool sweep = h->dim == 3 && h->variant == 0;
+    if (kernel) *kernel = sweep ? SG_STAGE_SWEEP : SG_STAGE_TILED;
+    if (tile_points) *tile_points = sweep ? 512 : 256 * h->ppt;
+    if (tune_ms) *tune_ms = h->tune_ms;
+    return SG_OK;
+}
 
 }  // extern "C"
 

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(SG_NT) sg_alpha_init_kernel(const GridDesc* gr
         }
         if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags + SG_FLAG_NONFINITE, 1);
         const double m = block_max(mx, red);
-        if (threadIdx.x == 0) atomicMax(alpha + g * 3, dbits(m));
+        if (threadIdx.x == 0) atomicMax(alpha + g * 3, alpha_enc((T)m));  // m is a T value
     }
 }
 
@@ -50,7 +50,8 @@ static __global__ void sg_dt_kernel(InstState* inst, int ninst, const unsigned l
             for (int k = 0; k < ph.dim; ++k) {
                 double a = 0.0;
                 if (ph.pde == 1) {
-                    for (int g = s.grid0; g < s.grid0 + s.ngrids; ++g) a = fmax(a, bitsd(alpha[g * 3]));
+                    for (int g = s.grid0; g < s.grid0 + s.ngrids; ++g)
+                        a = fmax(a, ph.alpha_f32 ? (double)alpha_dec<float>(alpha[g * 3]) : bitsd(alpha[g * 3]));
                 } else {
                     a = ph.adv[k] < 0.0 ? -ph.adv[k] : ph.adv[k];
                 }
@@ -64,6 +65,7 @@ static __global__ void sg_dt_kernel(InstState* inst, int ninst, const unsigned l
             s.last = 1;
         }
         s.dt = dt;
+        s.dtf = (float)dt;
         s.pending = 1;
         s.active = 1;
     }
@@ -142,6 +144,249 @@ __global__ void sg_prolong_axis_kernel(const T* __restrict__ in, T* __restrict__
         }
         if (acc) acc[idx] = acc[idx] + coeff * (double)res;
         else out[idx] = res;
+    }
+}
+
+// One prolongation axis with 2-D indexing (no 64-bit division): rows of `below` contiguous
+// values.  below == 1 (axis 0): threads run along the fine axis, blockIdx.y over `above`;
+// otherwise threads run along `below`, blockIdx.y over the (fine index, above) rows.
+// Same arithmetic per output as sg_prolong_axis_kernel.
+template <class T>
+__global__ void sg_prolong_axis2_kernel(const T* __restrict__ in, T* __restrict__ out, long long below, int min_,
+                                        int nf, long long above, int r, double eps, int lagrange) {
+    const T e12 = (T)(12.0 * eps);
+    if (below == 1) {
+        for (long long hi = blockIdx.y; hi < above; hi += gridDim.y) {
+            const T* line = in + hi * min_;
+            for (int jf = blockIdx.x * blockDim.x + threadIdx.x; jf < nf; jf += gridDim.x * blockDim.x) {
+                int ic;
+                T s;
+                fine_to_coarse<T>(jf, r, ic, s);
+                T v[5];
+#pragma unroll
+                for (int m = 0; m < 5; ++m) {
+                    int c = ic - 2 + m;
+                    c %= min_;
+                    if (c < 0) c += min_;
+                    v[m] = line[c];
+                }
+                T res;
+                if constexpr (sizeof(T) == 8) res = Weno<double>::interp(v[0], v[1], v[2], v[3], v[4], s, eps, lagrange);
+                else res = Weno<float>::interp(v[0], v[1], v[2], v[3], v[4], s, (float)e12, lagrange);
+                out[hi * nf + jf] = res;
+            }
+        }
+        return;
+    }
+    const long long rows = (long long)nf * above;
+    for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int jf = (int)(row % nf);
+        const long long hi = row / nf;
+        int ic;
+        T s;
+        fine_to_coarse<T>(jf, r, ic, s);
+        int cs[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            int c = ic - 2 + m;
+            c %= min_;
+            if (c < 0) c += min_;
+            cs[m] = c;
+        }
+        const T* base = in + hi * below * min_;
+        T* obase = out + (hi * nf + jf) * below;
+        for (long long lo = blockIdx.x * (long long)blockDim.x + threadIdx.x; lo < below;
+             lo += (long long)gridDim.x * blockDim.x) {
+            T res;
+            if (s == T(0)) {
+                res = base[lo + (long long)cs[2] * below];
+            } else {
+                T v[5];
+#pragma unroll
+                for (int m = 0; m < 5; ++m) v[m] = base[lo + (long long)cs[m] * below];
+                if constexpr (sizeof(T) == 8) res = Weno<double>::interp(v[0], v[1], v[2], v[3], v[4], s, eps, lagrange);
+                else res = Weno<float>::interp(v[0], v[1], v[2], v[3], v[4], s, (float)e12, lagrange);
+            }
+            obase[lo] = res;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Step 3, last axis fused with the combination: uhat = sum_g c_g P_{d-1} I_g, where I_g is
+// grid g prolonged over axes 0..d-2 (shape (below, n_g) with below = N_f^{d-1}).  Each thread
+// owns one fine position `lo` in axes 0..d-2 and a chunk of J consecutive fine indices of the
+// last axis; it loops over the grids in enumeration order with a 5-value window sliding along
+// the grid's coarse last axis, and writes uhat once.
+//   T = double: acc = acc + c_g v in FP64, grids in enumeration order -- the same operations
+//     as accumulating each grid's prolongation into uhat in turn.
+//   T = float:  the sum is kept as an unevaluated float pair (error-free sums and products),
+//     whose accuracy exceeds FP64's for these sums; GB300's FP64 rate is a small fraction of
+//     its FP32 rate.
+// ------------------------------------------------------------------------------------
+template <class T>
+struct CombineAcc;
+
+template <>
+struct CombineAcc<double> {
+    double a = 0.0;
+    __device__ __forceinline__ void add(double c, double v) { a = a + c * v; }
+    __device__ __forceinline__ double value() const { return a; }
+};
+
+template <>
+struct CombineAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float cf, float v) {  // cf: |c| <= C(5, 2), exact in float
+        const float p = cf * v;
+        const float pe = fmaf(cf, v, -p);    // exact product error
+        const float s = hi + p;              // two-sum of hi and p
+        const float bb = s - hi;
+        float e = (hi - (s - bb)) + (p - bb);
+        e += lo + pe;
+        hi = s + e;                          // renormalise
+        lo = e - (hi - s);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Interpolation window of one coarse line: the five values around the current coarse centre.
+//   double: Eqs. (8)-(11) evaluated literally per output (Weno<double>::interp).
+//   float:  the quantities that depend only on the five values (differences, the products of
+//     the smoothness terms) are formed once per centre; each output then needs the linear
+//     weights C_k(s), the three parabolas and one division.
+template <class T>
+struct InterpWin;
+
+template <>
+struct InterpWin<double> {
+    double w0, w1, w2, w3, w4;
+    __device__ __forceinline__ void prepare(double, int) {}
+    __device__ __forceinline__ double eval(double s, double eps, int lagrange) const {
+        return Weno<double>::interp(w0, w1, w2, w3, w4, s, eps, lagrange);
+    }
+};
+
+template <>
+struct InterpWin<float> {
+    float w0, w1, w2, w3, w4;
+    float t0, t1, t2, s0, s1, s2, EE0, EE1, EE2;
+    __device__ __forceinline__ void prepare(float eps12, int lagrange) {
+        const float d1 = w1 - w0, d2 = w2 - w1, d3 = w3 - w2, d4 = w4 - w3;
+        t0 = d2 - d1;
+        t1 = d3 - d2;
+        t2 = d4 - d3;
+        s0 = fmaf(3.f, d2, -d1);
+        s1 = d2 + d3;
+        s2 = fmaf(3.f, d3, -d4);
+        if (lagrange) {
+            EE0 = EE1 = EE2 = 1.f;
+        } else {
+            const float e0 = fmaf(13.f * t0, t0, fmaf(3.f * s0, s0, eps12));
+            const float e1 = fmaf(13.f * t1, t1, fmaf(3.f * s1, s1, eps12));
+            const float e2 = fmaf(13.f * t2, t2, fmaf(3.f * s2, s2, eps12));
+            const float E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
+            EE0 = E1 * E2;
+            EE1 = E0 * E2;
+            EE2 = E0 * E1;
+        }
+    }
+    __device__ __forceinline__ float eval(float s, float, int) const {
+        if (s == 0.f) return w2;
+        const float p0 = fmaf(s, t0, s0), p1 = fmaf(s, t1, s1), p2 = fmaf(s, t2, s2);
+        const float C0 = (s - 1.f) * (s - 2.f) * (1.f / 12.f);
+        const float C1 = fmaf(-s, s, 4.f) * (1.f / 6.f);
+        const float C2 = (s + 1.f) * (s + 2.f) * (1.f / 12.f);
+        const float a0 = C0 * EE0, a1 = C1 * EE1, a2 = C2 * EE2;
+        const float num = fmaf(a0, p0, fmaf(a1, p1, a2 * p2));
+        return fmaf(0.5f * s, __fdividef(num, a0 + a1 + a2), w2);
+    }
+};
+
+template <class T, int J>
+__global__ void __launch_bounds__(256) sg_combine_last_axis_kernel(const CombineGrid* __restrict__ tab, int G,
+                                                                    double* __restrict__ uhat, long long below,
+                                                                    int nf, double eps, int lagrange) {
+    const T e12 = (T)(12.0 * eps);
+    const int nchunks = (nf + J - 1) / J;
+    for (int ch = blockIdx.y; ch < nchunks; ch += gridDim.y) {
+        const int j0 = ch * J;
+        for (long long lo = blockIdx.x * (long long)blockDim.x + threadIdx.x; lo < below;
+             lo += (long long)gridDim.x * blockDim.x) {
+            CombineAcc<T> acc[J];
+            for (int g = 0; g < G; ++g) {
+                const CombineGrid cg = tab[g];
+                const T* col = (const T*)cg.src + lo;
+                const int n = cg.n, r = cg.r;
+                const T cT = (T)cg.coeff;  // converted once per grid
+                if (r == 1) {  // last axis already fine: values at coincident nodes
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const int jf = j0 + j;
+                        if (jf < nf) acc[j].add(cT, col[(long long)jf * below]);
+                    }
+                    continue;
+                }
+                // r = 2^lr: fine node jf = i r + m; centre i (2m < r) or i + 1, s = m/r or (m - r)/r
+                const int lr = __ffs(r) - 1;
+                const T inv_r = (T)1 / (T)r;  // exact: r is a power of two
+                auto centre = [&](int jf, int& ic, T& s) {
+                    const int i = jf >> lr, m = jf & (r - 1);
+                    if (2 * m < r) {
+                        ic = i;
+                        s = (T)m * inv_r;
+                    } else {
+                        ic = i + 1;
+                        s = (T)(m - r) * inv_r;
+                    }
+                };
+                int cur;
+                T s_unused;
+                centre(j0, cur, s_unused);
+                InterpWin<T> W;
+                {
+                    int c0 = cur - 2;
+                    c0 %= n;
+                    if (c0 < 0) c0 += n;
+                    int c = c0;
+                    W.w0 = col[(long long)c * below];
+                    if (++c == n) c = 0;
+                    W.w1 = col[(long long)c * below];
+                    if (++c == n) c = 0;
+                    W.w2 = col[(long long)c * below];
+                    if (++c == n) c = 0;
+                    W.w3 = col[(long long)c * below];
+                    if (++c == n) c = 0;
+                    W.w4 = col[(long long)c * below];
+                }
+                W.prepare(e12, lagrange);
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const int jf = j0 + j;
+                    if (jf >= nf) break;
+                    int ic;
+                    T s;
+                    centre(jf, ic, s);
+                    if (ic != cur) {  // centres advance by one coarse node at a time (r >= 2)
+                        W.w0 = W.w1;
+                        W.w1 = W.w2;
+                        W.w2 = W.w3;
+                        W.w3 = W.w4;
+                        int c = ic + 2;
+                        if (c >= n) c -= n;
+                        W.w4 = col[(long long)c * below];
+                        W.prepare(e12, lagrange);
+                        cur = ic;
+                    }
+                    acc[j].add(cT, W.eval(s, eps, lagrange));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int jf = j0 + j;
+                if (jf < nf) uhat[lo + (long long)jf * below] = acc[j].value();
+            }
+        }
     }
 }
 

@@ -6,7 +6,8 @@
 //   * the work queue is an array of (grid, tile) items, grid-major, tiles in row-major
 //     order of the tile grid;
 //   * alpha slots: three per grid (the max |f'(u)| of the input of RK stage 0, 1, 2), kept
-//     as the bit pattern of a non-negative double so that atomicMax on the integer orders
+//     as the bit pattern of a non-negative number in the state precision (FP64: the double's
+//     bits; FP32: the float's bits, zero-extended) so that atomicMax on the integer orders
 //     them like the values;
 //   * one InstState per instance carries its time, step size and step counters on the
 //     device, so that graph-captured steps need no host round trip.
@@ -30,6 +31,7 @@ struct GridDesc {
     int nt[SG_MAXD];     // tiles per axis
     double h[SG_MAXD];   // node spacing (hi-lo)/n
     double rdx[SG_MAXD]; // 1/h
+    float rdxf[SG_MAXD]; // (float)(1/h), for the FP32 kernels (no per-tile FP64 conversion)
     double lo[SG_MAXD];
     double coeff;        // combination coefficient (-1)^q C(d-1,q)
     int lev[SG_MAXD];
@@ -47,6 +49,7 @@ struct WorkItem {
 struct InstState {
     double t;
     double dt;
+    float dtf;              // (float)dt, for the FP32 kernels
     double t_end;
     double dt_nom;          // dt of the h^{5/3} rule (host-computed)
     double cfl;
@@ -69,6 +72,7 @@ struct PhysParams {
     int prolong;             // 0 WENO5 interpolation, 1 Lagrange
     double eps;
     double adv[SG_MAXD];
+    int alpha_f32;           // alpha slots hold float bits (FP32 state)
 };
 
 struct StageArgs {
@@ -89,6 +93,14 @@ struct ExactSpec {
     int dim, pde, nf;
     double lo[SG_MAXD], h[SG_MAXD], adv[SG_MAXD];
     double b, a, w, phi, t;
+};
+
+// One grid's entry for the fused last-axis prolongation + combination kernel.
+struct CombineGrid {
+    const void* src;  // the grid prolonged over axes 0..d-2: shape (N_f^{d-1}, n), axis 0 fastest
+    int n;            // coarse points of the last axis
+    int r;            // refinement ratio 2^{N_L - l_{d-1}} of the last axis
+    double coeff;     // combination coefficient
 };
 
 enum { SG_FLAG_NONFINITE = 0 };

@@ -27,4 +27,18 @@ void box_footprint(int d, const int* te, long long* box, long long* flux) {
     *flux = f;
 }
 
+void sweep_footprint(const int* te, long long* box, long long* flux) {
+    *box = (long long)((te[0] + 6) | 1) * (te[1] + 6) * (te[2] + 6);
+    *flux = 3 * 512;
+}
+
+void sweep_tile(const int* n, int* te) {
+    for (int k = 0; k < 3; ++k) {
+        int t = 0;
+        for (int c = 8; c >= 4 && !t; --c)
+            if (n[k] % c == 0) t = c;
+        te[k] = t ? t : (n[k] < 8 ? n[k] : 8);
+    }
+}
+
 }  // namespace sg

@@ -11,6 +11,11 @@ namespace sg {
 // Shared-memory footprint (elements) of the d <= 3 stage kernel for tile extents te[0..d-1]:
 // two padded boxes (box) and the flux arrays of all axes (flux).
 void box_footprint(int d, const int* te, long long* box, long long* flux);
+// The same for the d = 3 line-sweep kernel (odd x stride; three 512-point difference arrays).
+void sweep_footprint(const int* te, long long* box, long long* flux);
+// Tile extents of the d = 3 line-sweep kernel: <= 8 per axis (at most 512 points, 192 lines),
+// preferring a divisor of the axis length in [4, 8] so that no tile is ragged.
+void sweep_tile(const int* n, int* te);
 
 template <class T>
 struct Launch {
@@ -18,10 +23,13 @@ struct Launch {
     // (2 box + flux elements), d >= 4 the line-buffer kernel (fixed by ppt).
     static size_t stage_smem(int dim, int ppt, long long box, long long flux);
     // Raises the kernel's shared-memory limit and returns resident blocks per SM (0 if the
-    // configuration cannot run).
-    static int stage_prepare(int dim, int ppt, size_t smem);
+    // configuration cannot run).  variant: 0 = the default kernel of the dimension (d = 3:
+    // line sweep), 1 = the padded-box kernel for d = 3.
+    static int stage_prepare(int dim, int ppt, size_t smem, int variant = 0);
     // One RK stage over work items [a.item_begin, a.item_end) with `nblocks` blocks.
-    static cudaError_t stage(int dim, int ppt, const StageArgs& a, int nblocks, size_t smem, cudaStream_t s);
+    static cudaError_t stage(int dim, int ppt, const StageArgs& a, int nblocks, size_t smem, cudaStream_t s,
+                             int variant = 0);
+    static int stage_threads(int dim, int variant);
     // alpha slot 0 of every grid <- max |u0| (slots must be zero); flags non-finite values.
     static cudaError_t alpha_init(const GridDesc* grids, int ngrids, long long max_pts,
                                   unsigned long long* alpha, int* flags, cudaStream_t s);
@@ -32,6 +40,12 @@ struct Launch {
                                     int min_, int nf, long long above, int r, double eps,
                                     int lagrange, cudaStream_t s);
     static cudaError_t accumulate(const T* u, double* acc, double coeff, long long n, cudaStream_t s);
+    // One prolongation axis (2-D indexed form of prolong_axis without the accumulation).
+    static cudaError_t prolong_axis2(const T* in, T* out, long long below, int min_, int nf, long long above,
+                                     int r, double eps, int lagrange, cudaStream_t s);
+    // uhat = sum_g c_g P_{d-1} I_g over the G entries of tab (device array), written once.
+    static cudaError_t combine_last_axis(const CombineGrid* tab, int G, double* uhat, long long below, int nf,
+                                         double eps, int lagrange, cudaStream_t s);
     // FP64 reduction of n values u (+ comp if non-null); partial holds >= 1024 doubles.
     static cudaError_t reduce(const T* u, const T* comp, long long n, int kind, const ExactSpec& X,
                               double* partial, double* out, cudaStream_t s);

@@ -1,6 +1,8 @@
 // sg_launch_impl.cuh -- definitions of sg::Launch<T>; included by exactly one translation
 // unit per precision.
 #pragma once
+#include <algorithm>
+
 #include "sg_kernels.cuh"
 #include "sg_launch.h"
 
@@ -8,11 +10,14 @@ namespace sg {
 
 namespace detail {
 
+// d = 3: the line-sweep kernel (SG_NT3 threads; the points-per-thread choice does not apply);
+// d <= 2: the padded-box kernel; d >= 4: the line-buffer kernel.
 template <class T, int D, int PPT>
 struct StageKernel {
-    static constexpr bool box = D <= 3;
+    static constexpr int threads = D == 3 ? SG_NT3 : SG_NT;
     static void* fn() {
-        if constexpr (D <= 3) return (void*)sg_stage_box_kernel<T, D, PPT>;
+        if constexpr (D == 3) return (void*)sg_stage_sweep3_kernel<T>;
+        else if constexpr (D <= 2) return (void*)sg_stage_box_kernel<T, D, PPT>;
         else return (void*)sg_stage_line_kernel<T, D, PPT>;
     }
 };
@@ -20,7 +25,8 @@ struct StageKernel {
 template <class T, int D, int PPT>
 cudaError_t stage_one(const StageArgs& a, int nblocks, size_t smem, cudaStream_t s) {
     // the dynamic shared-memory limit was raised by stage_prepare() when the handle was created
-    if constexpr (D <= 3) sg_stage_box_kernel<T, D, PPT><<<nblocks, SG_NT, smem, s>>>(a);
+    if constexpr (D == 3) sg_stage_sweep3_kernel<T><<<nblocks, SG_NT3, smem, s>>>(a);
+    else if constexpr (D <= 2) sg_stage_box_kernel<T, D, PPT><<<nblocks, SG_NT, smem, s>>>(a);
     else sg_stage_line_kernel<T, D, PPT><<<nblocks, SG_NT, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -33,7 +39,7 @@ int prepare_one(size_t smem) {
         return 0;
     }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, SG_NT, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, StageKernel<T, D, PPT>::threads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -76,7 +82,41 @@ size_t Launch<T>::stage_smem(int dim, int ppt, long long box, long long flux) {
 }
 
 template <class T>
-int Launch<T>::stage_prepare(int dim, int ppt, size_t smem) {
+int Launch<T>::stage_threads(int dim, int variant) {
+    return dim == 3 && variant == 0 ? SG_NT3 : SG_NT;
+}
+
+namespace detail {
+template <class T>
+int prepare_box3(int ppt, size_t smem) {
+    const void* kern = ppt == 1 ? (const void*)sg_stage_box_kernel<T, 3, 1>
+                     : ppt == 2 ? (const void*)sg_stage_box_kernel<T, 3, 2> : (const void*)sg_stage_box_kernel<T, 3, 4>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, SG_NT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+template <class T>
+cudaError_t stage_box3(int ppt, const StageArgs& a, int nblocks, size_t smem, cudaStream_t s) {
+    switch (ppt) {
+        case 1: sg_stage_box_kernel<T, 3, 1><<<nblocks, SG_NT, smem, s>>>(a); break;
+        case 2: sg_stage_box_kernel<T, 3, 2><<<nblocks, SG_NT, smem, s>>>(a); break;
+        case 4: sg_stage_box_kernel<T, 3, 4><<<nblocks, SG_NT, smem, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+}  // namespace detail
+
+template <class T>
+int Launch<T>::stage_prepare(int dim, int ppt, size_t smem, int variant) {
+    if (dim == 3 && variant == 1) return detail::prepare_box3<T>(ppt, smem);
     switch (dim) {
         case 1: return detail::prepare_d<T, 1>(ppt, smem);
         case 2: return detail::prepare_d<T, 2>(ppt, smem);
@@ -89,8 +129,10 @@ int Launch<T>::stage_prepare(int dim, int ppt, size_t smem) {
 }
 
 template <class T>
-cudaError_t Launch<T>::stage(int dim, int ppt, const StageArgs& a, int nblocks, size_t smem, cudaStream_t s) {
+cudaError_t Launch<T>::stage(int dim, int ppt, const StageArgs& a, int nblocks, size_t smem, cudaStream_t s,
+                             int variant) {
     if (nblocks < 1) return cudaSuccess;
+    if (dim == 3 && variant == 1) return detail::stage_box3<T>(ppt, a, nblocks, smem, s);
     switch (dim) {
         case 1: return detail::stage_d<T, 1>(ppt, a, nblocks, smem, s);
         case 2: return detail::stage_d<T, 2>(ppt, a, nblocks, smem, s);
@@ -132,6 +174,31 @@ cudaError_t Launch<T>::prolong_axis(const T* in, T* out, double* acc, double coe
 template <class T>
 cudaError_t Launch<T>::accumulate(const T* u, double* acc, double coeff, long long n, cudaStream_t s) {
     sg_accumulate_kernel<T><<<detail::grid_for(n, 256), 256, 0, s>>>(u, acc, coeff, n);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Launch<T>::prolong_axis2(const T* in, T* out, long long below, int min_, int nf, long long above,
+                                     int r, double eps, int lagrange, cudaStream_t s) {
+    dim3 grid;
+    if (below == 1) {
+        grid.x = (unsigned)std::min<long long>((nf + 255) / 256, 65535);
+        grid.y = (unsigned)std::min<long long>(above, 65535);
+    } else {
+        grid.x = (unsigned)std::min<long long>((below + 255) / 256, 65535);
+        grid.y = (unsigned)std::min<long long>((long long)nf * above, 65535);
+    }
+    sg_prolong_axis2_kernel<T><<<grid, 256, 0, s>>>(in, out, below, min_, nf, above, r, eps, lagrange);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Launch<T>::combine_last_axis(const CombineGrid* tab, int G, double* uhat, long long below, int nf,
+                                         double eps, int lagrange, cudaStream_t s) {
+    constexpr int J = 8;
+    dim3 grid((unsigned)std::min<long long>((below + 255) / 256, 65535),
+              (unsigned)std::min<long long>((nf + J - 1) / J, 65535));
+    sg_combine_last_axis_kernel<T, J><<<grid, 256, 0, s>>>(tab, G, uhat, below, nf, eps, lagrange);
     return cudaGetLastError();
 }
 

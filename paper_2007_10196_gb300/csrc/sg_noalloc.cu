@@ -175,11 +175,13 @@ extern "C" sg_status sg_step_grid_noalloc(int dim, const long* shape, const doub
             gd.nt[k] = (n[k] + gd.te[k] - 1) / gd.te[k];
             gd.h[k] = (hi[k] - lo[k]) / (double)n[k];
             gd.rdx[k] = 1.0 / gd.h[k];
+            gd.rdxf[k] = (float)gd.rdx[k];
             gd.lo[k] = lo[k];
             ntiles *= gd.nt[k];
         } else {
             gd.n[k] = gd.te[k] = gd.nt[k] = 1;
             gd.h[k] = gd.rdx[k] = 1.0;
+            gd.rdxf[k] = 1.0f;
         }
     }
     if (ntiles > kMaxTiles) return na_fail(SG_ERR_ARG, "grid needs more work items than the scratch holds");
@@ -195,6 +197,7 @@ extern "C" sg_status sg_step_grid_noalloc(int dim, const long* shape, const doub
 
     InstState is{};
     is.dt = dt;
+    is.dtf = (float)dt;
     is.t_end = dt;
     is.active = 1;
     is.ngrids = 1;

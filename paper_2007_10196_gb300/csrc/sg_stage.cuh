@@ -70,8 +70,8 @@ struct StageIO<float> {
         if (stage == 1) return U[g] + Ub[g];
         return U[g] + D2[g];
     }
-    __device__ __forceinline__ float update(long long g, float L, double dt) const {
-        const float d = (float)dt * L;
+    __device__ __forceinline__ float update(long long g, float L, float dt) const {
+        const float d = dt * L;
         const float u = U[g];
         if (stage == 0) {
             Ub[g] = d;
@@ -98,14 +98,19 @@ __device__ __forceinline__ int stage_parity(const InstState* S) {
     return (int)((S->steps - S->step0) & 1);
 }
 
+__device__ __forceinline__ double sg_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float sg_max(float a, float b) { return fmaxf(a, b); }
+
 // Epilogue shared by both kernels: non-finite flag, alpha slot of the next stage, and the
-// clearing of the slot two stages ahead (by the grid's first item).
+// clearing of the slot two stages ahead (by the grid's first item).  The block max is taken in
+// the state precision and widened to double once per tile.
+template <class T>
 __device__ __forceinline__ void stage_epilogue(const StageArgs& A, const WorkItem& w, const GridDesc* G, int it,
-                                               double mx, bool bad, double* red) {
+                                               T mx, bool bad, T* red) {
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(A.flags + SG_FLAG_NONFINITE, 1);
     if (A.phys.pde == 1) {
-        const double m = block_max(mx, red);
-        if (threadIdx.x == 0) atomicMax(A.alpha + w.grid * 3 + (A.stage + 1) % 3, dbits(m));
+        const T m = block_max(mx, red);
+        if (threadIdx.x == 0) atomicMax(A.alpha + w.grid * 3 + (A.stage + 1) % 3, alpha_enc(m));
     }
     if (threadIdx.x == 0 && it == G->first_item) A.alpha[w.grid * 3 + (A.stage + 2) % 3] = 0ull;
 }
@@ -128,19 +133,20 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
     T* bp = reinterpret_cast<T*>(sg_smem_raw);
     T* bm = bp + A.box_elems;
     T* fb = bm + A.box_elems;
-    __shared__ double red[SG_NT / 32];
+    __shared__ T red[SG_NT / 32];
 
     const int tid = threadIdx.x;
     const PhysParams& ph = A.phys;
     const bool burgers = ph.pde == 1;
     const T eps12 = (T)(12.0 * ph.eps);
+    const T adv0 = (T)ph.adv[0], adv1 = (T)ph.adv[1], adv2 = (T)ph.adv[2];
 
     for (int it = A.item_begin + blockIdx.x; it < A.item_end; it += gridDim.x) {
         const WorkItem w = A.items[it];
         const GridDesc* G = A.grids + w.grid;
         const InstState* S = A.inst + G->inst;
         if (!S->active) continue;  // uniform: the state is not written during this kernel
-        const double dt = S->dt;
+        const T dt = inst_dt<T>(S);
         StageIO<T> io;
         io.setup(G, A.stage, stage_parity<T>(S));
 
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
         }
         const int P = e[0] * e[1] * e[2];
         const int B0 = e[0] + 6, B1 = D >= 2 ? e[1] + 6 : 1;
-        const T alpha_b = (T)bitsd(A.alpha[w.grid * 3 + A.stage]);
+        const T alpha_b = alpha_dec<T>(A.alpha[w.grid * 3 + A.stage]);
         const T half_alpha = (T)0.5 * alpha_b;
         FDiv fe0, fe1, fr0, fp0, fp1;
         fe0.init(e[0]);
@@ -245,10 +251,10 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
         const int NF = NF0 + NF1 + NF2;
         for (int q = tid; q < NF; q += SG_NT) {
             int b, Sx;
-            double ak;
+            T ak;
             if (q < NF0) {
                 Sx = 1;
-                ak = ph.adv[0];
+                ak = adv0;
                 const int r = (int)fp0.div((unsigned)q);
                 const int i = q - r * (e[0] + 1);
                 int y = 0, z = 0;
@@ -259,7 +265,7 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
                 b = i + B0 * ((y + (D >= 2 ? 3 : 0)) + B1 * (z + (D >= 3 ? 3 : 0)));
             } else if (D >= 2 && q < NF0 + NF1) {
                 Sx = B0;
-                ak = ph.adv[1];
+                ak = adv1;
                 const int qq = q - NF0;
                 const int r = (int)fe0.div((unsigned)qq);
                 const int x = qq - r * e[0];
@@ -268,7 +274,7 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
                 b = (x + 3) + B0 * (i + B1 * (z + (D >= 3 ? 3 : 0)));
             } else {
                 Sx = B0 * B1;
-                ak = ph.adv[2];
+                ak = adv2;
                 const int qq = q - NF0 - NF1;
                 const int r = (int)fe0.div((unsigned)qq);
                 const int x = qq - r * e[0];
@@ -281,14 +287,14 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
                 if (burgers) {
                     F = Weno<double>::interface_split((const double*)bp + b, (const double*)bm + b, Sx, ph);
                 } else {
-                    const double a = ak;
+                    const double a = (double)ak;
                     F = Weno<double>::interface((const double*)bp + b, Sx, a < 0.0 ? -a : a, a, ph);
                 }
             } else {
                 if (burgers) {
                     F = Weno<float>::interface_split((const float*)bp + b, (const float*)bm + b, Sx, eps12, ph.scheme);
                 } else {
-                    const float a = (float)ak;
+                    const float a = (float)ak;  // already float: no conversion
                     F = Weno<float>::interface((const float*)bp + b, Sx, fabsf(a), a, ph, eps12);
                 }
             }
@@ -297,9 +303,9 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
         __syncthreads();
 
         // ---- 3) flux difference, stage update, alpha of the result
-        double mx = 0.0;
+        T mx = T(0);
         bool bad = false;
-        const T r0 = (T)G->rdx[0], r1 = (T)G->rdx[1], r2 = (T)G->rdx[2];
+        const T r0 = grid_rdx<T>(G, 0), r1 = grid_rdx<T>(G, 1), r2 = grid_rdx<T>(G, 2);
 #pragma unroll
         for (int qq = 0; qq < PPT; ++qq) {
             const int p = tid + qq * SG_NT;
@@ -327,7 +333,328 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
             const long long g = (org[0] + c0) + gs[1] * (org[1] + c1) + gs[2] * (org[2] + c2);
             const T o = io.update(g, L, dt);
             if (!sg_isfinite(o)) bad = true;
-            mx = fmax(mx, (double)sg_abs(o));
+            mx = sg_max(mx, sg_abs(o));
+        }
+        stage_epilogue(A, w, G, it, mx, bad, red);
+        __syncthreads();  // the next tile overwrites the shared arrays
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// d = 3: line-sweep kernel.  Per tile (extents <= 8 on every axis, so at most 8^3 points and
+// 3 * 64 = 192 lines): one load of the padded box (as above, x stride made odd so that threads
+// on neighbouring x-lines hit different banks); then every thread takes one line of one axis
+// and sweeps it, keeping the five-point windows of f^+ and f^- in registers, so each new
+// interface costs one shared-memory load per side; the flux difference of each point goes to
+// a per-axis array D_k; finally each point forms L = ((0 - D_0) - D_1) - D_2 (the axis order
+// of the FP64 definition) and takes the stage update.
+//
+// SweepSide<T>: one side of the WENO5 reconstruction sliding along a line.  push_back shifts
+// in a value at the far end (the positive-wind stencil f_{i-2..i+2}); push_front at the near
+// end (the mirrored negative-wind stencil f_{i+3..i-1}).
+//   double: keeps the raw window and evaluates Eqs. (3)-(6) literally per interface.
+//   float: keeps first differences d1..d4 and T_j = 13 t_j^2 + 12 eps (t = second differences)
+//     and updates them incrementally, so consecutive interfaces share them.
+// ------------------------------------------------------------------------------------
+template <class T>
+struct SweepSide;
+
+template <>
+struct SweepSide<double> {
+    double w0, w1, w2, w3, w4;
+    __device__ __forceinline__ void init(double a, double b, double c, double d, double e, double) {
+        w0 = a; w1 = b; w2 = c; w3 = d; w4 = e;
+    }
+    __device__ __forceinline__ void push_back(double v, double) {
+        w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = v;
+    }
+    __device__ __forceinline__ void push_front(double v, double) {
+        w4 = w3; w3 = w2; w2 = w1; w1 = w0; w0 = v;
+    }
+};
+
+template <>
+struct SweepSide<float> {
+    float w0, w1, c, w3, w4;    // the window (c = centre); shifted, never recomputed
+    float d1, d2, d3, d4;       // first differences: the same values a fresh window would give
+    float T0, T1, T2;           // 13 t^2 + 12 eps of the three second differences
+    __device__ __forceinline__ void init(float a, float b, float cc, float d, float e, float eps12) {
+        w0 = a; w1 = b; c = cc; w3 = d; w4 = e;
+        d1 = b - a; d2 = cc - b; d3 = d - cc; d4 = e - d;
+        const float t0 = d2 - d1, t1 = d3 - d2, t2 = d4 - d3;
+        T0 = fmaf(13.f * t0, t0, eps12);
+        T1 = fmaf(13.f * t1, t1, eps12);
+        T2 = fmaf(13.f * t2, t2, eps12);
+    }
+    __device__ __forceinline__ void push_back(float v, float eps12) {
+        w0 = w1; w1 = c; c = w3; w3 = w4;
+        d1 = d2; d2 = d3; d3 = d4; d4 = v - w4;
+        w4 = v;
+        T0 = T1; T1 = T2;
+        const float t2 = d4 - d3;
+        T2 = fmaf(13.f * t2, t2, eps12);
+    }
+    __device__ __forceinline__ void push_front(float v, float eps12) {
+        w4 = w3; w3 = c; c = w1; w1 = w0;
+        d4 = d3; d3 = d2; d2 = d1; d1 = w0 - v;
+        w0 = v;
+        T2 = T1; T1 = T0;
+        const float t0 = d2 - d1;
+        T0 = fmaf(13.f * t0, t0, eps12);
+    }
+    // numerator and denominator of fhat - c (as in Weno<float>::side)
+    __device__ __forceinline__ void value(int linear, float& num, float& den) const {
+        const float p0 = fmaf(5.f / 6.f, d2, (-1.f / 3.f) * d1);
+        const float p1 = fmaf(1.f / 6.f, d2, (1.f / 3.f) * d3);
+        const float p2 = fmaf(2.f / 3.f, d3, (-1.f / 6.f) * d4);
+        float a0, a1, a2;
+        if (linear) {
+            a0 = 0.1f;
+            a1 = 0.6f;
+            a2 = 0.3f;
+        } else {
+            const float s0 = fmaf(3.f, d2, -d1), s1 = d2 + d3, s2 = fmaf(3.f, d3, -d4);
+            const float e0 = fmaf(3.f * s0, s0, T0);
+            const float e1 = fmaf(3.f * s1, s1, T1);
+            const float e2 = fmaf(3.f * s2, s2, T2);
+            const float E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
+            a0 = (1.f / 6.f) * (E1 * E2);
+            a1 = E0 * E2;
+            a2 = 0.5f * (E0 * E1);
+        }
+        num = fmaf(a0, p0, fmaf(a1, p1, a2 * p2));
+        den = a0 + a1 + a2;
+    }
+};
+
+__device__ __forceinline__ double sweep_flux(const SweepSide<double>& P, const SweepSide<double>& M,
+                                             const PhysParams& ph) {
+    const double fplus = Weno<double>::side(P.w0, P.w1, P.w2, P.w3, P.w4, ph.eps, ph.scheme);
+    const double fminus = Weno<double>::side(M.w0, M.w1, M.w2, M.w3, M.w4, ph.eps, ph.scheme);
+    return fplus + fminus;
+}
+
+__device__ __forceinline__ float sweep_flux(const SweepSide<float>& P, const SweepSide<float>& M,
+                                            const PhysParams& ph) {
+    float np, dp, nm, dm;
+    P.value(ph.scheme, np, dp);
+    M.value(ph.scheme, nm, dm);
+    return Weno<float>::combine(P.c, M.c, np, dp, nm, dm);
+}
+
+#define SG_NT3 192  // threads of the d = 3 sweep kernel: one per line of an 8x8x8 tile
+
+template <class T>
+__global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep3_kernel(const StageArgs A) {
+    extern __shared__ __align__(16) unsigned char sg_smem_raw[];
+    T* bp = reinterpret_cast<T*>(sg_smem_raw);   // f^+ (Burgers) or u (advection)
+    T* bm = bp + A.box_elems;                     // f^-
+    T* Dk = bm + A.box_elems;                     // 3 x 512 flux differences
+    __shared__ T red[SG_NT / 32];
+
+    const int tid = threadIdx.x;
+    const PhysParams& ph = A.phys;
+    const bool burgers = ph.pde == 1;
+    const T eps12 = (T)(12.0 * ph.eps);
+    const T adv[3] = {(T)ph.adv[0], (T)ph.adv[1], (T)ph.adv[2]};
+
+    for (int it = A.item_begin + blockIdx.x; it < A.item_end; it += gridDim.x) {
+        const WorkItem w = A.items[it];
+        const GridDesc* G = A.grids + w.grid;
+        const InstState* S = A.inst + G->inst;
+        if (!S->active) continue;  // uniform: the state is not written during this kernel
+        const T dt = inst_dt<T>(S);
+        StageIO<T> io;
+        io.setup(G, A.stage, stage_parity<T>(S));
+
+        int org[3], e[3], n[3];
+        {
+            unsigned tt = (unsigned)w.tile;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const unsigned nt = (unsigned)G->nt[k];
+                const unsigned tc = tt % nt;
+                tt /= nt;
+                n[k] = G->n[k];
+                org[k] = (int)tc * G->te[k];
+                e[k] = min(G->te[k], n[k] - org[k]);
+            }
+        }
+        const long long gs1 = n[0], gs2 = (long long)n[0] * n[1];
+        const int P = e[0] * e[1] * e[2];
+        const int R0 = e[0] + 6;                 // valid row length along x
+        const int B0 = R0 | 1;                   // odd row stride
+        const int B1 = e[1] + 6;
+        const T alpha_b = alpha_dec<T>(A.alpha[w.grid * 3 + A.stage]);
+        const T half_alpha = (T)0.5 * alpha_b;
+        FDiv fR0, fe0, fe1;
+        fR0.init(R0);
+        fe0.init(e[0]);
+        fe1.init(e[1]);
+
+        // ---- 1) padded box: interior rows with the x halos, then the y and z halos.  Tiles are
+        // at most 8^3, so each thread has at most 5 + 2 + 2 values to fetch: all loads are
+        // issued first (unrolled gather), then split and stored (scatter).
+        constexpr int M0 = (14 * 64 + SG_NT3 - 1) / SG_NT3, M1 = (8 * 6 * 8 + SG_NT3 - 1) / SG_NT3;
+        constexpr int MT = M0 + 2 * M1;
+        T val[MT];
+        int bid[MT];
+        {
+            const int n0 = R0 * e[1] * e[2];
+#pragma unroll
+            for (int j = 0; j < M0; ++j) {
+                const int q = tid + j * SG_NT3;
+                bid[j] = -1;
+                if (q < n0) {
+                    const int r = (int)fR0.div(q), x = q - r * R0;
+                    const int z = (int)fe1.div(r), y = r - z * e[1];
+                    int gx = org[0] + x - 3;
+                    if (gx < 0) gx += n[0];
+                    else if (gx >= n[0]) gx -= n[0];
+                    bid[j] = x + B0 * ((y + 3) + B1 * (z + 3));
+                    val[j] = io.load(gx + gs1 * (org[1] + y) + gs2 * (org[2] + z));
+                }
+            }
+            const int n1 = e[0] * 6 * e[2];
+#pragma unroll
+            for (int j = 0; j < M1; ++j) {
+                const int q = tid + j * SG_NT3;
+                bid[M0 + j] = -1;
+                if (q < n1) {
+                    const int r = (int)fe0.div(q), x = q - r * e[0];
+                    const int z = r / 6, h = r - z * 6;
+                    const int y = h < 3 ? h - 3 : e[1] + h - 3;
+                    int gy = org[1] + y;
+                    if (gy < 0) gy += n[1];
+                    else if (gy >= n[1]) gy -= n[1];
+                    bid[M0 + j] = (x + 3) + B0 * ((y + 3) + B1 * (z + 3));
+                    val[M0 + j] = io.load((org[0] + x) + gs1 * gy + gs2 * (org[2] + z));
+                }
+            }
+            const int n2 = e[0] * e[1] * 6;
+#pragma unroll
+            for (int j = 0; j < M1; ++j) {
+                const int q = tid + j * SG_NT3;
+                bid[M0 + M1 + j] = -1;
+                if (q < n2) {
+                    const int r = (int)fe0.div(q), x = q - r * e[0];
+                    const int h = (int)fe1.div(r), y = r - h * e[1];
+                    const int z = h < 3 ? h - 3 : e[2] + h - 3;
+                    int gz = org[2] + z;
+                    if (gz < 0) gz += n[2];
+                    else if (gz >= n[2]) gz -= n[2];
+                    bid[M0 + M1 + j] = (x + 3) + B0 * ((y + 3) + B1 * (z + 3));
+                    val[M0 + M1 + j] = io.load((org[0] + x) + gs1 * (org[1] + y) + gs2 * gz);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < MT; ++j) {
+                const int bidx = bid[j];
+                if (bidx < 0) continue;
+                const T v = val[j];
+                if (burgers) {
+                    if constexpr (sizeof(T) == 8) {
+                        double fp, fm;
+                        Weno<double>::split(v, alpha_b, 0.0, 1, fp, fm);
+                        bp[bidx] = fp;
+                        bm[bidx] = fm;
+                    } else {
+                        float fp, fm;
+                        Weno<float>::split_burgers(v, half_alpha, fp, fm);
+                        bp[bidx] = fp;
+                        bm[bidx] = fm;
+                    }
+                } else {
+                    bp[bidx] = v;
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- 2) one line per thread: sweep the interfaces, store the flux differences
+        const int L0 = e[1] * e[2], L1 = e[0] * e[2], L2 = e[0] * e[1];
+        for (int task = tid; task < L0 + L1 + L2; task += SG_NT3) {
+            int k, b0, S, pbase, pstride;
+            if (task < L0) {
+                k = 0;
+                const int z = (int)fe1.div(task), y = task - z * e[1];
+                b0 = B0 * ((y + 3) + B1 * (z + 3));
+                S = 1;
+                pbase = e[0] * (y + e[1] * z);
+                pstride = 1;
+            } else if (task < L0 + L1) {
+                k = 1;
+                const int q = task - L0;
+                const int z = (int)fe0.div(q), x = q - z * e[0];
+                b0 = (x + 3) + B0 * B1 * (z + 3);
+                S = B0;
+                pbase = x + e[0] * e[1] * z;
+                pstride = e[0];
+            } else {
+                k = 2;
+                const int q = task - L0 - L1;
+                const int y = (int)fe0.div(q), x = q - y * e[0];
+                b0 = (x + 3) + B0 * (y + 3);
+                S = B0 * B1;
+                pbase = x + e[0] * y;
+                pstride = e[0] * e[1];
+            }
+            const int ek = e[k];
+            const T rdx = grid_rdx<T>(G, k);
+            const T ak = k == 0 ? adv[0] : (k == 1 ? adv[1] : adv[2]);
+            const T alpha = burgers ? alpha_b : (ak < T(0) ? -ak : ak);
+            // values of f^+ / f^- at box coordinate j along the line
+            auto fplus = [&](int j) -> T {
+                if (burgers) return bp[b0 + j * S];
+                T fp, fm;
+                if constexpr (sizeof(T) == 8) Weno<double>::split(bp[b0 + j * S], alpha, ak, 0, fp, fm);
+                else {
+                    fp = (T)0.5 * (ak + alpha) * bp[b0 + j * S];
+                }
+                return fp;
+            };
+            auto fminus = [&](int j) -> T {
+                if (burgers) return bm[b0 + j * S];
+                T fp, fm;
+                if constexpr (sizeof(T) == 8) Weno<double>::split(bp[b0 + j * S], alpha, ak, 0, fp, fm);
+                else {
+                    fm = (T)0.5 * (ak - alpha) * bp[b0 + j * S];
+                }
+                return fm;
+            };
+            SweepSide<T> Pw, Mw;
+            // interface 0 (between local points -1 and 0): f^+ at box 0..4, f^- mirrored at box 5..1
+            Pw.init(fplus(0), fplus(1), fplus(2), fplus(3), fplus(4), eps12);
+            Mw.init(fminus(5), fminus(4), fminus(3), fminus(2), fminus(1), eps12);
+            T* D = Dk + k * 512;
+            T Fprev = sweep_flux(Pw, Mw, ph);
+            // ek <= 8: fully unrolled, so the window shifts are register renames, not moves
+#pragma unroll
+            for (int i = 1; i <= 8; ++i) {
+                if (i > ek) break;
+                Pw.push_back(fplus(i + 4), eps12);
+                Mw.push_front(fminus(i + 5), eps12);
+                const T F = sweep_flux(Pw, Mw, ph);
+                D[pbase + (i - 1) * pstride] = (F - Fprev) * rdx;
+                Fprev = F;
+            }
+        }
+        __syncthreads();
+
+        // ---- 3) L = ((0 - D_0) - D_1) - D_2, stage update, alpha of the result
+        T mx = T(0);
+        bool bad = false;
+        for (int p = tid; p < P; p += SG_NT3) {
+            const int r = (int)fe0.div(p), c0 = p - r * e[0];
+            const int c2 = (int)fe1.div(r), c1 = r - c2 * e[1];
+            T L = T(0);
+            L = L - Dk[p];
+            L = L - Dk[512 + p];
+            L = L - Dk[1024 + p];
+            const long long g = (org[0] + c0) + gs1 * (org[1] + c1) + gs2 * (org[2] + c2);
+            const T o = io.update(g, L, dt);
+            if (!sg_isfinite(o)) bad = true;
+            mx = sg_max(mx, sg_abs(o));
         }
         stage_epilogue(A, w, G, it, mx, bad, red);
         __syncthreads();  // the next tile overwrites the shared arrays
@@ -353,17 +680,18 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
     extern __shared__ __align__(16) unsigned char sg_smem_raw[];
     T* lb = reinterpret_cast<T*>(sg_smem_raw);
     T* fb = lb + LineSmem<PPT>::LB;
-    __shared__ double red[SG_NT / 32];
+    __shared__ T red[SG_NT / 32];
 
     const int tid = threadIdx.x;
     const PhysParams& ph = A.phys;
+    const float eps12f = (float)(12.0 * ph.eps);
 
     for (int it = A.item_begin + blockIdx.x; it < A.item_end; it += gridDim.x) {
         const WorkItem w = A.items[it];
         const GridDesc* G = A.grids + w.grid;
         const InstState* S = A.inst + G->inst;
         if (!S->active) continue;
-        const double dt = S->dt;
+        const T dt = inst_dt<T>(S);
         StageIO<T> io;
         io.setup(G, A.stage, stage_parity<T>(S));
 
@@ -386,7 +714,7 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
                 P *= ext[k];
             }
         }
-        const double alpha_slot = bitsd(A.alpha[w.grid * 3 + A.stage]);
+        const T alpha_slot = alpha_dec<T>(A.alpha[w.grid * 3 + A.stage]);
 
         int cp[PPT][D];
         bool own[PPT];
@@ -412,7 +740,7 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
             const int lines = P / ek;
             const int ls = (ek + 6) | 1;  // odd strides avoid bank conflicts
             const int fs = (ek + 1) | 1;
-            const T alpha = ph.pde == 1 ? (T)alpha_slot : (T)sg_abs(ph.adv[k]);
+            const T alpha = ph.pde == 1 ? alpha_slot : (T)sg_abs(ph.adv[k]);
             const T ak = (T)ph.adv[k];
             FDiv fl, fr, ff;
             fl.init((unsigned)lines);
@@ -456,12 +784,12 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
                     fb[line * fs + i] = Weno<double>::interface((const double*)v, 1, (double)alpha, (double)ak, ph);
                 } else {
                     fb[line * fs + i] = Weno<float>::interface((const float*)v, 1, (float)alpha, (float)ak, ph,
-                                                               (float)(12.0 * ph.eps));
+                                                               eps12f);
                 }
             }
             __syncthreads();
 
-            const T rdx = (T)G->rdx[k];
+            const T rdx = grid_rdx<T>(G, k);
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
                 if (!own[q]) continue;
@@ -478,7 +806,7 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
             __syncthreads();
         }
 
-        double mx = 0.0;
+        T mx = T(0);
         bool bad = false;
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
@@ -488,7 +816,7 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
             for (int k = 0; k < D; ++k) g += (long long)(org[k] + cp[q][k]) * gstr[k];
             const T o = io.update(g, acc[q], dt);
             if (!sg_isfinite(o)) bad = true;
-            mx = fmax(mx, (double)sg_abs(o));
+            mx = sg_max(mx, sg_abs(o));
         }
         stage_epilogue(A, w, G, it, mx, bad, red);
     }

@@ -16,11 +16,13 @@
 
 // Exact unsigned division by a run-time divisor d <= 2^16 for x < 2^16 (multiply-high by
 // ceil(2^32 / d)).  x (d - 1) < 2^32 guarantees floor(x m / 2^32) = floor(x / d).
+// ceil(2^32 / d) = floor((2^32 - 1) / d) + 1 for d >= 2, so one 32-bit division suffices
+// (a 64-bit one is emulated, partly on GB300's slow FP64 pipe).
 struct FDiv {
     unsigned m, d;
     __device__ __forceinline__ void init(unsigned dd) {
         d = dd;
-        m = dd <= 1u ? 0u : (unsigned)((0x100000000ull + dd - 1ull) / (unsigned long long)dd);
+        m = dd <= 1u ? 0u : 0xFFFFFFFFu / dd + 1u;
     }
     __device__ __forceinline__ unsigned div(unsigned x) const { return d <= 1u ? x : __umulhi(x, m); }
 };
@@ -29,6 +31,32 @@ __device__ __forceinline__ unsigned long long dbits(double v) {
     return (unsigned long long)__double_as_longlong(v);
 }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// Alpha slots: a non-negative max |u| stored as bits that unsigned atomicMax orders like the
+// values -- the double's bits for FP64 state, the float's bits zero-extended for FP32 state
+// (so the FP32 kernels never touch the FP64 pipe to read or write them).
+__device__ __forceinline__ unsigned long long alpha_enc(double v) { return dbits(v); }
+__device__ __forceinline__ unsigned long long alpha_enc(float v) { return (unsigned long long)__float_as_uint(v); }
+template <class T>
+__device__ __forceinline__ T alpha_dec(unsigned long long b);
+template <>
+__device__ __forceinline__ double alpha_dec<double>(unsigned long long b) { return bitsd(b); }
+template <>
+__device__ __forceinline__ float alpha_dec<float>(unsigned long long b) { return __uint_as_float((unsigned)b); }
+
+// dt and 1/h in the state precision (FP32: host- or dt-kernel-rounded copies)
+template <class T>
+__device__ __forceinline__ T inst_dt(const InstState* S);
+template <>
+__device__ __forceinline__ double inst_dt<double>(const InstState* S) { return S->dt; }
+template <>
+__device__ __forceinline__ float inst_dt<float>(const InstState* S) { return S->dtf; }
+template <class T>
+__device__ __forceinline__ T grid_rdx(const GridDesc* G, int k);
+template <>
+__device__ __forceinline__ double grid_rdx<double>(const GridDesc* G, int k) { return G->rdx[k]; }
+template <>
+__device__ __forceinline__ float grid_rdx<float>(const GridDesc* G, int k) { return G->rdxf[k]; }
 
 template <class T>
 __device__ __forceinline__ T sg_abs(T v) { return v < T(0) ? -v : v; }
@@ -46,6 +74,21 @@ __device__ __forceinline__ double block_max(double v, double* red) {
     if (wid == 0) {
         v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    __syncthreads();
+    return v;
+}
+
+// Float version: the FP32 kernels keep every per-point operation in FP32 (GB300's FP64 pipe
+// runs at a small fraction of the FP32 rate); the block result is widened once.
+__device__ __forceinline__ float block_max(float v, float* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     }
     __syncthreads();
     return v;

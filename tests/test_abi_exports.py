@@ -58,6 +58,7 @@ def test_params_struct_layout_and_defaults(built):
     assert p.struct_size == ctypes.sizeof(P.sg_params)
     assert p.eps == 1e-3 and p.precision == P.SG_F64 and p.cfl == 0.4
     assert list(p.hi) == [4.0] * 6
+    assert p.tile_points == 0 and p.stage_kernel == P.SG_STAGE_AUTO and p.combine_budget_gb == 0.0
 
 
 def test_argument_errors_without_gpu(built):
@@ -76,6 +77,15 @@ def test_argument_errors_without_gpu(built):
         P.sg_create(2, 10, 3, P.SG_PDE_ADVECTION, P.sg_params_init(eps=0.0))
     assert e.value.status == P.SG_ERR_ARG
     assert "eps" in P.sg_last_error()
+    with pytest.raises(P.SgError) as e:  # the sweep kernel exists for d = 3 only
+        P.sg_create(2, 10, 3, P.SG_PDE_ADVECTION, P.sg_params_init(stage_kernel=P.SG_STAGE_SWEEP))
+    assert e.value.status == P.SG_ERR_UNSUPPORTED
+    with pytest.raises(P.SgError) as e:
+        P.sg_create(3, 10, 3, P.SG_PDE_ADVECTION, P.sg_params_init(stage_kernel=3))
+    assert e.value.status == P.SG_ERR_ARG
+    with pytest.raises(P.SgError) as e:
+        P.sg_create(3, 10, 3, P.SG_PDE_ADVECTION, P.sg_params_init(tile_points=300))
+    assert e.value.status == P.SG_ERR_ARG
     assert P.lib().sg_destroy(None) == 0
 
 
