@@ -43,10 +43,18 @@ WORKLOAD = "burgers3d_batch256_t0.3_cfl0.4_f32_batched"
 # one-sided WENO5 reconstructions (2 x 54) and their combination (7), the flux difference (3);
 # plus the RK update (4 on average over the three stages).
 FLOPS_PER_POINT_STAGE_3D = 3 * (6 + 2 * 54 + 7 + 3) + 4
-# Algorithmic HBM bytes per point per full RK step (FP32): stage 1 reads u^n and writes u1,
-# stages 2 and 3 read the stage input and u^n and write the result: 8 + 12 + 12.
-BYTES_PER_POINT_STEP = 32
+# Algorithmic HBM bytes per point per full RK step, FP32 compensated state (u^n = U + C, stage
+# increments D1, D2): stage 1 reads U, writes D1 (8); stage 2 reads U, D1, writes D2 (12);
+# stage 3 reads U, D2, C, writes U and C (20).
+BYTES_PER_POINT_STEP = 40
+# FP64 Shu-Osher form: stage 1 reads u^n, writes u1 (16); stages 2 and 3 read their input and
+# u^n and write the result (24 + 24).
+BYTES_PER_POINT_STEP_F64 = 64
 FP32_LANES_PER_SM = 128
+# Burgers shock time of u0 = 0.5 + a sin(pi (x+y+z)/2): characteristics in s = x+y+z move at
+# 3u, so they first cross at t = 1 / (3 a pi/2); members with a below this stay smooth to t_end.
+A_SMOOTH_AT_T_END = 2.0 / (3.0 * math.pi * 0.3)
+STAGE_SOURCES = ("sg_stage.cuh", "sg_weno.cuh", "sg_device.h")
 
 
 def _env_rank():
@@ -168,19 +176,87 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def _stage_traffic(points_per_launch):
-    """DRAM bytes per stage launch from the committed ncu summary, scaled by the points one
-    launch processes, if the kernel source still matches the one profiled; else None."""
+def stage_source_hash():
+    """sha256 over the sources that define the stage kernels."""
+    h = hashlib.sha256()
+    for name in STAGE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2007_10196_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _stage_traffic(kernel, points_per_launch):
+    """DRAM bytes per stage launch from the committed ncu summary (bytes per point-stage of the
+    profiled launches), scaled by the points one launch processes -- if that summary is of the
+    same kernel built from the same sources; else None."""
     path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
-        src = open(os.path.join(ROOT, "paper_2007_10196_gb300", "csrc", "sg_kernels.cuh"), "rb").read()
-        if hashlib.sha256(src).hexdigest() != rec["kernel_sha256"]:
+        if rec["kernel"] != kernel or rec["sources_sha256"] != stage_source_hash():
             return None
         return rec["dram_bytes_per_point_stage"] * points_per_launch
     except (OSError, ValueError, KeyError):
         return None
+
+
+def kernel_name(P, h):
+    kern, tp, _ = P.sg_stage_config(h)
+    if kern == P.SG_STAGE_SWEEP:
+        return "sg_stage_sweep3_kernel<float>"
+    return "sg_stage_box_kernel<float,3,%d>" % (tp // 256)
+
+
+def compare_fp64_plain(P, stream, members, nmax=4):
+    """The plain FP64 path (one launch per grid per RK stage) against the batched FP32 path on
+    the same members: stepping rates to t_end, and the L1 error of the combined solution
+    against the exact (characteristic) solution for both, on members still smooth at t_end."""
+    import torch
+    sel = [m for m in members if m.a < A_SMOOTH_AT_T_END][:nmax]
+    if not sel:
+        return None
+    ics = [(0.5, m.a, math.pi / 2, 0.0) for m in sel]
+    pts = [n for _, n in _batch_points(sel)]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for prec, exe in ((P.SG_F64, P.SG_PLAIN), (P.SG_F32, P.SG_BATCHED)):
+        hs = [P.create(3, m.nr, m.nl, P.SG_PDE_BURGERS, precision=prec, exec=exe, dt_rule=P.SG_DT_CFL,
+                       cfl=inputs.BATCH_CFL, cuda_stream=stream.cuda_stream) for m in sel]
+        b = P.sg_batch_create(hs) if exe == P.SG_BATCHED else None
+        try:
+            ms = 0.0
+            for rep in range(2):  # the first pass autotunes and warms up
+                for h, ic in zip(hs, ics):
+                    P.sg_init(h, P.SG_IC_SINE, ic)
+                ev0.record(stream)
+                if b is not None:
+                    P.sg_step(b, inputs.BATCH_T_END)
+                else:
+                    for h in hs:
+                        P.sg_step(h, inputs.BATCH_T_END)
+                ev1.record(stream)
+                ev1.synchronize()
+                ms = ev0.elapsed_time(ev1)
+            upd = sum(P.sg_time(h)[1] * n for h, n in zip(hs, pts))
+            l1 = []
+            for h in hs:
+                P.sg_prolong_combine(h)
+                l1.append(P.sg_reduce(h, -1, P.SG_REDUCE_L1_EXACT))
+            res[prec] = (upd / (ms / 1e3), l1, ms)
+        finally:
+            if b is not None:
+                P.sg_destroy(b)
+            for h in hs:
+                P.sg_destroy(h)
+    r64, l64, ms64 = res[P.SG_F64]
+    r32, l32, ms32 = res[P.SG_F32]
+    return {"fp64_plain_value": r64, "fp32_batched_value": r32, "unit": UNIT, "speedup": r32 / r64,
+            "fp64_plain_hbm_gbs": r64 * BYTES_PER_POINT_STEP_F64 / 1e9,
+            "fp64_plain_ms": ms64, "fp32_batched_ms": ms32,
+            "members": [(m.nr, m.nl, round(m.a, 4)) for m in sel],
+            "l1_exact_fp64": l64, "l1_exact_fp32": l32,
+            "l1_ratio_fp32_over_fp64_max": max(a / b for a, b in zip(l32, l64)),
+            "note": "same members, both stepped to t_end and combined; L1 against the exact solution"}
 
 
 def aggregate(local_ms, local_updates, dist=None, device="cpu"):
@@ -315,8 +391,13 @@ def run_ours(args, rank, world, local_rank):
     mean_ms = statistics.mean(times)
     total_ms, total_upd = aggregate(sum(times), upd_per_pass * args.steps, dist, "cuda")
 
+    kname = kernel_name(P, batch)
     for h in [batch] + hs:
         P.sg_destroy(h)
+    compare = None
+    if rank == 0 and not args.no_compare:  # untimed: after the timed region and the e2e pass
+        with torch.cuda.stream(stream):
+            compare = compare_fp64_plain(P, stream, members)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -329,7 +410,7 @@ def run_ours(args, rank, world, local_rank):
     point_stages = 3 * upd_per_pass * args.steps
     achieved = point_stages * FLOPS_PER_POINT_STAGE_3D / (stage_ms / 1e3) / 1e12
     hbm_gbs = upd_per_pass * args.steps * BYTES_PER_POINT_STEP / (stage_ms / 1e3) / 1e9
-    traffic = _stage_traffic(point_stages / max(stage_launches, 1))
+    traffic = _stage_traffic(kname, point_stages / max(stage_launches, 1))
     clocks = clk.summary()
     cpu = None
     if pool is not None:
@@ -350,7 +431,7 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": "replicas" if world == 1 else "dp%d" % world},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
-                     "kernel": "sg_stage_kernel<float,3,2>",
+                     "kernel": kname,
                      "peak_source": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (%s SM clock)" % (nsm, FP32_LANES_PER_SM, sm_max, src)},
         "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
                 "frac": hbm_gbs / float(peaks.get("hbm_gbs", 6800.0)), "peak_source": src,
@@ -359,6 +440,7 @@ def run_ours(args, rank, world, local_rank):
                          "stage_launches": stage_launches // args.steps},
         "stepping_rate": upd_per_pass / (statistics.mean(step_ms) / 1e3),
         "bound_overshoot": over,
+        "fp64_plain_vs_fp32_batched": compare,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -400,6 +482,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64-plain comparison")
     ap.add_argument("--members", type=int, default=256,
                     help="first M members of the batch only (small cases for profiling)")
     args = ap.parse_args()

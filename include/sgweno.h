@@ -162,6 +162,14 @@ sg_status sg_prolong_combine(sg_handle h);
  * SG_ERR_STATE for -1 before sg_prolong_combine, SG_ERR_ARG for a small buffer. */
 sg_status sg_read(sg_handle h, int which, void *host_dst, size_t dst_bytes);
 
+/* Sampled read: dst[j] = value at flat index idx[j] (axis 0 fastest) of the combined solution
+ * (which = SG_WHICH_COMBINED; doubles), grid `which` >= 0, or SG_WHICH_ALL_GRIDS (values in the
+ * handle's precision), j < n.  idx and dst are host arrays owned by the caller; dst_bytes
+ * must hold n values.  Gathers on the device, so a large combined solution (256^4 doubles is
+ * 34 GB) can be checked at sample points without copying it.  SG_ERR_ARG for an index out of
+ * range (nothing is read), SG_ERR_STATE as for sg_read.  Synchronises the handle's stream. */
+sg_status sg_read_points(sg_handle h, int which, const long long *idx, size_t n, void *dst, size_t dst_bytes);
+
 /* FP64 reduction of the combined solution (which = -1) or of grid g, kind one of
  * SG_REDUCE_*.  L1_EXACT / LINF_EXACT need which = -1 and an SG_IC_SINE initial condition
  * (SG_ERR_STATE otherwise). */

@@ -38,7 +38,7 @@ EXPORTED = [
     "sg_params_init", "sg_create", "sg_init", "sg_init_grid", "sg_init_grids", "sg_step",
     "sg_prolong_combine", "sg_read", "sg_reduce", "sg_num_grids", "sg_grid_info", "sg_time",
     "sg_batch_create", "sg_destroy", "sg_last_error", "sg_set_allocator", "sg_launch_count",
-    "sg_set_profiling", "sg_profile", "sg_step_grid_noalloc", "sg_stage_config",
+    "sg_set_profiling", "sg_profile", "sg_step_grid_noalloc", "sg_stage_config", "sg_read_points",
 ]
 SG_NOALLOC_MAX_POINTS = 1048576
 SG_PROF_STAGE = 0
@@ -108,6 +108,7 @@ def lib():
         "sg_set_profiling": (st, [H, C.c_int]),
         "sg_profile": (st, [H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
         "sg_stage_config": (st, [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+        "sg_read_points": (st, [H, C.c_int, C.POINTER(C.c_longlong), C.c_size_t, C.c_void_p, C.c_size_t]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -213,6 +214,17 @@ def sg_read(h, which: int, out=None, count: int | None = None):
             raise ValueError("count is required when out is None")
         out = np.empty(count, dtype=dt)
     _check(lib().sg_read(h, which, out.ctypes.data, out.nbytes))
+    return out
+
+
+def sg_read_points(h, which: int, idx):
+    """Values at flat indices `idx` of the combined solution (which = -1, doubles), of grid
+    `which` or of all grids (-2), gathered on the device."""
+    ix = np.ascontiguousarray(idx, dtype=np.int64)
+    dt = np.dtype(np.float64) if which == SG_WHICH_COMBINED else _dtype(h)
+    out = np.empty(ix.size, dtype=dt)
+    _check(lib().sg_read_points(h, which, ix.ctypes.data_as(C.POINTER(C.c_longlong)), ix.size,
+                                out.ctypes.data, out.nbytes))
     return out
 
 

@@ -1135,6 +1135,49 @@ sg_status sg_read(sg_handle h, int which, void* host_dst, size_t dst_bytes) {
     return SG_OK;
 }
 
+sg_status sg_read_points(sg_handle h, int which, const long long* host_idx, size_t n, void* host_dst,
+                         size_t dst_bytes) {
+    SG_TRY(check_handle(h));
+    if (h->is_batch) return fail(SG_ERR_ARG, "sg_read_points applies to batch members");
+    if (n == 0) return SG_OK;
+    if (!host_idx || !host_dst) return fail(SG_ERR_ARG, "NULL index or destination array");
+    const void* src;
+    long long count;
+    size_t esz;
+    if (which == SG_WHICH_COMBINED) {
+        if (!h->combined) return fail(SG_ERR_STATE, "no combined solution: call sg_prolong_combine first");
+        src = h->uhat.p;
+        count = h->fine_pts;
+        esz = sizeof(double);
+    } else if (which >= 0 && which < h->G) {
+        src = h->hgrids[which].u0;
+        count = h->npts[which];
+        esz = h->esize;
+    } else if (which == SG_WHICH_ALL_GRIDS) {
+        src = h->hgrids[0].u0;
+        count = h->total_pts;
+        esz = h->esize;
+    } else {
+        return fail(SG_ERR_ARG, "which = %d out of range", which);
+    }
+    if (dst_bytes < n * esz) return fail(SG_ERR_ARG, "destination holds %zu bytes, need %zu", dst_bytes, n * esz);
+    for (size_t j = 0; j < n; ++j)
+        if (host_idx[j] < 0 || host_idx[j] >= count)
+            return fail(SG_ERR_ARG, "index %lld at position %zu outside [0, %lld)", host_idx[j], j, count);
+    DevBuf didx, dout;
+    SG_TRY(didx.alloc(n * sizeof(long long)));
+    SG_TRY(dout.alloc(n * esz));
+    SG_CUDA(cudaMemcpyAsync(didx.p, host_idx, n * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+    if (esz == 8)
+        SG_CUDA(sg::Launch<double>::gather((const double*)src, didx.as<long long>(), dout.as<double>(), (long long)n, h->stream));
+    else
+        SG_CUDA(sg::Launch<float>::gather((const float*)src, didx.as<long long>(), dout.as<float>(), (long long)n, h->stream));
+    h->launches += 1;
+    SG_CUDA(cudaMemcpyAsync(host_dst, dout.p, n * esz, cudaMemcpyDeviceToHost, h->stream));
+    SG_CUDA(cudaStreamSynchronize(h->stream));
+    return SG_OK;
+}
+
 sg_status sg_reduce(sg_handle h, int which, int kind, double* out) {
     SG_TRY(check_handle(h));
     if (h->is_batch) return fail(SG_ERR_ARG, "sg_reduce applies to batch members");

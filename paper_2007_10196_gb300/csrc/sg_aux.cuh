@@ -399,6 +399,15 @@ __global__ void sg_accumulate_kernel(const T* __restrict__ u, double* __restrict
         acc[i] = acc[i] + coeff * (double)u[i];
 }
 
+// out[j] = u[idx[j]] (indices checked by the host).
+template <class T>
+__global__ void sg_gather_kernel(const T* __restrict__ u, const long long* __restrict__ idx, T* __restrict__ out,
+                                 long long n) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x)
+        out[j] = u[idx[j]];
+}
+
 // ------------------------------------------------------------------------------------
 // FP64 reductions, deterministic two-pass (fixed grid, fixed order).
 // kind: 0 sum u, 1 sum u^2, 2 min, 3 max, 4 sum |u - exact|, 5 max |u - exact|

@@ -40,6 +40,8 @@ struct Launch {
                                     int min_, int nf, long long above, int r, double eps,
                                     int lagrange, cudaStream_t s);
     static cudaError_t accumulate(const T* u, double* acc, double coeff, long long n, cudaStream_t s);
+    // out[j] = u[idx[j]], j < n (device arrays; indices already checked)
+    static cudaError_t gather(const T* u, const long long* idx, T* out, long long n, cudaStream_t s);
     // One prolongation axis (2-D indexed form of prolong_axis without the accumulation).
     static cudaError_t prolong_axis2(const T* in, T* out, long long below, int min_, int nf, long long above,
                                      int r, double eps, int lagrange, cudaStream_t s);

@@ -178,6 +178,13 @@ cudaError_t Launch<T>::accumulate(const T* u, double* acc, double coeff, long lo
 }
 
 template <class T>
+cudaError_t Launch<T>::gather(const T* u, const long long* idx, T* out, long long n, cudaStream_t s) {
+    if (n < 1) return cudaSuccess;
+    sg_gather_kernel<T><<<detail::grid_for(n, 256), 256, 0, s>>>(u, idx, out, n);
+    return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t Launch<T>::prolong_axis2(const T* in, T* out, long long below, int min_, int nf, long long above,
                                      int r, double eps, int lagrange, cudaStream_t s) {
     dim3 grid;
