@@ -147,8 +147,10 @@ sg_status sg_init_grids(sg_handle h, const void *host_values, size_t bytes);
 /* Step 2: advances every component grid with the common time step until t = t_end (last
  * step shortened) or until max_steps further steps have been taken.  *t_reached (may be
  * NULL) receives the time reached (for a batch: the smallest over members).  Errors:
- * SG_ERR_STATE before init, SG_ERR_NONFINITE if a stage produced NaN/Inf (the state then
- * holds that stage's output), SG_ERR_ARG if t_end is not finite or max_steps < 0. */
+ * SG_ERR_STATE before init, SG_ERR_NONFINITE if a stage produced NaN/Inf or a time step came
+ * out non-positive or non-finite (stepping stops at the next check, at most one captured graph
+ * of steps later; the state then holds the last stage's output), SG_ERR_ARG if t_end is not
+ * finite or max_steps < 0. */
 sg_status sg_step(sg_handle h, double t_end, long max_steps, double *t_reached);
 
 /* Step 3: prolongs every component grid onto the finest grid (axis 0 first) and forms

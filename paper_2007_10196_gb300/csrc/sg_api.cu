@@ -411,7 +411,8 @@ sg_status enqueue_steps(sg_ctx* h, int nsteps, long long* kernels) {
     if (h->profile) SG_TRY(ensure_events(h, 3 * nsteps));
     h->ev_pairs_used = h->profile ? 3 * nsteps : 0;
     for (int s = 0; s < nsteps; ++s) {
-        SG_CUDA(sg::launch_dt(h->dinst.as<InstState>(), h->ninst, h->alpha.as<unsigned long long>(), ph, 0, h->stream));
+        SG_CUDA(sg::launch_dt(h->dinst.as<InstState>(), h->ninst, h->alpha.as<unsigned long long>(), ph, 0,
+                              h->flags.as<int>(), h->stream));
         ++nk;
         for (int stage = 0; stage < 3; ++stage) {
             StageArgs a{};
@@ -696,20 +697,24 @@ sg_status run_steps(sg_ctx* h) {
             SG_TRY(enqueue_steps(h, K, &nk));
             h->launches += nk;
         }
+        int lflags[4] = {0, 0, 0, 0};
         SG_CUDA(cudaMemcpyAsync(h->hinst.p, h->dinst.p, sizeof(InstState) * h->ninst, cudaMemcpyDeviceToHost, h->stream));
+        SG_CUDA(cudaMemcpyAsync(lflags, h->flags.p, sizeof lflags, cudaMemcpyDeviceToHost, h->stream));
         SG_CUDA(cudaStreamSynchronize(h->stream));
         SG_TRY(collect_profile(h));
         bool all = true;
         for (int i = 0; i < h->ninst; ++i) all = all && finished(h->hinst.p[i]);
-        if (all) break;
+        if (all || lflags[SG_FLAG_NONFINITE] || lflags[SG_FLAG_BADDT]) break;  // done, or failed: stop early
     }
-    SG_CUDA(sg::launch_dt(h->dinst.as<InstState>(), h->ninst, h->alpha.as<unsigned long long>(), phys_of(h), 1, h->stream));
+    SG_CUDA(sg::launch_dt(h->dinst.as<InstState>(), h->ninst, h->alpha.as<unsigned long long>(), phys_of(h), 1,
+                          h->flags.as<int>(), h->stream));
     h->launches += 1;
     int hflags[4] = {0, 0, 0, 0};
     SG_CUDA(cudaMemcpyAsync(h->hinst.p, h->dinst.p, sizeof(InstState) * h->ninst, cudaMemcpyDeviceToHost, h->stream));
     SG_CUDA(cudaMemcpyAsync(hflags, h->flags.p, sizeof hflags, cudaMemcpyDeviceToHost, h->stream));
     SG_CUDA(cudaStreamSynchronize(h->stream));
     if (hflags[SG_FLAG_NONFINITE]) return fail(SG_ERR_NONFINITE, "a non-finite value appeared in the solution");
+    if (hflags[SG_FLAG_BADDT]) return fail(SG_ERR_NONFINITE, "the time step came out non-positive or non-finite");
     return SG_OK;
 }
 

@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(SG_NT) sg_alpha_init_kernel(const GridDesc* gr
 // a step: adds the previous (pending) step to t, then sets dt for the next step or marks the
 // instance inactive.  commit_only = 1 after the last step: only adds the pending step.
 static __global__ void sg_dt_kernel(InstState* inst, int ninst, const unsigned long long* alpha,
-                             PhysParams ph, int commit_only) {
+                             PhysParams ph, int commit_only, int* flags) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ninst) return;
     InstState s = inst[i];
@@ -60,6 +60,11 @@ static __global__ void sg_dt_kernel(InstState* inst, int ninst, const unsigned l
             dt = s.cfl / sum;
         }
         s.last = 0;
+        if (!(dt > 0.0) || !isfinite(dt)) {  // e.g. alpha overflowed: stop instead of stalling
+            atomicOr(flags + SG_FLAG_BADDT, 1);
+            inst[i] = s;  // inactive, nothing pending
+            return;
+        }
         if (dt >= s.t_end - s.t) {  // shortened last step: the run ends exactly at t_end
             dt = s.t_end - s.t;
             s.last = 1;

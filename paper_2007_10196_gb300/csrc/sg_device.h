@@ -103,4 +103,6 @@ struct CombineGrid {
     double coeff;     // combination coefficient
 };
 
-enum { SG_FLAG_NONFINITE = 0 };
+// flags[0]: a non-finite value appeared; flags[1]: a time step came out non-positive or
+// non-finite (the instance is stopped)
+enum { SG_FLAG_NONFINITE = 0, SG_FLAG_BADDT = 1 };

@@ -9,9 +9,9 @@ namespace sg {
 template struct Launch<double>;
 
 cudaError_t launch_dt(InstState* inst, int ninst, const unsigned long long* alpha,
-                      const PhysParams& ph, int commit_only, cudaStream_t s) {
+                      const PhysParams& ph, int commit_only, int* flags, cudaStream_t s) {
     if (ninst < 1) return cudaSuccess;
-    sg_dt_kernel<<<(ninst + 127) / 128, 128, 0, s>>>(inst, ninst, alpha, ph, commit_only);
+    sg_dt_kernel<<<(ninst + 127) / 128, 128, 0, s>>>(inst, ninst, alpha, ph, commit_only, flags);
     return cudaGetLastError();
 }
 
@@ -29,7 +29,7 @@ void box_footprint(int d, const int* te, long long* box, long long* flux) {
 
 void sweep_footprint(const int* te, long long* box, long long* flux) {
     *box = (long long)((te[0] + 6) | 1) * (te[1] + 6) * (te[2] + 6);
-    *flux = 3 * 512;
+    *flux = 3 * SG_DK_AXIS;
 }
 
 void sweep_tile(const int* n, int* te) {

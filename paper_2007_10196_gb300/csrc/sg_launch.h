@@ -56,8 +56,9 @@ struct Launch {
 extern template struct Launch<double>;
 extern template struct Launch<float>;
 
+// flags: the device flag array (SG_FLAG_BADDT is set if a step comes out non-positive)
 cudaError_t launch_dt(InstState* inst, int ninst, const unsigned long long* alpha,
-                      const PhysParams& ph, int commit_only, cudaStream_t s);
+                      const PhysParams& ph, int commit_only, int* flags, cudaStream_t s);
 
 // Sets the calling thread's message returned by sg_last_error (defined in sg_api.cu).
 void set_last_error(const char* msg);

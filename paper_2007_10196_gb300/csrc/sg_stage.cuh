@@ -107,10 +107,15 @@ __device__ __forceinline__ float sg_max(float a, float b) { return fmaxf(a, b); 
 template <class T>
 __device__ __forceinline__ void stage_epilogue(const StageArgs& A, const WorkItem& w, const GridDesc* G, int it,
                                                T mx, bool bad, T* red) {
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(A.flags + SG_FLAG_NONFINITE, 1);
     if (A.phys.pde == 1) {
-        const T m = block_max(mx, red);
-        if (threadIdx.x == 0) atomicMax(A.alpha + w.grid * 3 + (A.stage + 1) % 3, alpha_enc(m));
+        // one reduction for both: a non-finite value is carried as -1 (|u| >= 0 otherwise)
+        const T m = block_max(bad ? T(-1) : mx, red, bad);
+        if (threadIdx.x == 0) {
+            if (m < T(0)) atomicOr(A.flags + SG_FLAG_NONFINITE, 1);
+            else atomicMax(A.alpha + w.grid * 3 + (A.stage + 1) % 3, alpha_enc(m));
+        }
+    } else if (__syncthreads_or(bad) && threadIdx.x == 0) {
+        atomicOr(A.flags + SG_FLAG_NONFINITE, 1);
     }
     if (threadIdx.x == 0 && it == G->first_item) A.alpha[w.grid * 3 + (A.stage + 2) % 3] = 0ull;
 }
@@ -443,13 +448,17 @@ __device__ __forceinline__ float sweep_flux(const SweepSide<float>& P, const Swe
 }
 
 #define SG_NT3 192  // threads of the d = 3 sweep kernel: one per line of an 8x8x8 tile
+// Flux differences of axis k: line l of the tile (axis 0: y + e1 z; axis 1: x + e0 z; axis 2:
+// x + e0 y), point i along it, at Dk[SG_DK_AXIS k + 9 l + i].  The odd line stride puts the
+// lines a warp sweeps, and the points a warp updates, on distinct banks.
+#define SG_DK_AXIS 576
 
 template <class T>
 __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep3_kernel(const StageArgs A) {
     extern __shared__ __align__(16) unsigned char sg_smem_raw[];
     T* bp = reinterpret_cast<T*>(sg_smem_raw);   // f^+ (Burgers) or u (advection)
     T* bm = bp + A.box_elems;                     // f^-
-    T* Dk = bm + A.box_elems;                     // 3 x 512 flux differences
+    T* Dk = bm + A.box_elems;                     // 3 x SG_DK_AXIS flux differences
     __shared__ T red[SG_NT / 32];
 
     const int tid = threadIdx.x;
@@ -574,30 +583,27 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
         // ---- 2) one line per thread: sweep the interfaces, store the flux differences
         const int L0 = e[1] * e[2], L1 = e[0] * e[2], L2 = e[0] * e[1];
         for (int task = tid; task < L0 + L1 + L2; task += SG_NT3) {
-            int k, b0, S, pbase, pstride;
+            int k, b0, S, line;
             if (task < L0) {
                 k = 0;
                 const int z = (int)fe1.div(task), y = task - z * e[1];
                 b0 = B0 * ((y + 3) + B1 * (z + 3));
                 S = 1;
-                pbase = e[0] * (y + e[1] * z);
-                pstride = 1;
+                line = task;
             } else if (task < L0 + L1) {
                 k = 1;
                 const int q = task - L0;
                 const int z = (int)fe0.div(q), x = q - z * e[0];
                 b0 = (x + 3) + B0 * B1 * (z + 3);
                 S = B0;
-                pbase = x + e[0] * e[1] * z;
-                pstride = e[0];
+                line = q;
             } else {
                 k = 2;
                 const int q = task - L0 - L1;
                 const int y = (int)fe0.div(q), x = q - y * e[0];
                 b0 = (x + 3) + B0 * (y + 3);
                 S = B0 * B1;
-                pbase = x + e[0] * y;
-                pstride = e[0] * e[1];
+                line = q;
             }
             const int ek = e[k];
             const T rdx = grid_rdx<T>(G, k);
@@ -626,7 +632,7 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
             // interface 0 (between local points -1 and 0): f^+ at box 0..4, f^- mirrored at box 5..1
             Pw.init(fplus(0), fplus(1), fplus(2), fplus(3), fplus(4), eps12);
             Mw.init(fminus(5), fminus(4), fminus(3), fminus(2), fminus(1), eps12);
-            T* D = Dk + k * 512;
+            T* D = Dk + k * SG_DK_AXIS + 9 * line;
             T Fprev = sweep_flux(Pw, Mw, ph);
             // ek <= 8: fully unrolled, so the window shifts are register renames, not moves
 #pragma unroll
@@ -635,7 +641,7 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
                 Pw.push_back(fplus(i + 4), eps12);
                 Mw.push_front(fminus(i + 5), eps12);
                 const T F = sweep_flux(Pw, Mw, ph);
-                D[pbase + (i - 1) * pstride] = (F - Fprev) * rdx;
+                D[i - 1] = (F - Fprev) * rdx;
                 Fprev = F;
             }
         }
@@ -648,16 +654,17 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
             const int r = (int)fe0.div(p), c0 = p - r * e[0];
             const int c2 = (int)fe1.div(r), c1 = r - c2 * e[1];
             T L = T(0);
-            L = L - Dk[p];
-            L = L - Dk[512 + p];
-            L = L - Dk[1024 + p];
+            L = L - Dk[9 * (c1 + e[1] * c2) + c0];
+            L = L - Dk[SG_DK_AXIS + 9 * (c0 + e[0] * c2) + c1];
+            L = L - Dk[2 * SG_DK_AXIS + 9 * (c0 + e[0] * c1) + c2];
             const long long g = (org[0] + c0) + gs1 * (org[1] + c1) + gs2 * (org[2] + c2);
             const T o = io.update(g, L, dt);
             if (!sg_isfinite(o)) bad = true;
             mx = sg_max(mx, sg_abs(o));
         }
+        // no trailing barrier: the epilogue's first barrier already follows every thread's last
+        // read of Dk, and the next tile writes Dk only after its own gather barrier
         stage_epilogue(A, w, G, it, mx, bad, red);
-        __syncthreads();  // the next tile overwrites the shared arrays
     }
 }
 

@@ -64,6 +64,9 @@ __device__ __forceinline__ T sg_abs(T v) { return v < T(0) ? -v : v; }
 __device__ __forceinline__ bool sg_isfinite(double v) { return isfinite(v); }
 __device__ __forceinline__ bool sg_isfinite(float v) { return isfinite(v); }
 
+__device__ __forceinline__ double sg_fmax_(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float sg_fmax_(float a, float b) { return fmaxf(a, b); }
+
 // Block-wide max of non-negative values; the result is valid in thread 0.  Contains two
 // barriers, so every thread of the block must call it.
 __device__ __forceinline__ double block_max(double v, double* red) {
@@ -74,6 +77,25 @@ __device__ __forceinline__ double block_max(double v, double* red) {
     if (wid == 0) {
         v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    __syncthreads();
+    return v;
+}
+
+// Block-wide max where any thread's `neg` forces the result to -1 (used to fold the
+// non-finite flag into the alpha reduction); result valid in thread 0; two barriers.
+template <class T>
+__device__ __forceinline__ T block_max(T v, T* red, bool neg) {
+    const unsigned anyneg = __ballot_sync(0xffffffffu, neg);
+    for (int o = 16; o > 0; o >>= 1) v = sg_fmax_(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = anyneg ? T(-1) : v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? red[lane] : T(0);
+        const unsigned n2 = __ballot_sync(0xffffffffu, v < T(0));
+        for (int o = 16; o > 0; o >>= 1) v = sg_fmax_(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (n2) v = T(-1);
     }
     __syncthreads();
     return v;

@@ -323,6 +323,20 @@ def test_error_paths(sg):
         with pytest.raises(P.SgError) as e:
             P.sg_read(h, -1, count=10)
         assert e.value.status == P.SG_ERR_STATE
+        # an infinite value under the CFL rule makes alpha infinite and the step zero: the
+        # call must stop with an error at the first check instead of stepping forever
+        for prec in (P.SG_F64, P.SG_F32):
+            c = make(2, 6, 2, P.SG_PDE_BURGERS, precision=prec, dt_rule=P.SG_DT_CFL)
+            try:
+                g = [np.full(int(np.prod(s)), 0.5) for s in shp]
+                g[0][3] = np.inf
+                P.sg_init_grids(c, np.concatenate(g))
+                with pytest.raises(P.SgError) as e:
+                    P.sg_step(c, 1e6)
+                assert e.value.status == P.SG_ERR_NONFINITE
+                assert P.sg_time(c)[1] <= 16  # at most one captured graph of steps
+            finally:
+                P.sg_destroy(c)
         # the handle stays usable after errors
         P.sg_init(h, P.SG_IC_SINE, (0.5, 1.0, math.pi / 2, 0.0))
         P.sg_step(h, 0.01)
