@@ -348,6 +348,7 @@ sg_status build_tables(sg_ctx* h) {
             if (k < h->dim) {
                 d.n[k] = n[k];
                 d.nt[k] = (n[k] + d.te[k] - 1) / d.te[k];
+                d.ntmag[k] = sg_div_magic64((unsigned)d.nt[k]);
                 d.h[k] = (h->prm.hi[k] - h->prm.lo[k]) / (double)n[k];
                 d.rdx[k] = 1.0 / d.h[k];
                 d.rdxf[k] = (float)d.rdx[k];
@@ -358,6 +359,7 @@ sg_status build_tables(sg_ctx* h) {
                 d.n[k] = 1;
                 d.te[k] = 1;
                 d.nt[k] = 1;
+                d.ntmag[k] = 0;
                 d.h[k] = 1.0;
                 d.rdx[k] = 1.0;
                 d.rdxf[k] = 1.0f;

@@ -105,17 +105,32 @@ __global__ void sg_restrict_sine_kernel(GridDesc G, int dim, double p0, double p
 // If acc != nullptr the result is added, times coeff, into the FP64 accumulator instead
 // (the last prolonged axis, fused with the combination sum of Eq. 13).
 // ------------------------------------------------------------------------------------
+// 2^-e exactly (0 <= e <= 126), built from its bits: no division
+template <class T>
+__device__ __forceinline__ T pow2_neg(int e);
+template <>
+__device__ __forceinline__ float pow2_neg<float>(int e) { return __int_as_float((127 - e) << 23); }
+template <>
+__device__ __forceinline__ double pow2_neg<double>(int e) { return __longlong_as_double((long long)(1023 - e) << 52); }
+
+// r is a power of two: shifts and masks instead of integer division, and s = m / r formed as
+// m 2^-lr, the same value as the quotient (both exact)
 template <class T>
 __device__ __forceinline__ void fine_to_coarse(int jf, int r, int& ic, T& s) {
-    const int i = jf / r, m = jf - i * r;
+    const int lr = __ffs(r) - 1;
+    const int i = jf >> lr, m = jf & (r - 1);
+    const T inv = pow2_neg<T>(lr);
     if (2 * m < r) {
         ic = i;
-        s = (T)m / (T)r;
+        s = (T)m * inv;
     } else {
         ic = i + 1;
-        s = (T)(m - r) / (T)r;
+        s = (T)(m - r) * inv;
     }
 }
+
+// c in [-n, 2n) -> c mod n (a stencil index at most two cells outside [0, n))
+__device__ __forceinline__ int wrap_index(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
 
 template <class T>
 __global__ void sg_prolong_axis_kernel(const T* __restrict__ in, T* __restrict__ out,
@@ -136,9 +151,7 @@ __global__ void sg_prolong_axis_kernel(const T* __restrict__ in, T* __restrict__
         T v[5];
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
-            int c = ic - 2 + m;
-            c %= min_;
-            if (c < 0) c += min_;
+            const int c = wrap_index(ic - 2 + m, min_);
             v[m] = line[(long long)c * below];
         }
         T res;
@@ -158,7 +171,8 @@ __global__ void sg_prolong_axis_kernel(const T* __restrict__ in, T* __restrict__
 // Same arithmetic per output as sg_prolong_axis_kernel.
 template <class T>
 __global__ void sg_prolong_axis2_kernel(const T* __restrict__ in, T* __restrict__ out, long long below, int min_,
-                                        int nf, long long above, int r, double eps, int lagrange) {
+                                        int nf, long long above, int r, double eps, int lagrange,
+                                        unsigned long long nfmag) {
     const T e12 = (T)(12.0 * eps);
     if (below == 1) {
         for (long long hi = blockIdx.y; hi < above; hi += gridDim.y) {
@@ -170,10 +184,7 @@ __global__ void sg_prolong_axis2_kernel(const T* __restrict__ in, T* __restrict_
                 T v[5];
 #pragma unroll
                 for (int m = 0; m < 5; ++m) {
-                    int c = ic - 2 + m;
-                    c %= min_;
-                    if (c < 0) c += min_;
-                    v[m] = line[c];
+                    v[m] = line[wrap_index(ic - 2 + m, min_)];
                 }
                 T res;
                 if constexpr (sizeof(T) == 8) res = Weno<double>::interp(v[0], v[1], v[2], v[3], v[4], s, eps, lagrange);
@@ -185,18 +196,16 @@ __global__ void sg_prolong_axis2_kernel(const T* __restrict__ in, T* __restrict_
     }
     const long long rows = (long long)nf * above;
     for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
-        const int jf = (int)(row % nf);
-        const long long hi = row / nf;
+        // nfmag != 0: rows < 2^32, divide by multiplying
+        const long long hi = nfmag ? (long long)div_mag((unsigned)row, (unsigned)nf, nfmag) : row / nf;
+        const int jf = (int)(row - hi * nf);
         int ic;
         T s;
         fine_to_coarse<T>(jf, r, ic, s);
         int cs[5];
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
-            int c = ic - 2 + m;
-            c %= min_;
-            if (c < 0) c += min_;
-            cs[m] = c;
+            cs[m] = wrap_index(ic - 2 + m, min_);
         }
         const T* base = in + hi * below * min_;
         T* obase = out + (hi * nf + jf) * below;
@@ -247,10 +256,9 @@ struct CombineAcc<float> {
         const float pe = fmaf(cf, v, -p);    // exact product error
         const float s = hi + p;              // two-sum of hi and p
         const float bb = s - hi;
-        float e = (hi - (s - bb)) + (p - bb);
-        e += lo + pe;
-        hi = s + e;                          // renormalise
-        lo = e - (hi - s);
+        const float e = (hi - (s - bb)) + (p - bb);
+        hi = s;                              // hi: the float sum; lo: the sum of its exact errors
+        lo += e + pe;                        // (lo's own rounding is O(u^2) of the result)
     }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
@@ -274,39 +282,46 @@ struct InterpWin<double> {
 
 template <>
 struct InterpWin<float> {
+    // Per centre, the interpolant of Eqs. (8)-(11) is w2 + (s/2) N(s) / D(s) with N cubic and D
+    // quadratic in s: N = sum_k C_k(s) beta_w_k (s_k + s t_k), D = sum_k C_k(s) beta_w_k, where
+    // beta_w_k = prod_{j != k} (eps + beta_j)^2 (up to a common factor) and C_k(s) the linear
+    // weights.  prepare() forms their coefficients once; eval() is two Horner evaluations.
     float w0, w1, w2, w3, w4;
-    float t0, t1, t2, s0, s1, s2, EE0, EE1, EE2;
+    float n0, n1, n2, n3, d0, d1, d2;
     __device__ __forceinline__ void prepare(float eps12, int lagrange) {
-        const float d1 = w1 - w0, d2 = w2 - w1, d3 = w3 - w2, d4 = w4 - w3;
-        t0 = d2 - d1;
-        t1 = d3 - d2;
-        t2 = d4 - d3;
-        s0 = fmaf(3.f, d2, -d1);
-        s1 = d2 + d3;
-        s2 = fmaf(3.f, d3, -d4);
-        if (lagrange) {
-            EE0 = EE1 = EE2 = 1.f;
-        } else {
+        const float d1_ = w1 - w0, d2_ = w2 - w1, d3_ = w3 - w2, d4_ = w4 - w3;
+        const float t0 = d2_ - d1_, t1 = d3_ - d2_, t2 = d4_ - d3_;
+        const float s0 = fmaf(3.f, d2_, -d1_), s1 = d2_ + d3_, s2 = fmaf(3.f, d3_, -d4_);
+        float E0 = 1.f, E1 = 1.f, E2 = 1.f;  // beta_w_k; 1 for Lagrange
+        if (!lagrange) {
             const float e0 = fmaf(13.f * t0, t0, fmaf(3.f * s0, s0, eps12));
             const float e1 = fmaf(13.f * t1, t1, fmaf(3.f * s1, s1, eps12));
             const float e2 = fmaf(13.f * t2, t2, fmaf(3.f * s2, s2, eps12));
-            const float E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
-            EE0 = E1 * E2;
-            EE1 = E0 * E2;
-            EE2 = E0 * E1;
+            const float q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
+            E0 = q1 * q2;
+            E1 = q0 * q2;
+            E2 = q0 * q1;
         }
+        // C_0 = 1/6 - s/4 + s^2/12, C_1 = 2/3 - s^2/6, C_2 = 1/6 + s/4 + s^2/12
+        const float A0 = E0 * s0, A1 = E1 * s1, A2 = E2 * s2;
+        const float B0 = E0 * t0, B1 = E1 * t1, B2 = E2 * t2;
+        const float Ap = A0 + A2, Bp = B0 + B2, Ep = E0 + E2;
+        n0 = fmaf(Ap, 1.f / 6.f, (2.f / 3.f) * A1);
+        n1 = fmaf(Bp, 1.f / 6.f, fmaf(A2 - A0, 0.25f, (2.f / 3.f) * B1));
+        n2 = fmaf(B2 - B0, 0.25f, fmaf(Ap, 1.f / 12.f, (-1.f / 6.f) * A1));
+        n3 = fmaf(Bp, 1.f / 12.f, (-1.f / 6.f) * B1);
+        d0 = fmaf(Ep, 1.f / 6.f, (2.f / 3.f) * E1);
+        d1 = (E2 - E0) * 0.25f;
+        d2 = fmaf(Ep, 1.f / 12.f, (-1.f / 6.f) * E1);
     }
     __device__ __forceinline__ float eval(float s, float, int) const {
         if (s == 0.f) return w2;
-        const float p0 = fmaf(s, t0, s0), p1 = fmaf(s, t1, s1), p2 = fmaf(s, t2, s2);
-        const float C0 = (s - 1.f) * (s - 2.f) * (1.f / 12.f);
-        const float C1 = fmaf(-s, s, 4.f) * (1.f / 6.f);
-        const float C2 = (s + 1.f) * (s + 2.f) * (1.f / 12.f);
-        const float a0 = C0 * EE0, a1 = C1 * EE1, a2 = C2 * EE2;
-        const float num = fmaf(a0, p0, fmaf(a1, p1, a2 * p2));
-        return fmaf(0.5f * s, __fdividef(num, a0 + a1 + a2), w2);
+        const float N = fmaf(fmaf(fmaf(n3, s, n2), s, n1), s, n0);
+        const float D = fmaf(fmaf(d2, s, d1), s, d0);
+        return fmaf(0.5f * s, __fdividef(N, D), w2);
     }
 };
+
 
 template <class T, int J>
 __global__ void __launch_bounds__(256) sg_combine_last_axis_kernel(const CombineGrid* __restrict__ tab, int G,
@@ -334,7 +349,7 @@ __global__ void __launch_bounds__(256) sg_combine_last_axis_kernel(const Combine
                 }
                 // r = 2^lr: fine node jf = i r + m; centre i (2m < r) or i + 1, s = m/r or (m - r)/r
                 const int lr = __ffs(r) - 1;
-                const T inv_r = (T)1 / (T)r;  // exact: r is a power of two
+                const T inv_r = pow2_neg<T>(lr);  // 1 / r exactly (r is a power of two)
                 auto centre = [&](int jf, int& ic, T& s) {
                     const int i = jf >> lr, m = jf & (r - 1);
                     if (2 * m < r) {
@@ -350,10 +365,7 @@ __global__ void __launch_bounds__(256) sg_combine_last_axis_kernel(const Combine
                 centre(j0, cur, s_unused);
                 InterpWin<T> W;
                 {
-                    int c0 = cur - 2;
-                    c0 %= n;
-                    if (c0 < 0) c0 += n;
-                    int c = c0;
+                    int c = wrap_index(cur - 2, n);
                     W.w0 = col[(long long)c * below];
                     if (++c == n) c = 0;
                     W.w1 = col[(long long)c * below];

@@ -29,6 +29,7 @@ struct GridDesc {
     int n[SG_MAXD];      // nodes per axis
     int te[SG_MAXD];     // tile extent per axis
     int nt[SG_MAXD];     // tiles per axis
+    unsigned long long ntmag[SG_MAXD];  // floor((2^64 - 1) / nt) + 1: division-free tile decomposition
     double h[SG_MAXD];   // node spacing (hi-lo)/n
     double rdx[SG_MAXD]; // 1/h
     float rdxf[SG_MAXD]; // (float)(1/h), for the FP32 kernels (no per-tile FP64 conversion)
@@ -40,6 +41,9 @@ struct GridDesc {
     int n_items;
     int pad_;
 };
+
+// Host side: the 64-bit multiplier of GridDesc.ntmag.
+inline unsigned long long sg_div_magic64(unsigned d) { return d <= 1u ? 0ull : ~0ull / d + 1ull; }
 
 struct WorkItem {
     int grid;

@@ -195,7 +195,9 @@ cudaError_t Launch<T>::prolong_axis2(const T* in, T* out, long long below, int m
         grid.x = (unsigned)std::min<long long>((below + 255) / 256, 65535);
         grid.y = (unsigned)std::min<long long>((long long)nf * above, 65535);
     }
-    sg_prolong_axis2_kernel<T><<<grid, 256, 0, s>>>(in, out, below, min_, nf, above, r, eps, lagrange);
+    const unsigned long long rows = (unsigned long long)nf * (unsigned long long)above;
+    const unsigned long long nfmag = rows < (1ull << 32) ? sg_div_magic64((unsigned)nf) : 0ull;
+    sg_prolong_axis2_kernel<T><<<grid, 256, 0, s>>>(in, out, below, min_, nf, above, r, eps, lagrange, nfmag);
     return cudaGetLastError();
 }
 

@@ -173,6 +173,7 @@ extern "C" sg_status sg_step_grid_noalloc(int dim, const long* shape, const doub
         if (k < dim) {
             gd.n[k] = n[k];
             gd.nt[k] = (n[k] + gd.te[k] - 1) / gd.te[k];
+            gd.ntmag[k] = sg_div_magic64((unsigned)gd.nt[k]);
             gd.h[k] = (hi[k] - lo[k]) / (double)n[k];
             gd.rdx[k] = 1.0 / gd.h[k];
             gd.rdxf[k] = (float)gd.rdx[k];
@@ -180,6 +181,7 @@ extern "C" sg_status sg_step_grid_noalloc(int dim, const long* shape, const doub
             ntiles *= gd.nt[k];
         } else {
             gd.n[k] = gd.te[k] = gd.nt[k] = 1;
+            gd.ntmag[k] = 0;
             gd.h[k] = gd.rdx[k] = 1.0;
             gd.rdxf[k] = 1.0f;
         }

@@ -158,14 +158,12 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
         int org[3] = {0, 0, 0}, e[3] = {1, 1, 1}, n[3] = {1, 1, 1};
         long long gs[3] = {1, 0, 0};
         {
-            unsigned tt = (unsigned)w.tile;
+            int tc[D];
+            tile_coords<D>(G, (unsigned)w.tile, tc);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                const unsigned nt = (unsigned)G->nt[k];
-                const unsigned tc = tt % nt;
-                tt /= nt;
                 n[k] = G->n[k];
-                org[k] = (int)tc * G->te[k];
+                org[k] = tc[k] * G->te[k];
                 e[k] = min(G->te[k], n[k] - org[k]);
             }
             if (D >= 2) gs[1] = n[0];
@@ -478,14 +476,12 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
 
         int org[3], e[3], n[3];
         {
-            unsigned tt = (unsigned)w.tile;
+            int tc[3];
+            tile_coords<3>(G, (unsigned)w.tile, tc);
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const unsigned nt = (unsigned)G->nt[k];
-                const unsigned tc = tt % nt;
-                tt /= nt;
                 n[k] = G->n[k];
-                org[k] = (int)tc * G->te[k];
+                org[k] = tc[k] * G->te[k];
                 e[k] = min(G->te[k], n[k] - org[k]);
             }
         }
@@ -707,14 +703,12 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
         FDiv fd[D];
         int P = 1;
         {
-            unsigned tt = (unsigned)w.tile;
+            int tc[D];
+            tile_coords<D>(G, (unsigned)w.tile, tc);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                const unsigned nt = (unsigned)G->nt[k];
-                const unsigned tc = tt % nt;
-                tt /= nt;
                 nn[k] = G->n[k];
-                org[k] = (int)tc * G->te[k];
+                org[k] = tc[k] * G->te[k];
                 ext[k] = min(G->te[k], nn[k] - org[k]);
                 gstr[k] = k == 0 ? 1LL : gstr[k - 1] * (long long)nn[k - 1];
                 fd[k].init((unsigned)ext[k]);

@@ -18,14 +18,46 @@
 // ceil(2^32 / d)).  x (d - 1) < 2^32 guarantees floor(x m / 2^32) = floor(x / d).
 // ceil(2^32 / d) = floor((2^32 - 1) / d) + 1 for d >= 2, so one 32-bit division suffices
 // (a 64-bit one is emulated, partly on GB300's slow FP64 pipe).
+// Multipliers of FDiv for divisors up to 1024, so that setting one up needs no division:
+// integer division by a runtime value goes through float conversions, which GB300 runs on
+// its (slow) FP64 pipe.
+struct SgMagic {
+    unsigned v[1025];
+};
+constexpr SgMagic sg_make_magic() {
+    SgMagic t{};
+    for (unsigned d = 0; d <= 1024; ++d) t.v[d] = d <= 1 ? 0u : 0xFFFFFFFFu / d + 1u;
+    return t;
+}
+static __constant__ SgMagic sg_magic = sg_make_magic();
+
 struct FDiv {
     unsigned m, d;
     __device__ __forceinline__ void init(unsigned dd) {
         d = dd;
-        m = dd <= 1u ? 0u : 0xFFFFFFFFu / dd + 1u;
+        m = dd <= 1024u ? sg_magic.v[dd] : 0xFFFFFFFFu / dd + 1u;
     }
     __device__ __forceinline__ unsigned div(unsigned x) const { return d <= 1u ? x : __umulhi(x, m); }
 };
+
+// x / d for any 32-bit x with the 64-bit multiplier mag = floor((2^64 - 1) / d) + 1 made on the
+// host (exact: x (mag d - 2^64) < 2^64 for x, d < 2^32).
+__device__ __forceinline__ unsigned div_mag(unsigned x, unsigned d, unsigned long long mag) {
+    return d <= 1u ? x : (unsigned)__umul64hi((unsigned long long)x, mag);
+}
+
+// Work item tile -> tile coordinates along the first D axes of grid G (tile index row-major,
+// axis 0 fastest).
+template <int D>
+__device__ __forceinline__ void tile_coords(const GridDesc* G, unsigned tile, int (&tc)[D]) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const unsigned nt = (unsigned)G->nt[k];
+        const unsigned q = div_mag(tile, nt, G->ntmag[k]);
+        tc[k] = (int)(tile - q * nt);
+        tile = q;
+    }
+}
 
 __device__ __forceinline__ unsigned long long dbits(double v) {
     return (unsigned long long)__double_as_longlong(v);
@@ -285,9 +317,11 @@ struct Weno<float> {
         const float s0 = fmaf(3.f, d2, -d1), s1 = d2 + d3, s2 = fmaf(3.f, d3, -d4);
         // P_k(s) - c = (s/2) (s_k + s t_k)
         const float p0 = fmaf(s, t0, s0), p1 = fmaf(s, t1, s1), p2 = fmaf(s, t2, s2);
-        const float C0 = (s - 1.f) * (s - 2.f) * (1.f / 12.f);
-        const float C1 = fmaf(-s, s, 4.f) * (1.f / 6.f);
-        const float C2 = (s + 1.f) * (s + 2.f) * (1.f / 12.f);
+        // linear weights C_k(s) of Eq. (9): (s-1)(s-2)/12, (4-s^2)/6, (s+1)(s+2)/12
+        const float ss = s * s;
+        const float q = fmaf(ss, 1.f / 12.f, 1.f / 6.f);
+        const float C0 = fmaf(s, -0.25f, q), C2 = fmaf(s, 0.25f, q);
+        const float C1 = fmaf(ss, -1.f / 6.f, 2.f / 3.f);
         float w0 = C0, w1 = C1, w2 = C2;
         if (!lagrange) {
             const float e0 = fmaf(13.f * t0, t0, fmaf(3.f * s0, s0, eps12));
