@@ -65,6 +65,11 @@ struct StageIO<float> {
         D2 = (float*)G->u2;
         Cc = (float*)G->u3;
     }
+    // the arrays whose sum is the stencil input: U, and D1 (stage 1) or D2 (stage 2)
+    __device__ __forceinline__ void stencil_src(const float*& a, const float*& b) const {
+        a = U;
+        b = stage == 0 ? nullptr : (stage == 1 ? Ub : D2);
+    }
     __device__ __forceinline__ float load(long long g) const {
         if (stage == 0) return U[g];
         if (stage == 1) return U[g] + Ub[g];
@@ -90,6 +95,56 @@ struct StageIO<float> {
         Ub[g] = s;
         Cc[g] = err;
         return s;
+    }
+    // true if every array of the stage starts on a 16-byte boundary (update4 may be used)
+    __device__ __forceinline__ bool aligned16() const {
+        const unsigned long long a = reinterpret_cast<unsigned long long>(U) | reinterpret_cast<unsigned long long>(Ub) |
+                                     reinterpret_cast<unsigned long long>(D2) | reinterpret_cast<unsigned long long>(Cc);
+        return (a & 15) == 0;
+    }
+    // update() of four consecutive points g..g+3 (g a multiple of 4) with 16-byte accesses;
+    // the same arithmetic per point
+    __device__ __forceinline__ float4 update4(long long g, const float (&L)[4], float dt) const {
+        const float4 u = *reinterpret_cast<const float4*>(U + g);
+        const float uu[4] = {u.x, u.y, u.z, u.w};
+        float o[4];
+        if (stage == 0) {
+            float dd[4];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                dd[l] = dt * L[l];
+                o[l] = uu[l] + dd[l];
+            }
+            *reinterpret_cast<float4*>(Ub + g) = make_float4(dd[0], dd[1], dd[2], dd[3]);
+        } else if (stage == 1) {
+            const float4 b = *reinterpret_cast<const float4*>(Ub + g);
+            const float bb[4] = {b.x, b.y, b.z, b.w};
+            float nd[4];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const float d = dt * L[l];
+                nd[l] = 0.25f * (bb[l] + d);
+                o[l] = uu[l] + nd[l];
+            }
+            *reinterpret_cast<float4*>(D2 + g) = make_float4(nd[0], nd[1], nd[2], nd[3]);
+        } else {
+            const float4 d2 = *reinterpret_cast<const float4*>(D2 + g);
+            const float4 c = *reinterpret_cast<const float4*>(Cc + g);
+            const float dd2[4] = {d2.x, d2.y, d2.z, d2.w}, cc[4] = {c.x, c.y, c.z, c.w};
+            float er[4];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const float d = dt * L[l];
+                const float y = fmaf(2.f / 3.f, dd2[l] + d, cc[l]);
+                const float sm = uu[l] + y;
+                const float bb = sm - uu[l];
+                er[l] = (uu[l] - (sm - bb)) + (y - bb);
+                o[l] = sm;
+            }
+            *reinterpret_cast<float4*>(Ub + g) = make_float4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<float4*>(Cc + g) = make_float4(er[0], er[1], er[2], er[3]);
+        }
+        return make_float4(o[0], o[1], o[2], o[3]);
     }
 };
 
@@ -497,14 +552,121 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
         fe0.init(e[0]);
         fe1.init(e[1]);
 
-        // ---- 1) padded box: interior rows with the x halos, then the y and z halos.  Tiles are
-        // at most 8^3, so each thread has at most 5 + 2 + 2 values to fetch: all loads are
-        // issued first (unrolled gather), then split and stored (scatter).
+        // split of one loaded stencil value into the box
+        auto put = [&](int bidx, T v) {
+            if (burgers) {
+                if constexpr (sizeof(T) == 8) {
+                    double fp, fm;
+                    Weno<double>::split(v, alpha_b, 0.0, 1, fp, fm);
+                    bp[bidx] = fp;
+                    bm[bidx] = fm;
+                } else {
+                    float fp, fm;
+                    Weno<float>::split_burgers(v, half_alpha, fp, fm);
+                    bp[bidx] = fp;
+                    bm[bidx] = fm;
+                }
+            } else {
+                bp[bidx] = v;
+            }
+        };
+        // FP32, tile 8 wide at an x origin and row length that are multiples of 4, on grids whose
+        // arrays start on a 16-byte boundary (grids are packed back to back, so not all do):
+        // every row segment the box needs is read as 16-byte float4 loads (4 per x-row with its
+        // halos, 2 per halo row), wrapping whole chunks at the faces
+        bool vec = false;
+        const T* A0 = nullptr;
+        const T* A1 = nullptr;
+        if constexpr (sizeof(T) == 4) {
+            io.stencil_src(A0, A1);
+            const unsigned long long align = reinterpret_cast<unsigned long long>(A0) |
+                                             reinterpret_cast<unsigned long long>(A1);
+            vec = e[0] == 8 && (org[0] & 3) == 0 && (n[0] & 3) == 0 && (align & 15) == 0;
+        }
+        if constexpr (sizeof(T) == 4) {
+            if (vec) {
+                const int nr0 = e[1] * e[2] * 4, nr1 = 12 * e[2], nr2 = 12 * e[1];
+                const int ntask = nr0 + nr1 + nr2;
+                // task t: one float4 chunk; its box index with two flags (drop the chunk's first
+                // value: x = -4; drop its last: x = 11) packed above bit 16
+                auto chunk = [&](int t, long long& g) -> int {
+                    int gx, gy, gz, bx, y, z, flags = 0;
+                    if (t < nr0) {
+                        const int c = t & 3, r = t >> 2;
+                        z = (int)fe1.div(r);
+                        y = r - z * e[1];
+                        bx = 4 * c - 1;  // box x of the chunk's first value (x = 4c - 4)
+                        flags = (c == 0 ? 1 : 0) | (c == 3 ? 2 : 0);
+                        gx = org[0] + 4 * c - 4;
+                        gx = gx < 0 ? gx + n[0] : (gx >= n[0] ? gx - n[0] : gx);
+                        gy = org[1] + y;
+                        gz = org[2] + z;
+                    } else if (t < nr0 + nr1) {
+                        const int q = t - nr0, c = q & 1, r = q >> 1;
+                        z = r / 6;
+                        const int h = r - z * 6;
+                        y = h < 3 ? h - 3 : e[1] + h - 3;
+                        bx = 4 * c + 3;
+                        gx = org[0] + 4 * c;
+                        gy = org[1] + y;
+                        gy = gy < 0 ? gy + n[1] : (gy >= n[1] ? gy - n[1] : gy);
+                        gz = org[2] + z;
+                    } else {
+                        const int q = t - nr0 - nr1, c = q & 1, r = q >> 1;
+                        const int h = (int)fe1.div(r);
+                        y = r - h * e[1];
+                        z = h < 3 ? h - 3 : e[2] + h - 3;
+                        bx = 4 * c + 3;
+                        gx = org[0] + 4 * c;
+                        gy = org[1] + y;
+                        gz = org[2] + z;
+                        gz = gz < 0 ? gz + n[2] : (gz >= n[2] ? gz - n[2] : gz);
+                    }
+                    g = gx + gs1 * gy + gs2 * gz;
+                    return (bx + 1 + B0 * ((y + 3) + B1 * (z + 3))) | (flags << 16);  // +1: >= 0
+                };
+                auto fetch = [&](long long g) {
+                    float4 v = *reinterpret_cast<const float4*>(A0 + g);
+                    if (A1) {
+                        const float4 d = *reinterpret_cast<const float4*>(A1 + g);
+                        v.x += d.x;
+                        v.y += d.y;
+                        v.z += d.z;
+                        v.w += d.w;
+                    }
+                    return v;
+                };
+                auto store = [&](int code, const float4& v) {
+                    const int b = (code & 0xFFFF) - 1;
+                    if (!(code & (1 << 16))) put(b, v.x);
+                    put(b + 1, v.y);
+                    put(b + 2, v.z);
+                    if (!(code & (2 << 16))) put(b + 3, v.w);
+                };
+                // at most 3 chunks per thread: two in flight, then the third
+                {
+                    const int t0 = tid, t1 = tid + SG_NT3;
+                    long long g0 = 0, g1 = 0;
+                    const int c0 = t0 < ntask ? chunk(t0, g0) : -1;
+                    const int c1 = t1 < ntask ? chunk(t1, g1) : -1;
+                    float4 v0, v1;
+                    if (c0 >= 0) v0 = fetch(g0);
+                    if (c1 >= 0) v1 = fetch(g1);
+                    if (c0 >= 0) store(c0, v0);
+                    if (c1 >= 0) store(c1, v1);
+                }
+                for (int t = tid + 2 * SG_NT3; t < ntask; t += SG_NT3) {
+                    long long g;
+                    const int c = chunk(t, g);
+                    store(c, fetch(g));
+                }
+            }
+        }
         constexpr int M0 = (14 * 64 + SG_NT3 - 1) / SG_NT3, M1 = (8 * 6 * 8 + SG_NT3 - 1) / SG_NT3;
         constexpr int MT = M0 + 2 * M1;
         T val[MT];
         int bid[MT];
-        {
+        if (!vec) {
             const int n0 = R0 * e[1] * e[2];
 #pragma unroll
             for (int j = 0; j < M0; ++j) {
@@ -553,26 +715,8 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
                 }
             }
 #pragma unroll
-            for (int j = 0; j < MT; ++j) {
-                const int bidx = bid[j];
-                if (bidx < 0) continue;
-                const T v = val[j];
-                if (burgers) {
-                    if constexpr (sizeof(T) == 8) {
-                        double fp, fm;
-                        Weno<double>::split(v, alpha_b, 0.0, 1, fp, fm);
-                        bp[bidx] = fp;
-                        bm[bidx] = fm;
-                    } else {
-                        float fp, fm;
-                        Weno<float>::split_burgers(v, half_alpha, fp, fm);
-                        bp[bidx] = fp;
-                        bm[bidx] = fm;
-                    }
-                } else {
-                    bp[bidx] = v;
-                }
-            }
+            for (int j = 0; j < MT; ++j)
+                if (bid[j] >= 0) put(bid[j], val[j]);
         }
         __syncthreads();
 
@@ -646,7 +790,35 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
         // ---- 3) L = ((0 - D_0) - D_1) - D_2, stage update, alpha of the result
         T mx = T(0);
         bool bad = false;
-        for (int p = tid; p < P; p += SG_NT3) {
+        bool vec_upd = false;
+        if constexpr (sizeof(T) == 4) vec_upd = vec && io.aligned16();
+        if constexpr (sizeof(T) == 4) {
+            if (vec_upd) {  // four consecutive x points per thread, 16-byte loads and stores
+                const int ngrp = 2 * e[1] * e[2];
+                for (int t = tid; t < ngrp; t += SG_NT3) {
+                    const int c0 = 4 * (t & 1), r = t >> 1;
+                    const int c2 = (int)fe1.div(r), c1 = r - c2 * e[1];
+                    float L[4];
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        float a = 0.f;
+                        a = a - Dk[9 * (c1 + e[1] * c2) + c0 + l];
+                        a = a - Dk[SG_DK_AXIS + 9 * (c0 + l + e[0] * c2) + c1];
+                        a = a - Dk[2 * SG_DK_AXIS + 9 * (c0 + l + e[0] * c1) + c2];
+                        L[l] = a;
+                    }
+                    const long long g = (org[0] + c0) + gs1 * (org[1] + c1) + gs2 * (org[2] + c2);
+                    const float4 o = io.update4(g, L, dt);
+                    const float oo[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        if (!sg_isfinite(oo[l])) bad = true;
+                        mx = sg_max(mx, sg_abs(oo[l]));
+                    }
+                }
+            }
+        }
+        for (int p = vec_upd ? P : tid; p < P; p += SG_NT3) {
             const int r = (int)fe0.div(p), c0 = p - r * e[0];
             const int c2 = (int)fe1.div(r), c1 = r - c2 * e[1];
             T L = T(0);
