@@ -461,27 +461,27 @@ struct SweepSide<float> {
         T0 = fmaf(13.f * t0, t0, eps12);
     }
     // numerator and denominator of fhat - c (as in Weno<float>::side)
+    // With E_k = (12 eps + 12 beta_k)^2, the weights are proportional to
+    // a_0 = E_1 E_2 / 6, a_1 = E_0 E_2, a_2 = E_0 E_1 / 2 (linear scheme: all E_k = 1, giving
+    // 0.1, 0.6, 0.3), and num = sum a_k p_k, den = sum a_k are formed factored:
+    // num = E_1 (E_2 p_0/6 + E_0 p_2/2) + E_0 E_2 p_1,  den = E_1 (E_2/6 + E_0/2) + E_0 E_2.
     __device__ __forceinline__ void value(int linear, float& num, float& den) const {
-        const float p0 = fmaf(5.f / 6.f, d2, (-1.f / 3.f) * d1);
+        const float p0s = fmaf(5.f / 36.f, d2, (-1.f / 18.f) * d1);  // p_0 / 6
         const float p1 = fmaf(1.f / 6.f, d2, (1.f / 3.f) * d3);
-        const float p2 = fmaf(2.f / 3.f, d3, (-1.f / 6.f) * d4);
-        float a0, a1, a2;
-        if (linear) {
-            a0 = 0.1f;
-            a1 = 0.6f;
-            a2 = 0.3f;
-        } else {
+        const float p2h = fmaf(1.f / 3.f, d3, (-1.f / 12.f) * d4);   // p_2 / 2
+        float E0 = 1.f, E1 = 1.f, E2 = 1.f;
+        if (!linear) {
             const float s0 = fmaf(3.f, d2, -d1), s1 = d2 + d3, s2 = fmaf(3.f, d3, -d4);
             const float e0 = fmaf(3.f * s0, s0, T0);
             const float e1 = fmaf(3.f * s1, s1, T1);
             const float e2 = fmaf(3.f * s2, s2, T2);
-            const float E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
-            a0 = (1.f / 6.f) * (E1 * E2);
-            a1 = E0 * E2;
-            a2 = 0.5f * (E0 * E1);
+            E0 = e0 * e0;
+            E1 = e1 * e1;
+            E2 = e2 * e2;
         }
-        num = fmaf(a0, p0, fmaf(a1, p1, a2 * p2));
-        den = a0 + a1 + a2;
+        const float X = E0 * E2;
+        num = fmaf(E1, fmaf(E2, p0s, E0 * p2h), X * p1);
+        den = fmaf(E1, fmaf(E2, 1.f / 6.f, 0.5f * E0), X);
     }
 };
 

@@ -245,28 +245,26 @@ template <>
 struct Weno<float> {
     static __device__ __forceinline__ void side(float a, float b, float c, float d, float e,
                                                 float eps12, int linear, float& num, float& den) {
+        // weights proportional to E_1 E_2 / 6, E_0 E_2, E_0 E_1 / 2 with E_k = (12 eps + 12 beta_k)^2
+        // (linear scheme: E_k = 1), num and den formed factored (as SweepSide<float>::value)
         const float d1 = b - a, d2 = c - b, d3 = d - c, d4 = e - d;
-        const float p0 = fmaf(5.f / 6.f, d2, (-1.f / 3.f) * d1);
+        const float p0s = fmaf(5.f / 36.f, d2, (-1.f / 18.f) * d1);  // p_0 / 6
         const float p1 = fmaf(1.f / 6.f, d2, (1.f / 3.f) * d3);
-        const float p2 = fmaf(2.f / 3.f, d3, (-1.f / 6.f) * d4);
-        float a0, a1, a2;
-        if (linear) {
-            a0 = 0.1f;
-            a1 = 0.6f;
-            a2 = 0.3f;
-        } else {
+        const float p2h = fmaf(1.f / 3.f, d3, (-1.f / 12.f) * d4);   // p_2 / 2
+        float E0 = 1.f, E1 = 1.f, E2 = 1.f;
+        if (!linear) {
             const float t0 = d2 - d1, t1 = d3 - d2, t2 = d4 - d3;
             const float s0 = fmaf(3.f, d2, -d1), s1 = d2 + d3, s2 = fmaf(3.f, d3, -d4);
             const float e0 = fmaf(13.f * t0, t0, fmaf(3.f * s0, s0, eps12));
             const float e1 = fmaf(13.f * t1, t1, fmaf(3.f * s1, s1, eps12));
             const float e2 = fmaf(13.f * t2, t2, fmaf(3.f * s2, s2, eps12));
-            const float E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
-            a0 = (1.f / 6.f) * (E1 * E2);
-            a1 = E0 * E2;
-            a2 = 0.5f * (E0 * E1);
+            E0 = e0 * e0;
+            E1 = e1 * e1;
+            E2 = e2 * e2;
         }
-        num = fmaf(a0, p0, fmaf(a1, p1, a2 * p2));
-        den = a0 + a1 + a2;
+        const float X = E0 * E2;
+        num = fmaf(E1, fmaf(E2, p0s, E0 * p2h), X * p1);
+        den = fmaf(E1, fmaf(E2, 1.f / 6.f, 0.5f * E0), X);
     }
 
     // Burgers split, Eq. (7): f^{+-} = u (u/4 +- alpha/2).

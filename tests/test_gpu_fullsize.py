@@ -78,14 +78,23 @@ def test_full_run_fp32_batched_matches_fp64_accuracy(sg, name):
     W = inputs.WORKLOADS[name]
     d, Nf = W.dim, W.nr << W.nl
     _, flat = _sample(d, Nf, 4096, seed=10 + d)
+    import time
     res = {}
     for prec, exe in ((P.SG_F64, P.SG_PLAIN), (P.SG_F32, P.SG_BATCHED)):
         h = make(d, W.nr, W.nl, W.pde, precision=prec, exec=exe, dt_rule=W.dt_rule, dt_coef=W.dt_coef)
         try:
             P.sg_init(h, P.SG_IC_SINE, W.ic)
+            t0 = time.perf_counter()
             t = P.sg_step(h, W.t_end)
+            t1 = time.perf_counter()
             assert t == W.t_end
             P.sg_prolong_combine(h)
+            t2 = time.perf_counter()
+            pts = sum(int(np.prod(x)) for x in _levels(h, d)[1])
+            print("%s %s: %d points, %d steps, step %.2f s (%.3g point-updates/s, first call includes "
+                  "autotuning), combine %.2f s" % (name, "f64 plain" if prec == P.SG_F64 else "f32 batched", pts,
+                                                   P.sg_time(h)[1], t1 - t0, pts * P.sg_time(h)[1] / (t1 - t0),
+                                                   t2 - t1))
             res[prec] = (P.sg_reduce(h, -1, P.SG_REDUCE_L1_EXACT), P.sg_reduce(h, -1, P.SG_REDUCE_LINF_EXACT),
                          P.sg_read_points(h, P.SG_WHICH_COMBINED, flat), P.sg_time(h)[1])
         finally:
