@@ -38,6 +38,12 @@ struct StageIO<double> {
         un = (const double*)G->u0;
         out = (double*)(s == 0 ? G->u1 : s == 1 ? G->u2 : G->u0);
     }
+    // advances every pointer by o elements (tile-relative indexing)
+    __device__ __forceinline__ void shift(long long o) {
+        in += o;
+        un += o;
+        out += o;
+    }
     __device__ __forceinline__ double load(long long g) const { return in[g]; }
     // writes the stage result at g; returns it (for the alpha reduction)
     __device__ __forceinline__ double update(long long g, double L, double dt) const {
@@ -64,6 +70,13 @@ struct StageIO<float> {
         Ub = (float*)(parity ? G->u0 : G->u1);
         D2 = (float*)G->u2;
         Cc = (float*)G->u3;
+    }
+    // advances every pointer by o elements (tile-relative indexing)
+    __device__ __forceinline__ void shift(long long o) {
+        U += o;
+        Ub += o;
+        D2 += o;
+        Cc += o;
     }
     // the arrays whose sum is the stencil input: U, and D1 (stage 1) or D2 (stage 2)
     __device__ __forceinline__ void stencil_src(const float*& a, const float*& b) const {
@@ -540,7 +553,10 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
                 e[k] = min(G->te[k], n[k] - org[k]);
             }
         }
-        const long long gs1 = n[0], gs2 = (long long)n[0] * n[1];
+        // global indices below are 32-bit offsets from the tile's first point (a grid holds
+        // fewer than 2^31 points): one 64-bit address computation per tile
+        const int n0 = n[0], n01 = n[0] * n[1];
+        io.shift(org[0] + (long long)n0 * org[1] + (long long)n01 * org[2]);
         const int P = e[0] * e[1] * e[2];
         const int R0 = e[0] + 6;                 // valid row length along x
         const int B0 = R0 | 1;                   // odd row stride
@@ -622,7 +638,7 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
                         gz = org[2] + z;
                         gz = gz < 0 ? gz + n[2] : (gz >= n[2] ? gz - n[2] : gz);
                     }
-                    g = gx + gs1 * gy + gs2 * gz;
+                    g = (gx - org[0]) + n0 * (gy - org[1]) + n01 * (gz - org[2]);
                     return (bx + 1 + B0 * ((y + 3) + B1 * (z + 3))) | (flags << 16);  // +1: >= 0
                 };
                 auto fetch = [&](long long g) {
@@ -667,19 +683,19 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
         T val[MT];
         int bid[MT];
         if (!vec) {
-            const int n0 = R0 * e[1] * e[2];
+            const int nv0 = R0 * e[1] * e[2];
 #pragma unroll
             for (int j = 0; j < M0; ++j) {
                 const int q = tid + j * SG_NT3;
                 bid[j] = -1;
-                if (q < n0) {
+                if (q < nv0) {
                     const int r = (int)fR0.div(q), x = q - r * R0;
                     const int z = (int)fe1.div(r), y = r - z * e[1];
                     int gx = org[0] + x - 3;
                     if (gx < 0) gx += n[0];
                     else if (gx >= n[0]) gx -= n[0];
                     bid[j] = x + B0 * ((y + 3) + B1 * (z + 3));
-                    val[j] = io.load(gx + gs1 * (org[1] + y) + gs2 * (org[2] + z));
+                    val[j] = io.load((gx - org[0]) + n0 * y + n01 * z);
                 }
             }
             const int n1 = e[0] * 6 * e[2];
@@ -695,7 +711,7 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
                     if (gy < 0) gy += n[1];
                     else if (gy >= n[1]) gy -= n[1];
                     bid[M0 + j] = (x + 3) + B0 * ((y + 3) + B1 * (z + 3));
-                    val[M0 + j] = io.load((org[0] + x) + gs1 * gy + gs2 * (org[2] + z));
+                    val[M0 + j] = io.load(x + n0 * (gy - org[1]) + n01 * z);
                 }
             }
             const int n2 = e[0] * e[1] * 6;
@@ -711,7 +727,7 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
                     if (gz < 0) gz += n[2];
                     else if (gz >= n[2]) gz -= n[2];
                     bid[M0 + M1 + j] = (x + 3) + B0 * ((y + 3) + B1 * (z + 3));
-                    val[M0 + M1 + j] = io.load((org[0] + x) + gs1 * (org[1] + y) + gs2 * gz);
+                    val[M0 + M1 + j] = io.load(x + n0 * y + n01 * (gz - org[2]));
                 }
             }
 #pragma unroll
@@ -807,8 +823,7 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
                         a = a - Dk[2 * SG_DK_AXIS + 9 * (c0 + l + e[0] * c1) + c2];
                         L[l] = a;
                     }
-                    const long long g = (org[0] + c0) + gs1 * (org[1] + c1) + gs2 * (org[2] + c2);
-                    const float4 o = io.update4(g, L, dt);
+                    const float4 o = io.update4(c0 + n0 * c1 + n01 * c2, L, dt);
                     const float oo[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
                     for (int l = 0; l < 4; ++l) {
@@ -825,8 +840,7 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
             L = L - Dk[9 * (c1 + e[1] * c2) + c0];
             L = L - Dk[SG_DK_AXIS + 9 * (c0 + e[0] * c2) + c1];
             L = L - Dk[2 * SG_DK_AXIS + 9 * (c0 + e[0] * c1) + c2];
-            const long long g = (org[0] + c0) + gs1 * (org[1] + c1) + gs2 * (org[2] + c2);
-            const T o = io.update(g, L, dt);
+            const T o = io.update(c0 + n0 * c1 + n01 * c2, L, dt);
             if (!sg_isfinite(o)) bad = true;
             mx = sg_max(mx, sg_abs(o));
         }
