@@ -188,6 +188,21 @@ __device__ __forceinline__ void stage_epilogue(const StageArgs& A, const WorkIte
     if (threadIdx.x == 0 && it == G->first_item) A.alpha[w.grid * 3 + (A.stage + 2) % 3] = 0ull;
 }
 
+// Barrier-free variant for the sweep kernel: each warp folds its max |u| into the alpha slot
+// with one atomicMax (max is exact and order-independent, so the slot gets the same value) and
+// raises the non-finite flag itself; a warp holding a non-finite value leaves the slot alone.
+template <class T>
+__device__ __forceinline__ void stage_epilogue_warp(const StageArgs& A, const WorkItem& w, const GridDesc* G,
+                                                    int it, T mx, bool bad) {
+    const unsigned anybad = __ballot_sync(0xffffffffu, bad);
+    if (A.phys.pde == 1) {
+        for (int o = 16; o > 0; o >>= 1) mx = sg_fmax_(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0 && !anybad) atomicMax(A.alpha + w.grid * 3 + (A.stage + 1) % 3, alpha_enc(mx));
+    }
+    if ((threadIdx.x & 31) == 0 && anybad) atomicOr(A.flags + SG_FLAG_NONFINITE, 1);
+    if (threadIdx.x == 0 && it == G->first_item) A.alpha[w.grid * 3 + (A.stage + 2) % 3] = 0ull;
+}
+
 // ------------------------------------------------------------------------------------
 // d <= 3: padded-box kernel.  Per tile: one load of the tile with a 3-point halo on each face
 // (periodic wrap), the LF split computed once per loaded value (Burgers: the split is the
@@ -525,7 +540,6 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
     T* bp = reinterpret_cast<T*>(sg_smem_raw);   // f^+ (Burgers) or u (advection)
     T* bm = bp + A.box_elems;                     // f^-
     T* Dk = bm + A.box_elems;                     // 3 x SG_DK_AXIS flux differences
-    __shared__ T red[SG_NT / 32];
 
     const int tid = threadIdx.x;
     const PhysParams& ph = A.phys;
@@ -844,9 +858,9 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
             if (!sg_isfinite(o)) bad = true;
             mx = sg_max(mx, sg_abs(o));
         }
-        // no trailing barrier: the epilogue's first barrier already follows every thread's last
-        // read of Dk, and the next tile writes Dk only after its own gather barrier
-        stage_epilogue(A, w, G, it, mx, bad, red);
+        // no barrier here: the next tile writes the box only after this tile's sweep barrier
+        // (the box is not read in the update) and Dk only after its own gather barrier
+        stage_epilogue_warp(A, w, G, it, mx, bad);
     }
 }
 
