@@ -844,8 +844,8 @@ sg_status prolong_combine_fused_t(sg_ctx* h, CombineBuffers& cb) {
             for (int j = 0; j < k; ++j) lo *= m[j];
             for (int j = k + 1; j < d; ++j) hi *= m[j];
             T* dst = a + 1 == axes.size() ? cb.pool.as<T>() + slot[g] : bufs[a & 1];
-            SG_CUDA(sg::Launch<T>::prolong_axis2(src, dst, lo, (int)m[k], (int)Nf, hi, 1 << (h->nl - gd.lev[k]),
-                                                 h->prm.eps, h->prm.prolong, h->stream));
+            SG_CUDA(sg::Launch<T>::prolong_axis_win(src, dst, lo, (int)m[k], (int)Nf, hi, 1 << (h->nl - gd.lev[k]),
+                                                    h->prm.eps, h->prm.prolong, h->stream));
             h->launches += 1;
             m[k] = Nf;
             src = dst;
@@ -856,8 +856,13 @@ sg_status prolong_combine_fused_t(sg_ctx* h, CombineBuffers& cb) {
         tab[g].coeff = gd.coeff;
     }
     SG_CUDA(cudaMemcpyAsync(cb.tab.p, tab.data(), sizeof(CombineGrid) * tab.size(), cudaMemcpyHostToDevice, h->stream));
+    bool exact = true;  // |c| = C(d-1, q) a power of two for every grid (d <= 3)
+    for (int g = 0; g < h->G; ++g) {
+        const double a = std::fabs(h->coeff[g]);
+        exact = exact && a >= 1.0 && std::ldexp(1.0, std::ilogb(a)) == a;
+    }
     SG_CUDA(sg::Launch<T>::combine_last_axis(cb.tab.as<CombineGrid>(), h->G, h->uhat.as<double>(), below, (int)Nf,
-                                             h->prm.eps, h->prm.prolong, h->stream));
+                                             exact ? 1 : 0, h->prm.eps, h->prm.prolong, h->stream));
     h->launches += 1;
     SG_CUDA(cudaStreamSynchronize(h->stream));
     h->combined = true;

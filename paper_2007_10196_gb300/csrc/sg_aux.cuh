@@ -244,6 +244,7 @@ struct CombineAcc;
 template <>
 struct CombineAcc<double> {
     double a = 0.0;
+    template <bool EXACT = false>
     __device__ __forceinline__ void add(double c, double v) { a = a + c * v; }
     __device__ __forceinline__ double value() const { return a; }
 };
@@ -251,9 +252,11 @@ struct CombineAcc<double> {
 template <>
 struct CombineAcc<float> {
     float hi = 0.f, lo = 0.f;
+    // EXACT: every coefficient is a power of two (d <= 3), so c v is exact and has no error term
+    template <bool EXACT = false>
     __device__ __forceinline__ void add(float cf, float v) {  // cf: |c| <= C(5, 2), exact in float
         const float p = cf * v;
-        const float pe = fmaf(cf, v, -p);    // exact product error
+        const float pe = EXACT ? 0.f : fmaf(cf, v, -p);    // exact product error
         const float s = hi + p;              // two-sum of hi and p
         const float bb = s - hi;
         const float e = (hi - (s - bb)) + (p - bb);
@@ -323,7 +326,7 @@ struct InterpWin<float> {
 };
 
 
-template <class T, int J>
+template <class T, int J, bool EXACT>
 __global__ void __launch_bounds__(256) sg_combine_last_axis_kernel(const CombineGrid* __restrict__ tab, int G,
                                                                     double* __restrict__ uhat, long long below,
                                                                     int nf, double eps, int lagrange) {
@@ -343,7 +346,7 @@ __global__ void __launch_bounds__(256) sg_combine_last_axis_kernel(const Combine
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
                         const int jf = j0 + j;
-                        if (jf < nf) acc[j].add(cT, col[(long long)jf * below]);
+                        if (jf < nf) acc[j].template add<EXACT>(cT, col[(long long)jf * below]);
                     }
                     continue;
                 }
@@ -395,7 +398,7 @@ __global__ void __launch_bounds__(256) sg_combine_last_axis_kernel(const Combine
                         W.prepare(e12, lagrange);
                         cur = ic;
                     }
-                    acc[j].add(cT, W.eval(s, eps, lagrange));
+                    acc[j].template add<EXACT>(cT, W.eval(s, eps, lagrange));
                 }
             }
 #pragma unroll
@@ -404,6 +407,82 @@ __global__ void __launch_bounds__(256) sg_combine_last_axis_kernel(const Combine
                 if (jf < nf) uhat[lo + (long long)jf * below] = acc[j].value();
             }
         }
+    }
+}
+
+// One prolongation axis, J consecutive fine outputs per thread: the five coarse values around
+// the current centre slide along the axis and their s-independent part is formed once per
+// centre (InterpWin::prepare), so the r fine nodes that share a centre pay only for eval().
+// Axis with stride `below` > 1: threads run along `below`, blockIdx.y over (above, chunk of J
+// fine nodes).  below == 1: threads run over the chunks of a row, blockIdx.y over `above`.
+template <class T, int J>
+__global__ void __launch_bounds__(256) sg_prolong_axis_win_kernel(const T* __restrict__ in, T* __restrict__ out,
+                                                                  long long below, int n, int nf, long long above,
+                                                                  int r, double eps, int lagrange) {
+    const T e12 = (T)(12.0 * eps);
+    const int nchunks = (nf + J - 1) / J;
+    const int lr = __ffs(r) - 1;
+    const T inv_r = pow2_neg<T>(lr);
+    auto centre = [&](int jf, int& ic, T& s) {  // as fine_to_coarse
+        const int i = jf >> lr, m = jf & (r - 1);
+        if (2 * m < r) {
+            ic = i;
+            s = (T)m * inv_r;
+        } else {
+            ic = i + 1;
+            s = (T)(m - r) * inv_r;
+        }
+    };
+    auto run = [&](const T* col, T* ocol, long long stride, int j0) {
+        int cur;
+        T s0;
+        centre(j0, cur, s0);
+        InterpWin<T> W;
+        int c = wrap_index(cur - 2, n);
+        W.w0 = col[c * stride];
+        if (++c == n) c = 0;
+        W.w1 = col[c * stride];
+        if (++c == n) c = 0;
+        W.w2 = col[c * stride];
+        if (++c == n) c = 0;
+        W.w3 = col[c * stride];
+        if (++c == n) c = 0;
+        W.w4 = col[c * stride];
+        W.prepare(e12, lagrange);
+#pragma unroll 1
+        for (int j = 0; j < J; ++j) {
+            const int jf = j0 + j;
+            if (jf >= nf) break;
+            int ic;
+            T s;
+            centre(jf, ic, s);
+            if (ic != cur) {  // centres advance by one coarse node at a time (r >= 2)
+                W.w0 = W.w1;
+                W.w1 = W.w2;
+                W.w2 = W.w3;
+                W.w3 = W.w4;
+                int cn = ic + 2;
+                if (cn >= n) cn -= n;
+                W.w4 = col[cn * stride];
+                W.prepare(e12, lagrange);
+                cur = ic;
+            }
+            ocol[jf * stride] = W.eval(s, (T)eps, lagrange);
+        }
+    };
+    if (below == 1) {
+        for (long long hi = blockIdx.y; hi < above; hi += gridDim.y)
+            for (int ch = blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks; ch += gridDim.x * blockDim.x)
+                run(in + hi * n, out + hi * nf, 1, ch * J);
+        return;
+    }
+    const long long rows = above * nchunks;
+    for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
+        const long long hi = row / nchunks;  // once per block row
+        const int ch = (int)(row - hi * nchunks);
+        for (long long lo = blockIdx.x * (long long)blockDim.x + threadIdx.x; lo < below;
+             lo += (long long)gridDim.x * blockDim.x)
+            run(in + hi * below * n + lo, out + hi * below * nf + lo, below, ch * J);
     }
 }
 

@@ -42,11 +42,16 @@ struct Launch {
     static cudaError_t accumulate(const T* u, double* acc, double coeff, long long n, cudaStream_t s);
     // out[j] = u[idx[j]], j < n (device arrays; indices already checked)
     static cudaError_t gather(const T* u, const long long* idx, T* out, long long n, cudaStream_t s);
+    // One prolongation axis, J = 8 consecutive fine nodes per thread sharing the coarse window.
+    static cudaError_t prolong_axis_win(const T* in, T* out, long long below, int min_, int nf, long long above,
+                                        int r, double eps, int lagrange, cudaStream_t s);
     // One prolongation axis (2-D indexed form of prolong_axis without the accumulation).
     static cudaError_t prolong_axis2(const T* in, T* out, long long below, int min_, int nf, long long above,
                                      int r, double eps, int lagrange, cudaStream_t s);
     // uhat = sum_g c_g P_{d-1} I_g over the G entries of tab (device array), written once.
+    // exact_coeffs: every |c_g| is a power of two (products c_g v are exact in the FP32 sum)
     static cudaError_t combine_last_axis(const CombineGrid* tab, int G, double* uhat, long long below, int nf,
+                                         int exact_coeffs,
                                          double eps, int lagrange, cudaStream_t s);
     // FP64 reduction of n values u (+ comp if non-null); partial holds >= 1024 doubles.
     static cudaError_t reduce(const T* u, const T* comp, long long n, int kind, const ExactSpec& X,

@@ -185,6 +185,23 @@ cudaError_t Launch<T>::gather(const T* u, const long long* idx, T* out, long lon
 }
 
 template <class T>
+cudaError_t Launch<T>::prolong_axis_win(const T* in, T* out, long long below, int min_, int nf, long long above,
+                                        int r, double eps, int lagrange, cudaStream_t s) {
+    constexpr int J = 8;
+    const long long nchunks = (nf + J - 1) / J;
+    dim3 grid;
+    if (below == 1) {
+        grid.x = (unsigned)std::min<long long>((nchunks + 255) / 256, 65535);
+        grid.y = (unsigned)std::min<long long>(above, 65535);
+    } else {
+        grid.x = (unsigned)std::min<long long>((below + 255) / 256, 65535);
+        grid.y = (unsigned)std::min<long long>(above * nchunks, 65535);
+    }
+    sg_prolong_axis_win_kernel<T, J><<<grid, 256, 0, s>>>(in, out, below, min_, nf, above, r, eps, lagrange);
+    return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t Launch<T>::prolong_axis2(const T* in, T* out, long long below, int min_, int nf, long long above,
                                      int r, double eps, int lagrange, cudaStream_t s) {
     dim3 grid;
@@ -203,11 +220,13 @@ cudaError_t Launch<T>::prolong_axis2(const T* in, T* out, long long below, int m
 
 template <class T>
 cudaError_t Launch<T>::combine_last_axis(const CombineGrid* tab, int G, double* uhat, long long below, int nf,
+                                         int exact_coeffs,
                                          double eps, int lagrange, cudaStream_t s) {
     constexpr int J = 8;
     dim3 grid((unsigned)std::min<long long>((below + 255) / 256, 65535),
               (unsigned)std::min<long long>((nf + J - 1) / J, 65535));
-    sg_combine_last_axis_kernel<T, J><<<grid, 256, 0, s>>>(tab, G, uhat, below, nf, eps, lagrange);
+    if (exact_coeffs) sg_combine_last_axis_kernel<T, J, true><<<grid, 256, 0, s>>>(tab, G, uhat, below, nf, eps, lagrange);
+    else sg_combine_last_axis_kernel<T, J, false><<<grid, 256, 0, s>>>(tab, G, uhat, below, nf, eps, lagrange);
     return cudaGetLastError();
 }
 
