@@ -327,13 +327,31 @@ struct InterpWin<float> {
 
 
 template <class T, int J, bool EXACT>
-__global__ void __launch_bounds__(256) sg_combine_last_axis_kernel(const CombineGrid* __restrict__ tab, int G,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) sg_combine_last_axis_kernel(const CombineGrid* __restrict__ tab, int G,
                                                                     double* __restrict__ uhat, long long below,
                                                                     int nf, double eps, int lagrange) {
     const T e12 = (T)(12.0 * eps);
     const int nchunks = (nf + J - 1) / J;
+    // centre index and offset s of the chunk's J fine nodes for every refinement ratio
+    // r = 2^lr (lr <= 16): the same for all grids with that ratio and all columns of the block
+    __shared__ T s_tab[17 * J];
+    __shared__ int c_tab[17 * J];
     for (int ch = blockIdx.y; ch < nchunks; ch += gridDim.y) {
         const int j0 = ch * J;
+        __syncthreads();  // the previous chunk's readers are done
+        for (int t = threadIdx.x; t < 17 * J; t += blockDim.x) {
+            const int lr = t / J, jf = j0 + (t - lr * J), r = 1 << lr;
+            const int i = jf >> lr, m = jf & (r - 1);  // jf = i r + m; centre i or i + 1
+            const T inv_r = pow2_neg<T>(lr);
+            if (2 * m < r) {
+                c_tab[t] = i;
+                s_tab[t] = (T)m * inv_r;
+            } else {
+                c_tab[t] = i + 1;
+                s_tab[t] = (T)(m - r) * inv_r;
+            }
+        }
+        __syncthreads();
         for (long long lo = blockIdx.x * (long long)blockDim.x + threadIdx.x; lo < below;
              lo += (long long)gridDim.x * blockDim.x) {
             CombineAcc<T> acc[J];
@@ -350,22 +368,11 @@ __global__ void __launch_bounds__(256) sg_combine_last_axis_kernel(const Combine
                     }
                     continue;
                 }
-                // r = 2^lr: fine node jf = i r + m; centre i (2m < r) or i + 1, s = m/r or (m - r)/r
+                // r = 2^lr: centres and offsets of the chunk's nodes from the block's table
                 const int lr = __ffs(r) - 1;
-                const T inv_r = pow2_neg<T>(lr);  // 1 / r exactly (r is a power of two)
-                auto centre = [&](int jf, int& ic, T& s) {
-                    const int i = jf >> lr, m = jf & (r - 1);
-                    if (2 * m < r) {
-                        ic = i;
-                        s = (T)m * inv_r;
-                    } else {
-                        ic = i + 1;
-                        s = (T)(m - r) * inv_r;
-                    }
-                };
-                int cur;
-                T s_unused;
-                centre(j0, cur, s_unused);
+                const T* st = s_tab + lr * J;
+                const int* ct = c_tab + lr * J;
+                int cur = ct[0];
                 InterpWin<T> W;
                 {
                     int c = wrap_index(cur - 2, n);
@@ -384,9 +391,8 @@ __global__ void __launch_bounds__(256) sg_combine_last_axis_kernel(const Combine
                 for (int j = 0; j < J; ++j) {
                     const int jf = j0 + j;
                     if (jf >= nf) break;
-                    int ic;
-                    T s;
-                    centre(jf, ic, s);
+                    const int ic = ct[j];
+                    const T s = st[j];
                     if (ic != cur) {  // centres advance by one coarse node at a time (r >= 2)
                         W.w0 = W.w1;
                         W.w1 = W.w2;
