@@ -16,11 +16,9 @@
 
 // Exact unsigned division by a run-time divisor d <= 2^16 for x < 2^16 (multiply-high by
 // ceil(2^32 / d)).  x (d - 1) < 2^32 guarantees floor(x m / 2^32) = floor(x / d).
-// ceil(2^32 / d) = floor((2^32 - 1) / d) + 1 for d >= 2, so one 32-bit division suffices
-// (a 64-bit one is emulated, partly on GB300's slow FP64 pipe).
-// Multipliers of FDiv for divisors up to 1024, so that setting one up needs no division:
-// integer division by a runtime value goes through float conversions, which GB300 runs on
-// its (slow) FP64 pipe.
+// ceil(2^32 / d) = floor((2^32 - 1) / d) + 1 for d >= 2.
+// Multipliers of FDiv for divisors up to 1024, so that setting one up needs no division (an
+// integer division by a run-time value is a long instruction sequence with a reciprocal).
 struct SgMagic {
     unsigned v[1025];
 };
