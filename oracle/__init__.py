@@ -53,7 +53,7 @@ class Problem(C.Structure):
     ]
 
 
-ADVECTION, BURGERS = 0, 1
+ADVECTION, BURGERS, VLASOV = 0, 1, 2
 WENO5, LINEAR5 = 0, 1
 PROLONG_WENO5, PROLONG_LAGRANGE5 = 0, 1
 DT_POW53, DT_CFL = 0, 1
@@ -87,6 +87,9 @@ def lib():
             "orc_prolong_point": (C.c_double, [P, _ip, _dp, _lp]),
             "orc_combine_point": (C.c_double, [P, C.c_int, _ip, _dp, _dp, _lp]),
             "orc_mass": (C.c_double, [P, _ip, _dp]),
+            "orc_efield": (None, [P, _ip, _dp, _dp]),
+            "orc_restrict_landau": (None, [P, _ip, C.c_double, C.c_double, _dp]),
+            "orc_field_energy": (C.c_double, [P, _ip, _dp]),
             "orc_exact_sine": (C.c_double, [P] + [C.c_double] * 4 + [_dp, C.c_double]),
             "orc_error_norms": (None, [P, _dp] + [C.c_double] * 5
                                 + [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -248,3 +251,22 @@ def error_norms(p, uhat, b, a, w, phi, t):
     lib().orc_error_norms(C.byref(p), np.ascontiguousarray(uhat, np.float64), b, a, w, phi, t,
                           C.byref(l1), C.byref(li))
     return float(l1.value), float(li.value)
+
+
+def efield(p: Problem, levels, u):
+    """Vlasov-Poisson field E_i of one grid (pde VLASOV)."""
+    n0 = int(p.nr) << int(levels[0])
+    E = np.empty(n0, dtype=np.float64)
+    lib().orc_efield(C.byref(p), _lev(levels), np.ascontiguousarray(u, np.float64), E)
+    return E
+
+
+def restrict_landau(p: Problem, levels, a, k):
+    """f_0 = (1 + a cos(k x)) exp(-v^2/2) / sqrt(2 pi) on one grid (pde VLASOV)."""
+    u = np.empty(int(np.prod(shape(p, levels))), dtype=np.float64)
+    lib().orc_restrict_landau(C.byref(p), _lev(levels), float(a), float(k), u)
+    return u
+
+
+def field_energy(p: Problem, levels, u) -> float:
+    return float(lib().orc_field_energy(C.byref(p), _lev(levels), np.ascontiguousarray(u, np.float64)))

@@ -32,6 +32,15 @@
  *  - prolongation runs axis 0, 1, ..., d-1 (Section 2.2.1);
  *  - the combination sums grids in enumeration order (q = 0, 1, ...; lexicographic
  *    levels within each q, l_0 most significant), into an accumulator that starts at 0.
+ * Vlasov-Poisson (pde 2; not in the paper, the 1D1V kinetic workload run on the same
+ * method):
+ *  - x is periodic as above; v nodes are v_j = lo_1 + j h_v, j = 0..n_v-1, and f is zero
+ *    outside them (zero inflow): stencils and interpolation read 0 beyond either end;
+ *  - rho_i = h_v sum_j f_ij (j ascending); E solves dE/dx = rho - mean(rho) by the
+ *    trapezoid rule, E_0 = 0, E_i = E_{i-1} + h_x ((rho_{i-1} + rho_i) / 2 - mean(rho)),
+ *    then the mean of E is subtracted (periodic E with zero mean);
+ *  - E is recomputed from the input of every RK stage; the LF alpha of axis 0 is
+ *    max_j |v_j| of the grid, of axis 1 max_i |E_i|.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -43,7 +52,9 @@ typedef struct {
     int dim;           /* d, 1..6 */
     int nr;            /* N_r, root cells per axis */
     int nl;            /* N_L, finest level */
-    int pde;           /* 0: linear advection f_k = a_k u;  1: Burgers f_k = u^2/2 */
+    int pde;           /* 0: linear advection f_k = a_k u;  1: Burgers f_k = u^2/2;
+                          2: Vlasov-Poisson (d = 2, axis 0 = x, axis 1 = v): f_x = v u,
+                          f_v = E(x) u, E from the grid's own density (see orc_efield) */
     int scheme;        /* 0: WENO5-JS weights (5);  1: fifth-order linear scheme, w_r = d_r */
     int prolong;       /* 0: WENO5 interpolation (11);  1: fifth-order Lagrange (8) */
     double eps;        /* epsilon of (5) and (9) */
@@ -153,6 +164,38 @@ double orc_weno5_side(double a, double b, double c, double d, double e, double e
     return (al0 * q0 + al1 * q1 + al2 * q2) / (al0 + al1 + al2);
 }
 
+/* Vlasov-Poisson field of one grid (pde 2): E_i, i = 0..n_x-1, from the density of u. */
+void orc_efield(const orc_problem *P, const int *levels, const double *u, double *E)
+{
+    long n[ORC_MAXD];
+    long i, j;
+    double hx, hv, mean = 0.0, meanE = 0.0;
+    double *rho;
+    grid_points(P, levels, n);
+    hx = spacing(P, 0, n[0]);
+    hv = spacing(P, 1, n[1]);
+    rho = (double *)malloc(sizeof(double) * n[0]);
+    for (i = 0; i < n[0]; ++i) {
+        double sum = 0.0;
+        for (j = 0; j < n[1]; ++j) sum = sum + u[i + n[0] * j];
+        rho[i] = hv * sum;
+    }
+    for (i = 0; i < n[0]; ++i) mean = mean + rho[i];
+    mean = mean / (double)n[0];
+    E[0] = 0.0;
+    for (i = 1; i < n[0]; ++i) E[i] = E[i - 1] + hx * (0.5 * (rho[i - 1] + rho[i]) - mean);
+    for (i = 0; i < n[0]; ++i) meanE = meanE + E[i];
+    meanE = meanE / (double)n[0];
+    for (i = 0; i < n[0]; ++i) E[i] = E[i] - meanE;
+    free(rho);
+}
+
+/* Velocity node j of a Vlasov-Poisson grid. */
+static double vnode(const orc_problem *P, long j, long nv)
+{
+    return P->lo[1] + (double)j * spacing(P, 1, nv);
+}
+
 /* Flux of one axis, Eq. (1): f_k(u) = a_k u (advection) or u^2/2 (Burgers). */
 static double flux(const orc_problem *P, int k, double u)
 {
@@ -173,11 +216,92 @@ double orc_lf_alpha(const orc_problem *P, const int *levels, const double *u, in
     long n[ORC_MAXD];
     long N = grid_points(P, levels, n), p;
     double a = 0.0;
+    if (P->pde == 2) {  /* axis 0: max |v_j|; axis 1: max |E_i| */
+        if (k == 0) {
+            for (p = 0; p < n[1]; ++p) {
+                double s = fabs(vnode(P, p, n[1]));
+                if (s > a) a = s;
+            }
+        } else {
+            double *E = (double *)malloc(sizeof(double) * n[0]);
+            orc_efield(P, levels, u, E);
+            for (p = 0; p < n[0]; ++p) {
+                double s = fabs(E[p]);
+                if (s > a) a = s;
+            }
+            free(E);
+        }
+        return a;
+    }
     for (p = 0; p < N; ++p) {
         double s = wave_speed(P, k, u[p]);
         if (s > a) a = s;
     }
     return a;
+}
+
+/* Vlasov-Poisson spatial operator: as below, with the line's own wave speed (v_j along x,
+ * E_i along v) in the split (7), and zero values beyond the ends of v (n_v + 1 interfaces). */
+static void vp_operator(const orc_problem *P, const int *levels, const double *u, const long *n,
+                        double *L)
+{
+    long nx = n[0], nv = n[1], i, j;
+    double *E = (double *)malloc(sizeof(double) * nx);
+    double ax = orc_lf_alpha(P, levels, u, 0);
+    double av;
+    double rdx = 1.0 / spacing(P, 0, nx), rdv = 1.0 / spacing(P, 1, nv);
+    long nmax = nx > nv ? nx : nv;
+    double *fp = (double *)malloc(sizeof(double) * (nmax + 6));
+    double *fm = (double *)malloc(sizeof(double) * (nmax + 6));
+    double *F = (double *)malloc(sizeof(double) * (nmax + 1));
+    orc_efield(P, levels, u, E);
+    av = 0.0;
+    for (i = 0; i < nx; ++i)
+        if (fabs(E[i]) > av) av = fabs(E[i]);
+    /* axis 0 (x, periodic): line j has speed v_j */
+    for (j = 0; j < nv; ++j) {
+        double a = vnode(P, j, nv);
+        for (i = 0; i < nx; ++i) {
+            double uj = u[i + nx * j];
+            double fj = a * uj;
+            fp[i] = 0.5 * (fj + ax * uj);
+            fm[i] = 0.5 * (fj - ax * uj);
+        }
+        for (i = 0; i < nx; ++i) {
+            long im2 = (i - 2 + 2 * nx) % nx, im1 = (i - 1 + nx) % nx;
+            long ip1 = (i + 1) % nx, ip2 = (i + 2) % nx, ip3 = (i + 3) % nx;
+            double fplus = orc_weno5_side(fp[im2], fp[im1], fp[i], fp[ip1], fp[ip2], P->eps, P->scheme == 1);
+            double fminus = orc_weno5_side(fm[ip3], fm[ip2], fm[ip1], fm[i], fm[im1], P->eps, P->scheme == 1);
+            F[i] = fplus + fminus;
+        }
+        for (i = 0; i < nx; ++i) {
+            long il = (i - 1 + nx) % nx;
+            L[i + nx * j] = L[i + nx * j] - (F[i] - F[il]) * rdx;
+        }
+    }
+    /* axis 1 (v, zero beyond the ends): line i has speed E_i; fp/fm hold nodes -3..nv+2
+       at offset 3, interfaces m + 1/2 for m = -1..nv-1 at F[m + 1] */
+    for (i = 0; i < nx; ++i) {
+        double a = E[i];
+        long m;
+        for (m = -3; m < nv + 3; ++m) {
+            double uj = (m < 0 || m >= nv) ? 0.0 : u[i + nx * m];
+            double fj = a * uj;
+            fp[m + 3] = 0.5 * (fj + av * uj);
+            fm[m + 3] = 0.5 * (fj - av * uj);
+        }
+        for (m = -1; m < nv; ++m) {
+            const double *P5 = fp + m + 3, *M5 = fm + m + 3;
+            double fplus = orc_weno5_side(P5[-2], P5[-1], P5[0], P5[1], P5[2], P->eps, P->scheme == 1);
+            double fminus = orc_weno5_side(M5[3], M5[2], M5[1], M5[0], M5[-1], P->eps, P->scheme == 1);
+            F[m + 1] = fplus + fminus;
+        }
+        for (m = 0; m < nv; ++m) L[i + nx * m] = L[i + nx * m] - (F[m + 1] - F[m]) * rdv;
+    }
+    free(E);
+    free(fp);
+    free(fm);
+    free(F);
 }
 
 /* ------------------------------------------------------------------------------------
@@ -193,6 +317,10 @@ void orc_spatial_operator(const orc_problem *P, const int *levels, const double 
     stride[0] = 1;
     for (k = 1; k < P->dim; ++k) stride[k] = stride[k - 1] * n[k - 1];
     for (p = 0; p < N; ++p) L[p] = 0.0;
+    if (P->pde == 2) {
+        vp_operator(P, levels, u, n, L);
+        return;
+    }
 
     for (k = 0; k < P->dim; ++k) {
         long nk = n[k], sk = stride[k], i, line;
@@ -349,6 +477,35 @@ void orc_restrict_sine(const orc_problem *P, const int *levels, double b, double
     }
 }
 
+/* Landau-damping initial condition of the Vlasov-Poisson workload (pde 2):
+ * f_0(x, v) = (1 + a cos(k x)) exp(-v^2 / 2) / sqrt(2 pi) at the nodes of one grid. */
+void orc_restrict_landau(const orc_problem *P, const int *levels, double a, double kx, double *u)
+{
+    long n[ORC_MAXD], i, j;
+    grid_points(P, levels, n);
+    for (j = 0; j < n[1]; ++j) {
+        double v = vnode(P, j, n[1]);
+        double m = exp(-0.5 * (v * v)) / sqrt(2.0 * 3.14159265358979323846);
+        for (i = 0; i < n[0]; ++i) {
+            double x = P->lo[0] + (double)i * spacing(P, 0, n[0]);
+            u[i + n[0] * j] = (1.0 + a * cos(kx * x)) * m;
+        }
+    }
+}
+
+/* Electric field energy of one grid, (1/2) sum_i E_i^2 h_x (pde 2). */
+double orc_field_energy(const orc_problem *P, const int *levels, const double *u)
+{
+    long n[ORC_MAXD], i;
+    double s = 0.0, *E;
+    grid_points(P, levels, n);
+    E = (double *)malloc(sizeof(double) * n[0]);
+    orc_efield(P, levels, u, E);
+    for (i = 0; i < n[0]; ++i) s = s + E[i] * E[i];
+    free(E);
+    return 0.5 * s * spacing(P, 0, n[0]);
+}
+
 /* ------------------------------------------------------------------------------------
  * One-dimensional fifth-order interpolation at x = x_i + s h, s in [-1/2, 1/2),
  * Section 2.2.1, Eqs. (8)-(11).  (a..e) = (u_{i-2}, ..., u_{i+2}).
@@ -442,7 +599,16 @@ void orc_prolong_grid(const orc_problem *P, const int *levels, const double *u, 
                 long ic;
                 double s;
                 fine_to_coarse(jf, r, &ic, &s);
-                {
+                if (P->pde == 2 && k == 1) {  /* v: zero beyond the ends */
+                    double v5[5];
+                    int t;
+                    for (t = 0; t < 5; ++t) {
+                        long c = ic - 2 + t;
+                        v5[t] = (c < 0 || c >= Min) ? 0.0 : line[c * below];
+                    }
+                    oline[jf * below] = orc_weno5_interp(v5[0], v5[1], v5[2], v5[3], v5[4], s, P->eps,
+                                                         P->prolong == 1);
+                } else {
                     double a = line[((ic - 2) % Min + Min) % Min * below];
                     double b = line[((ic - 1) % Min + Min) % Min * below];
                     double c = line[((ic) % Min + Min) % Min * below];
@@ -516,7 +682,16 @@ static double prolong_rec(const orc_problem *P, const int *levels, const long *n
         return prolong_rec(P, levels, n, u, k - 1, J, ci);
     }
     for (t = 0; t < 5; ++t) {
-        ci[k] = (((ic - 2 + t) % n[k]) + n[k]) % n[k];
+        if (P->pde == 2 && k == 1) {  /* v: zero beyond the ends */
+            long c = ic - 2 + t;
+            if (c < 0 || c >= n[k]) {
+                v[t] = 0.0;
+                continue;
+            }
+            ci[k] = c;
+        } else {
+            ci[k] = (((ic - 2 + t) % n[k]) + n[k]) % n[k];
+        }
         v[t] = prolong_rec(P, levels, n, u, k - 1, J, ci);
     }
     return orc_weno5_interp(v[0], v[1], v[2], v[3], v[4], s, P->eps, P->prolong == 1);

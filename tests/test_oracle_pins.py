@@ -459,3 +459,78 @@ def test_burgers_convergence_order_single_grid(orc):
         errs.append(np.abs(out[0].reshape(N, N) - ex).mean())
     order = math.log2(errs[0] / errs[1])
     assert 4.3 < order < 6.5, errs
+
+
+# --------------------------------------------------------------------------------------
+# Vlasov-Poisson workload (1D1V Landau damping; not in the paper): field solve, steady
+# states, zero-inflow prolongation and the linear damping rate
+# --------------------------------------------------------------------------------------
+VP_LO, VP_HI = [0.0, -2 * math.pi], [4 * math.pi, 2 * math.pi]
+
+
+def _vp(orc, nr, nl, **kw):
+    return orc.problem(2, nr, nl, pde=orc.VLASOV, eps=EPS, lo=VP_LO, hi=VP_HI, **kw)
+
+
+def test_vlasov_field_solve_second_order(orc):
+    """rho = h_v sum_j f = 1 + a cos(k x) (up to the Maxwellian's truncated tail) gives
+    E = (a/k) sin(k x); the trapezoid integration converges at second order."""
+    errs = []
+    for n in (32, 64, 128):
+        p = _vp(orc, n, 0)
+        u = orc.restrict_landau(p, [0, 0], 0.05, 0.5)
+        E = orc.efield(p, [0, 0], u)
+        x = np.arange(n) * (4 * math.pi / n)
+        errs.append(np.max(np.abs(E - 0.1 * np.sin(0.5 * x))))
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
+
+
+def test_vlasov_uniform_maxwellian_is_steady(orc):
+    """a = 0: the density is uniform, so E vanishes up to the rounding of the mean, and f is
+    independent of x: L(f) vanishes to rounding (the x fluxes cancel exactly)."""
+    p = _vp(orc, 16, 0)
+    u = orc.restrict_landau(p, [0, 0], 0.0, 0.5)
+    assert np.max(np.abs(orc.efield(p, [0, 0], u))) < 1e-13
+    L = orc.spatial_operator(p, [0, 0], u).reshape(16, 16)
+    assert np.max(np.abs(L)) < 1e-13
+    # with E ~ 0 the operator is the x-transport alone, which cancels exactly on each v line
+    p2 = orc.problem(2, 16, 0, pde=orc.ADVECTION, eps=EPS, lo=VP_LO, hi=VP_HI, adv=(1.0, 0.0))
+    assert np.all(orc.spatial_operator(p2, [0, 0], u) == 0.0)
+
+
+def test_vlasov_zero_inflow_prolongation_matches_periodic_inside(orc):
+    """For data that vanish within five cells of both v ends, the zero-inflow prolongation
+    along v equals the periodic one (a different code path: the wrap-around branch)."""
+    rng = np.random.default_rng(21)
+    nr, nl = 10, 3
+    pv = _vp(orc, nr, nl)
+    pp = orc.problem(2, nr, nl, pde=orc.ADVECTION, eps=EPS, lo=VP_LO, hi=VP_HI)
+    lev, co = orc.grid_set(2, nl)
+    grids = []
+    for l in lev:
+        n0, n1 = orc.shape(pv, l)
+        g = rng.normal(size=(n1, n0))
+        g[:5, :] = 0.0
+        g[-5:, :] = 0.0
+        grids.append(g.reshape(-1))
+    assert np.array_equal(orc.combine(pv, lev, co, grids), orc.combine(pp, lev, co, grids))
+
+
+def test_vlasov_landau_damping_rate_and_mass(orc):
+    """Linear Landau damping, k = 0.5, a = 0.01: the field amplitude decays at the rate of
+    linear theory, 0.1533 (the root of the dispersion relation), within 3% on a 64^2 grid;
+    mass is conserved up to the Maxwellian's outflow at |v| = 2 pi (~1e-9)."""
+    p = _vp(orc, 64, 0)
+    lev = [0, 0]
+    u = orc.restrict_landau(p, lev, 0.01, 0.5)
+    m0 = orc.mass(p, lev, u)
+    ts, amp, t = [], [], 0.0
+    for _ in range(40):
+        out, _, t = orc.solve(p, [lev], [u], t + 0.5, t0=t, rule=orc.DT_CFL, cfl=0.4)
+        u = out[0]
+        ts.append(t)
+        amp.append(0.5 * math.log(orc.field_energy(p, lev, u)))
+    assert abs(orc.mass(p, lev, u) - m0) < 1e-8 * m0
+    pk = [i for i in range(1, len(amp) - 1) if amp[i] > amp[i - 1] and amp[i] > amp[i + 1]]
+    rate = -np.polyfit(np.array(ts)[pk], np.array(amp)[pk], 1)[0]
+    assert abs(rate - 0.1533) < 0.03 * 0.1533, rate
