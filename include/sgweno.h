@@ -45,9 +45,15 @@ typedef enum {
     SG_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
 } sg_status;
 
-/* PDE of Eq. (1): linear advection f_k(u) = a_k u, or Burgers f_k(u) = u^2/2 on every axis. */
-enum { SG_PDE_ADVECTION = 0, SG_PDE_BURGERS = 1 };
-/* Boundary conditions: periodic only. */
+/* PDE of Eq. (1): linear advection f_k(u) = a_k u, or Burgers f_k(u) = u^2/2 on every axis.
+ * SG_PDE_VLASOV: the 1D1V Vlasov-Poisson system f_t + v f_x + E(x) f_v = 0 (not in the paper;
+ * the kinetic workload run on the same method), dim = 2 with axis 0 = x (periodic) and axis 1
+ * = v (f = 0 beyond the v nodes: zero inflow; bc is ignored).  Every component grid carries
+ * its own field: rho_i = h_v sum_j f_ij, E from dE/dx = rho - mean(rho) integrated by the
+ * trapezoid rule from E_0 = 0 and shifted to zero mean, recomputed at every RK stage; the LF
+ * alpha of Eq. (7) is max|v_j| along x and max|E_i| along v. */
+enum { SG_PDE_ADVECTION = 0, SG_PDE_BURGERS = 1, SG_PDE_VLASOV = 2 };
+/* Boundary conditions: periodic (SG_PDE_VLASOV: zero inflow in v, implied). */
 enum { SG_BC_PERIODIC = 0 };
 /* Precision of the component-grid states and the WENO arithmetic.  The combination sum
  * (the finest-grid accumulator) and every reduction are FP64 in both. */
@@ -77,15 +83,18 @@ enum { SG_DT_POW53 = 0, SG_DT_CFL = 1 };
  * SG_STAGE_SWEEP: d = 3 only -- one thread per grid line of an 8 x 8 x 8 tile, sweeping it
  *                 with a register window; tile_points is ignored. */
 enum { SG_STAGE_AUTO = 0, SG_STAGE_TILED = 1, SG_STAGE_SWEEP = 2 };
-/* Initial condition kinds for sg_init. SG_IC_SINE: u_0(x) = p0 + p1 sin(p2 (x_0+...+x_{d-1}) + p3). */
-enum { SG_IC_SINE = 0 };
+/* Initial condition kinds for sg_init. SG_IC_SINE: u_0(x) = p0 + p1 sin(p2 (x_0+...+x_{d-1}) + p3).
+ * SG_IC_LANDAU (SG_PDE_VLASOV only, 2 parameters a, k): f_0 = (1 + a cos(k x)) exp(-v^2/2)/sqrt(2 pi). */
+enum { SG_IC_SINE = 0, SG_IC_LANDAU = 1 };
 /* Reductions (FP64).  MASS = sum u prod h, ENERGY = sum u^2 prod h, MIN/MAX of the values;
  * L1_EXACT = mean |u - u_exact|, LINF_EXACT = max |u - u_exact| against the exact solution of
  * the SG_IC_SINE initial condition at the current time (advection: translation; Burgers:
  * characteristic solution by Newton's method, valid before the shock time). */
+/* FIELD_ENERGY (SG_PDE_VLASOV only): (1/2) sum_i E_i^2 h_x of the field of grid `which` or of
+ * the combined solution, E as described for SG_PDE_VLASOV. */
 enum {
     SG_REDUCE_MASS = 0, SG_REDUCE_ENERGY = 1, SG_REDUCE_MIN = 2, SG_REDUCE_MAX = 3,
-    SG_REDUCE_L1_EXACT = 4, SG_REDUCE_LINF_EXACT = 5
+    SG_REDUCE_L1_EXACT = 4, SG_REDUCE_LINF_EXACT = 5, SG_REDUCE_FIELD_ENERGY = 6
 };
 
 #define SG_MAX_DIM 6

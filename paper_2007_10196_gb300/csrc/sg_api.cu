@@ -151,6 +151,8 @@ struct sg_ctx {
     std::vector<long long> offset;  // element offset of each grid inside a state region
     long long total_pts = 0;
     DevBuf arena;  // state regions u0, u1, u2 (and u3 = C for FP32), each all grids concatenated
+    DevBuf efield; // Vlasov-Poisson: E of every grid (n_0 values each), grids concatenated
+    std::vector<long long> ef_offset;
     long long box_elems = 0;  // stage kernel: elements of one padded box (d <= 3)
     size_t smem = 0;          // stage kernel: dynamic shared memory per block
     // device tables (single handle or batch)
@@ -338,6 +340,7 @@ sg_status build_tables(sg_ctx* h) {
         d.u1 = keep.empty() ? base + region + (size_t)h->offset[g] * h->esize : keep[g].second;
         d.u2 = base + 2 * region + (size_t)h->offset[g] * h->esize;
         d.u3 = h->esize == 4 ? base + 3 * region + (size_t)h->offset[g] * h->esize : nullptr;
+        d.ef = h->pde == SG_PDE_VLASOV ? h->efield.as<char>() + (size_t)h->ef_offset[g] * h->esize : nullptr;
         d.npts = h->npts[g];
         int n[SG_MAXD] = {1, 1, 1, 1, 1, 1};
         for (int k = 0; k < h->dim; ++k) n[k] = h->nr << h->levels[g][k];
@@ -405,6 +408,16 @@ sg_status ensure_events(sg_ctx* h, int pairs) {
     return SG_OK;
 }
 
+// Vlasov-Poisson: the field of every grid of the handle (or batch) from the stage input.
+cudaError_t launch_efield(const sg_ctx* h, int stage, int pre_dt) {
+    const int ng = (int)h->hgrids.size();
+    return h->esize == 8
+               ? sg::Launch<double>::efield(h->dgrids.as<GridDesc>(), ng, h->dinst.as<InstState>(),
+                                            h->alpha.as<unsigned long long>(), stage, pre_dt, h->stream)
+               : sg::Launch<float>::efield(h->dgrids.as<GridDesc>(), ng, h->dinst.as<InstState>(),
+                                           h->alpha.as<unsigned long long>(), stage, pre_dt, h->stream);
+}
+
 // Enqueues `nsteps` time steps (dt control + three RK stages each) on the handle's stream.
 // With profiling on, each stage launch (or per-grid launch group) is bracketed by an event pair.
 sg_status enqueue_steps(sg_ctx* h, int nsteps, long long* kernels) {
@@ -413,8 +426,12 @@ sg_status enqueue_steps(sg_ctx* h, int nsteps, long long* kernels) {
     if (h->profile) SG_TRY(ensure_events(h, 3 * nsteps));
     h->ev_pairs_used = h->profile ? 3 * nsteps : 0;
     for (int s = 0; s < nsteps; ++s) {
-        SG_CUDA(sg::launch_dt(h->dinst.as<InstState>(), h->ninst, h->alpha.as<unsigned long long>(), ph, 0,
-                              h->flags.as<int>(), h->stream));
+        if (h->pde == SG_PDE_VLASOV) {  // E of the step's input first: the CFL step needs max|E|
+            SG_CUDA(launch_efield(h, 0, 1));
+            ++nk;
+        }
+        SG_CUDA(sg::launch_dt(h->dinst.as<InstState>(), h->ninst, h->dgrids.as<GridDesc>(),
+                              h->alpha.as<unsigned long long>(), ph, 0, h->flags.as<int>(), h->stream));
         ++nk;
         for (int stage = 0; stage < 3; ++stage) {
             StageArgs a{};
@@ -427,6 +444,10 @@ sg_status enqueue_steps(sg_ctx* h, int nsteps, long long* kernels) {
             a.phys = ph;
             a.box_elems = (int)h->box_elems;
             const int pair = 3 * s + stage;
+            if (h->pde == SG_PDE_VLASOV && stage > 0) {
+                SG_CUDA(launch_efield(h, stage, 0));
+                ++nk;
+            }
             if (h->profile) SG_CUDA(cudaEventRecordWithFlags(h->ev[2 * pair], h->stream, cudaEventRecordExternal));
             const bool batched = h->is_batch || h->prm.exec == SG_BATCHED;
             if (batched) {
@@ -587,6 +608,7 @@ sg_status time_stage0(sg_ctx* h, double* ms) {
     }
     SG_CUDA(cudaMemcpyAsync(h->dinst.p, h->hinst.p, sizeof(InstState) * h->ninst, cudaMemcpyHostToDevice, h->stream));
     SG_CUDA(cudaMemsetAsync(h->alpha.p, 0, h->alpha.bytes, h->stream));
+    if (h->pde == SG_PDE_VLASOV) SG_CUDA(launch_efield(h, 0, 0));
     cudaEvent_t e0, e1;
     SG_CUDA(cudaEventCreate(&e0));
     SG_CUDA(cudaEventCreate(&e1));
@@ -708,8 +730,8 @@ sg_status run_steps(sg_ctx* h) {
         for (int i = 0; i < h->ninst; ++i) all = all && finished(h->hinst.p[i]);
         if (all || lflags[SG_FLAG_NONFINITE] || lflags[SG_FLAG_BADDT]) break;  // done, or failed: stop early
     }
-    SG_CUDA(sg::launch_dt(h->dinst.as<InstState>(), h->ninst, h->alpha.as<unsigned long long>(), phys_of(h), 1,
-                          h->flags.as<int>(), h->stream));
+    SG_CUDA(sg::launch_dt(h->dinst.as<InstState>(), h->ninst, h->dgrids.as<GridDesc>(),
+                          h->alpha.as<unsigned long long>(), phys_of(h), 1, h->flags.as<int>(), h->stream));
     h->launches += 1;
     int hflags[4] = {0, 0, 0, 0};
     SG_CUDA(cudaMemcpyAsync(h->hinst.p, h->dinst.p, sizeof(InstState) * h->ninst, cudaMemcpyDeviceToHost, h->stream));
@@ -774,7 +796,8 @@ sg_status prolong_combine_rmw_t(sg_ctx* h) {
             const bool last = a + 1 == axes.size();
             T* dst = last ? nullptr : bufs[a & 1];
             SG_CUDA(sg::Launch<T>::prolong_axis(src, dst, last ? acc : nullptr, gd.coeff, below, (int)m[k],
-                                                (int)Nf, above, r, h->prm.eps, h->prm.prolong, h->stream));
+                                                (int)Nf, above, r, h->prm.eps, h->prm.prolong,
+                                                (h->pde == SG_PDE_VLASOV && k == 1) ? 1 : 0, h->stream));
             h->launches += 1;
             m[k] = Nf;
             src = dst;
@@ -862,7 +885,8 @@ sg_status prolong_combine_fused_t(sg_ctx* h, CombineBuffers& cb) {
         exact = exact && a >= 1.0 && std::ldexp(1.0, std::ilogb(a)) == a;
     }
     SG_CUDA(sg::Launch<T>::combine_last_axis(cb.tab.as<CombineGrid>(), h->G, h->uhat.as<double>(), below, (int)Nf,
-                                             exact ? 1 : 0, h->prm.eps, h->prm.prolong, h->stream));
+                                             exact ? 1 : 0, h->pde == SG_PDE_VLASOV ? 1 : 0, h->prm.eps,
+                                             h->prm.prolong, h->stream));
     h->launches += 1;
     SG_CUDA(cudaStreamSynchronize(h->stream));
     h->combined = true;
@@ -878,6 +902,47 @@ sg_status prolong_combine_t(sg_ctx* h, CombineBuffers& cb) {
 
 sg_status check_handle(sg_handle h) {
     if (!h) return fail(SG_ERR_ARG, "NULL handle");
+    return SG_OK;
+}
+
+// Vlasov-Poisson field energy (1/2) sum_i E_i^2 h_x of grid `which` or of the combined solution.
+sg_status field_energy(sg_ctx* h, int which, double* out) {
+    if (h->pde != SG_PDE_VLASOV) return fail(SG_ERR_ARG, "the field energy needs the Vlasov-Poisson PDE");
+    int n0, n1;
+    double hx, hv;
+    const void* u;
+    const void* comp = nullptr;
+    bool dbl = true;
+    if (which == SG_WHICH_COMBINED) {
+        if (!h->combined) return fail(SG_ERR_STATE, "no combined solution: call sg_prolong_combine first");
+        n0 = n1 = (int)((long long)h->nr << h->nl);
+        hx = fine_spacing(h, 0);
+        hv = fine_spacing(h, 1);
+        u = h->uhat.p;
+    } else if (which >= 0 && which < h->G) {
+        const GridDesc& d = h->hgrids[which];
+        n0 = d.n[0];
+        n1 = d.n[1];
+        hx = d.h[0];
+        hv = d.h[1];
+        u = d.u0;
+        comp = d.u3;
+        dbl = h->esize == 8;
+    } else {
+        return fail(SG_ERR_ARG, "which = %d out of range", which);
+    }
+    DevBuf scratch;
+    SG_TRY(scratch.alloc(sizeof(double) * (size_t)n0));
+    double* dres = h->partial.as<double>() + 1024;
+    if (dbl)
+        SG_CUDA(sg::Launch<double>::field_energy((const double*)u, nullptr, n0, n1, hx, hv, scratch.as<double>(), dres, h->stream));
+    else
+        SG_CUDA(sg::Launch<float>::field_energy((const float*)u, (const float*)comp, n0, n1, hx, hv, scratch.as<double>(), dres, h->stream));
+    h->launches += 1;
+    double r = 0.0;
+    SG_CUDA(cudaMemcpyAsync(&r, dres, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+    SG_CUDA(cudaStreamSynchronize(h->stream));
+    *out = r;
     return SG_OK;
 }
 
@@ -918,7 +983,8 @@ sg_status sg_create(int dim, int root_cells, int level, int pde, const sg_params
     if (root_cells < 5) return fail(SG_ERR_ARG, "root_cells must be >= 5 (five distinct stencil points)");
     if (level < 0 || level > 16 || ((long long)root_cells << level) > (1LL << 20))
         return fail(SG_ERR_ARG, "level must be in [0, 16] with root_cells * 2^level <= 2^20");
-    if (pde != SG_PDE_ADVECTION && pde != SG_PDE_BURGERS) return fail(SG_ERR_ARG, "pde");
+    if (pde != SG_PDE_ADVECTION && pde != SG_PDE_BURGERS && pde != SG_PDE_VLASOV) return fail(SG_ERR_ARG, "pde");
+    if (pde == SG_PDE_VLASOV && dim != 2) return fail(SG_ERR_ARG, "the Vlasov-Poisson system is 1D1V: dim must be 2");
     sg_params prm;
     if (params) prm = *params;
     else sg_params_init(&prm);
@@ -970,6 +1036,14 @@ sg_status sg_create(int dim, int root_cells, int level, int pde, const sg_params
             h->own_stream = true;
         }
         sg_status st = h->arena.alloc((size_t)h->total_pts * h->esize * (h->esize == 4 ? 4 : 3));
+        if (st == SG_OK && pde == SG_PDE_VLASOV) {
+            long long ef_total = 0;
+            for (int g = 0; g < h->G; ++g) {
+                h->ef_offset.push_back(ef_total);
+                ef_total += (long long)root_cells << h->levels[g][0];
+            }
+            st = h->efield.alloc((size_t)ef_total * h->esize);
+        }
         if (st == SG_OK) st = build_tables(h);
         if (st == SG_OK) st = alloc_step_buffers(h, h->G, 1);
         if (st != SG_OK) {
@@ -989,6 +1063,23 @@ sg_status sg_create(int dim, int root_cells, int level, int pde, const sg_params
 sg_status sg_init(sg_handle h, int ic_kind, const double* p, int n_params) {
     SG_TRY(check_handle(h));
     if (h->is_batch) return fail(SG_ERR_ARG, "sg_init applies to batch members, not to the batch");
+    if (ic_kind == SG_IC_LANDAU) {
+        if (h->pde != SG_PDE_VLASOV) return fail(SG_ERR_ARG, "SG_IC_LANDAU needs the Vlasov-Poisson PDE");
+        if (n_params != 2 || !p || !std::isfinite(p[0]) || !std::isfinite(p[1]))
+            return fail(SG_ERR_ARG, "SG_IC_LANDAU takes 2 finite parameters (a, k)");
+        for (int g = 0; g < h->G; ++g) {
+            if (h->esize == 8) SG_CUDA(sg::Launch<double>::restrict_landau(h->hgrids[g], p[0], p[1], h->stream));
+            else SG_CUDA(sg::Launch<float>::restrict_landau(h->hgrids[g], p[0], p[1], h->stream));
+            h->launches += 1;
+        }
+        SG_CUDA(cudaStreamSynchronize(h->stream));
+        h->ic_sine = false;
+        h->initialized = true;
+        h->combined = false;
+        h->t = 0.0;
+        h->steps = 0;
+        return SG_OK;
+    }
     if (ic_kind != SG_IC_SINE || n_params != 4 || !p) return fail(SG_ERR_ARG, "SG_IC_SINE takes 4 parameters");
     for (int i = 0; i < 4; ++i)
         if (!std::isfinite(p[i])) return fail(SG_ERR_ARG, "initial-condition parameter %d not finite", i);
@@ -1194,6 +1285,7 @@ sg_status sg_reduce(sg_handle h, int which, int kind, double* out) {
     SG_TRY(check_handle(h));
     if (h->is_batch) return fail(SG_ERR_ARG, "sg_reduce applies to batch members");
     if (!out) return fail(SG_ERR_ARG, "NULL output");
+    if (kind == SG_REDUCE_FIELD_ENERGY) return field_energy(h, which, out);
     if (kind < SG_REDUCE_MASS || kind > SG_REDUCE_LINF_EXACT) return fail(SG_ERR_ARG, "unknown reduction %d", kind);
     ExactSpec X{};
     X.dim = h->dim;

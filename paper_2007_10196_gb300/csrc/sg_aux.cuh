@@ -2,7 +2,7 @@
 // device-side time-step control, Step 1 (restriction of the initial condition), Step 3
 // (prolongation of each grid and the FP64 signed combination sum) and FP64 reductions.
 #pragma once
-#include "sg_weno.cuh"
+#include "sg_stage.cuh"
 
 // max |u| of the stage-0 input over every tile of the queue -> alpha slot 0 (the slots of
 // stages 1 and 2 are cleared by the caller); also flags non-finite values.
@@ -30,8 +30,8 @@ __global__ void __launch_bounds__(SG_NT) sg_alpha_init_kernel(const GridDesc* gr
 // Per-instance time-step control, one thread per instance.  commit_only = 0 at the start of
 // a step: adds the previous (pending) step to t, then sets dt for the next step or marks the
 // instance inactive.  commit_only = 1 after the last step: only adds the pending step.
-static __global__ void sg_dt_kernel(InstState* inst, int ninst, const unsigned long long* alpha,
-                             PhysParams ph, int commit_only, int* flags) {
+static __global__ void sg_dt_kernel(InstState* inst, int ninst, const GridDesc* grids,
+                             const unsigned long long* alpha, PhysParams ph, int commit_only, int* flags) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ninst) return;
     InstState s = inst[i];
@@ -49,9 +49,20 @@ static __global__ void sg_dt_kernel(InstState* inst, int ninst, const unsigned l
             double sum = 0.0;
             for (int k = 0; k < ph.dim; ++k) {
                 double a = 0.0;
-                if (ph.pde == 1) {
+                if (ph.pde == 1 || (ph.pde == 2 && k == 1)) {  // Burgers max|u|; Vlasov-Poisson max|E|
                     for (int g = s.grid0; g < s.grid0 + s.ngrids; ++g)
                         a = fmax(a, ph.alpha_f32 ? (double)alpha_dec<float>(alpha[g * 3]) : bitsd(alpha[g * 3]));
+                } else if (ph.pde == 2) {  // Vlasov-Poisson along x: max |v_j|, at an end node
+                    for (int g = s.grid0; g < s.grid0 + s.ngrids; ++g) {
+                        const GridDesc& G = grids[g];
+                        if (ph.alpha_f32) {
+                            const float v0 = (float)G.lo[1], v1 = (float)G.lo[1] + (float)(G.n[1] - 1) * (float)G.h[1];
+                            a = fmax(a, (double)fmaxf(fabsf(v0), fabsf(v1)));
+                        } else {
+                            const double v0 = G.lo[1], v1 = G.lo[1] + (double)(G.n[1] - 1) * G.h[1];
+                            a = fmax(a, fmax(fabs(v0), fabs(v1)));
+                        }
+                    }
                 } else {
                     a = ph.adv[k] < 0.0 ? -ph.adv[k] : ph.adv[k];
                 }
@@ -98,6 +109,114 @@ __global__ void sg_restrict_sine_kernel(GridDesc G, int dim, double p0, double p
     }
 }
 
+// Landau initial condition of the Vlasov-Poisson workload (d = 2, axis 0 = x, axis 1 = v):
+// f_0 = (1 + a cos(k x)) exp(-v^2/2) / sqrt(2 pi).
+template <class T>
+__global__ void sg_restrict_landau_kernel(GridDesc G, double a, double kx) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < G.npts;
+         p += (long long)gridDim.x * blockDim.x) {
+        const long long j = p / G.n[0], i = p - j * G.n[0];
+        const double x = G.lo[0] + (double)i * G.h[0], v = G.lo[1] + (double)j * G.h[1];
+        const double m = exp(-0.5 * (v * v)) / sqrt(2.0 * 3.14159265358979323846);
+        const double f = (1.0 + a * cos(kx * x)) * m;
+        ((T*)G.u0)[p] = (T)f;
+        if (sizeof(T) == 4) ((T*)G.u3)[p] = (T)(f - (double)(T)f);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Vlasov-Poisson field of every grid from the input of RK stage `stage` (one block per
+// grid): rho_i = h_v sum_j f_ij (j ascending, one thread per i), then by one thread, in the
+// same order of operations as the definition: mean(rho), E_0 = 0, E_i = E_{i-1} +
+// h_x ((rho_{i-1} + rho_i)/2 - mean), and the mean of E removed.  E goes to G->ef and
+// max |E| to the grid's alpha slot of the stage (the LF alpha along v).  pre_dt: launched
+// before the step's time-step control, which has not yet counted the previous step (FP32
+// ping-pong parity).
+// ------------------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) sg_efield_kernel(const GridDesc* grids, int ngrids, const InstState* inst,
+                                                        unsigned long long* alpha, int stage, int pre_dt) {
+    for (int g = blockIdx.x; g < ngrids; g += gridDim.x) {
+        const GridDesc* G = grids + g;
+        const InstState* S = inst + G->inst;
+        const long long steps = S->steps + (pre_dt ? S->pending : 0);
+        StageIO<T> io;
+        io.setup(G, stage, (int)((steps - S->step0) & 1));
+        const int n0 = G->n[0], n1 = G->n[1];
+        T* E = (T*)G->ef;
+        const T hv = (T)G->h[1], hx = (T)G->h[0];
+        for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+            T sum = T(0);
+            for (int j = 0; j < n1; ++j) sum = sum + io.load(i + (long long)n0 * j);
+            E[i] = hv * sum;  // rho_i for now
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T mean = T(0);
+            for (int i = 0; i < n0; ++i) mean = mean + E[i];
+            mean = mean / (T)n0;
+            T prev = E[0], e = T(0), meanE = T(0);
+            E[0] = T(0);
+            for (int i = 1; i < n0; ++i) {
+                const T rho = E[i];
+                e = e + hx * ((T)0.5 * (prev + rho) - mean);
+                prev = rho;
+                E[i] = e;
+            }
+            for (int i = 0; i < n0; ++i) meanE = meanE + E[i];
+            meanE = meanE / (T)n0;
+            T mx = T(0);
+            for (int i = 0; i < n0; ++i) {
+                const T v = E[i] - meanE;
+                E[i] = v;
+                mx = sg_max(mx, sg_abs(v));
+            }
+            alpha[g * 3 + stage] = alpha_enc(mx);
+        }
+        __syncthreads();
+    }
+}
+
+// Field energy (1/2) sum_i E_i^2 h_x of one 2-D array (a grid, or the combined solution), E
+// as in sg_efield_kernel but in FP64 (FP32 grids: the float pair U + C).  One block; rho
+// goes through `scratch` (n0 doubles).
+template <class T>
+__global__ void __launch_bounds__(256) sg_field_energy_kernel(const T* u, const T* comp, int n0, int n1, double hx,
+                                                              double hv, double* scratch, double* out) {
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+        double sum = 0.0;
+        for (int j = 0; j < n1; ++j) {
+            const long long p = i + (long long)n0 * j;
+            double v = (double)u[p];
+            if (comp) v = v + (double)comp[p];
+            sum = sum + v;
+        }
+        scratch[i] = hv * sum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mean = 0.0;
+        for (int i = 0; i < n0; ++i) mean = mean + scratch[i];
+        mean = mean / (double)n0;
+        double prev = scratch[0], e = 0.0, meanE = 0.0;
+        scratch[0] = 0.0;
+        for (int i = 1; i < n0; ++i) {
+            const double rho = scratch[i];
+            e = e + hx * (0.5 * (prev + rho) - mean);
+            prev = rho;
+            scratch[i] = e;
+        }
+        for (int i = 0; i < n0; ++i) meanE = meanE + scratch[i];
+        meanE = meanE / (double)n0;
+        double s = 0.0;
+        for (int i = 0; i < n0; ++i) {
+            const double v = scratch[i] - meanE;
+            s = s + v * v;
+        }
+        *out = 0.5 * s * hx;
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // Prolongation of one axis (Section 2.2.1): in has shape (below, m_in, above) in the
 // axis-0-fastest sense, out has (below, Nf, above).  Fine node jf on an axis refined by
@@ -136,7 +255,7 @@ template <class T>
 __global__ void sg_prolong_axis_kernel(const T* __restrict__ in, T* __restrict__ out,
                                        double* __restrict__ acc, double coeff, long long below,
                                        int min_, int nf, long long above, int r, double eps,
-                                       int lagrange) {
+                                       int lagrange, int zero_bc) {
     const long long tot = below * nf * above;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -151,8 +270,8 @@ __global__ void sg_prolong_axis_kernel(const T* __restrict__ in, T* __restrict__
         T v[5];
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
-            const int c = wrap_index(ic - 2 + m, min_);
-            v[m] = line[(long long)c * below];
+            const int cr = ic - 2 + m;  // zero_bc: 0 beyond the ends, else periodic
+            v[m] = zero_bc && (cr < 0 || cr >= min_) ? T(0) : line[(long long)wrap_index(cr, min_) * below];
         }
         T res;
         if constexpr (sizeof(T) == 8) {
@@ -329,7 +448,7 @@ struct InterpWin<float> {
 template <class T, int J, bool EXACT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) sg_combine_last_axis_kernel(const CombineGrid* __restrict__ tab, int G,
                                                                     double* __restrict__ uhat, long long below,
-                                                                    int nf, double eps, int lagrange) {
+                                                                    int nf, double eps, int lagrange, int zero_last) {
     const T e12 = (T)(12.0 * eps);
     const int nchunks = (nf + J - 1) / J;
     // centre index and offset s of the chunk's J fine nodes for every refinement ratio
@@ -373,19 +492,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) sg_combine_last_a
                 const T* st = s_tab + lr * J;
                 const int* ct = c_tab + lr * J;
                 int cur = ct[0];
+                // coarse value at index c of the last axis: periodic, or 0 beyond the ends
+                auto at = [&](int c) -> T {
+                    if (zero_last && (c < 0 || c >= n)) return T(0);
+                    return col[(long long)wrap_index(c, n) * below];
+                };
                 InterpWin<T> W;
-                {
-                    int c = wrap_index(cur - 2, n);
-                    W.w0 = col[(long long)c * below];
-                    if (++c == n) c = 0;
-                    W.w1 = col[(long long)c * below];
-                    if (++c == n) c = 0;
-                    W.w2 = col[(long long)c * below];
-                    if (++c == n) c = 0;
-                    W.w3 = col[(long long)c * below];
-                    if (++c == n) c = 0;
-                    W.w4 = col[(long long)c * below];
-                }
+                W.w0 = at(cur - 2);
+                W.w1 = at(cur - 1);
+                W.w2 = at(cur);
+                W.w3 = at(cur + 1);
+                W.w4 = at(cur + 2);
                 W.prepare(e12, lagrange);
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
@@ -398,9 +515,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) sg_combine_last_a
                         W.w1 = W.w2;
                         W.w2 = W.w3;
                         W.w3 = W.w4;
-                        int c = ic + 2;
-                        if (c >= n) c -= n;
-                        W.w4 = col[(long long)c * below];
+                        W.w4 = at(ic + 2);
                         W.prepare(e12, lagrange);
                         cur = ic;
                     }

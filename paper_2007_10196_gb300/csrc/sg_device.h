@@ -25,6 +25,7 @@ struct GridDesc {
     void* u1;
     void* u2;
     void* u3;
+    void* ef;            // Vlasov-Poisson: E_i of the current stage input, n[0] values (else null)
     long long npts;
     int n[SG_MAXD];      // nodes per axis
     int te[SG_MAXD];     // tile extent per axis

@@ -35,10 +35,21 @@ struct Launch {
                                   unsigned long long* alpha, int* flags, cudaStream_t s);
     // u0 of one grid <- p0 + p1 sin(p2 sum x + p3) (FP32: also the compensation term u3).
     static cudaError_t restrict_sine(const GridDesc& g, int dim, const double* p, cudaStream_t s);
-    // One prolongation axis; acc != nullptr fuses "acc += coeff * result".
+    // One prolongation axis; acc != nullptr fuses "acc += coeff * result"; zero_bc: values
+    // beyond the ends of the axis are 0 (Vlasov-Poisson v), else periodic.
     static cudaError_t prolong_axis(const T* in, T* out, double* acc, double coeff, long long below,
                                     int min_, int nf, long long above, int r, double eps,
-                                    int lagrange, cudaStream_t s);
+                                    int lagrange, int zero_bc, cudaStream_t s);
+    // Vlasov-Poisson: E of every grid from the input of RK stage `stage` into GridDesc.ef,
+    // max|E| into the stage's alpha slot (pre_dt: launched before the step's dt control).
+    static cudaError_t efield(const GridDesc* grids, int ngrids, const InstState* inst, unsigned long long* alpha,
+                              int stage, int pre_dt, cudaStream_t s);
+    // Field energy of one 2-D array (n0 x n1, comp may be null) into *out (device);
+    // scratch holds n0 doubles.
+    static cudaError_t field_energy(const T* u, const T* comp, int n0, int n1, double hx, double hv,
+                                    double* scratch, double* out, cudaStream_t s);
+    // Landau initial condition on one grid.
+    static cudaError_t restrict_landau(const GridDesc& g, double a, double kx, cudaStream_t s);
     static cudaError_t accumulate(const T* u, double* acc, double coeff, long long n, cudaStream_t s);
     // out[j] = u[idx[j]], j < n (device arrays; indices already checked)
     static cudaError_t gather(const T* u, const long long* idx, T* out, long long n, cudaStream_t s);
@@ -51,7 +62,7 @@ struct Launch {
     // uhat = sum_g c_g P_{d-1} I_g over the G entries of tab (device array), written once.
     // exact_coeffs: every |c_g| is a power of two (products c_g v are exact in the FP32 sum)
     static cudaError_t combine_last_axis(const CombineGrid* tab, int G, double* uhat, long long below, int nf,
-                                         int exact_coeffs,
+                                         int exact_coeffs, int zero_last,
                                          double eps, int lagrange, cudaStream_t s);
     // FP64 reduction of n values u (+ comp if non-null); partial holds >= 1024 doubles.
     static cudaError_t reduce(const T* u, const T* comp, long long n, int kind, const ExactSpec& X,
@@ -62,7 +73,7 @@ extern template struct Launch<double>;
 extern template struct Launch<float>;
 
 // flags: the device flag array (SG_FLAG_BADDT is set if a step comes out non-positive)
-cudaError_t launch_dt(InstState* inst, int ninst, const unsigned long long* alpha,
+cudaError_t launch_dt(InstState* inst, int ninst, const GridDesc* grids, const unsigned long long* alpha,
                       const PhysParams& ph, int commit_only, int* flags, cudaStream_t s);
 
 // Sets the calling thread's message returned by sg_last_error (defined in sg_api.cu).

@@ -164,10 +164,32 @@ cudaError_t Launch<T>::restrict_sine(const GridDesc& g, int dim, const double* p
 template <class T>
 cudaError_t Launch<T>::prolong_axis(const T* in, T* out, double* acc, double coeff, long long below,
                                     int min_, int nf, long long above, int r, double eps,
-                                    int lagrange, cudaStream_t s) {
+                                    int lagrange, int zero_bc, cudaStream_t s) {
     const long long tot = below * nf * above;
     sg_prolong_axis_kernel<T><<<detail::grid_for(tot, 256), 256, 0, s>>>(in, out, acc, coeff, below, min_,
-                                                                          nf, above, r, eps, lagrange);
+                                                                          nf, above, r, eps, lagrange, zero_bc);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Launch<T>::efield(const GridDesc* grids, int ngrids, const InstState* inst, unsigned long long* alpha,
+                              int stage, int pre_dt, cudaStream_t s) {
+    if (ngrids < 1) return cudaSuccess;
+    const int nb = ngrids < 65535 ? ngrids : 65535;
+    sg_efield_kernel<T><<<nb, 256, 0, s>>>(grids, ngrids, inst, alpha, stage, pre_dt);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Launch<T>::field_energy(const T* u, const T* comp, int n0, int n1, double hx, double hv,
+                                    double* scratch, double* out, cudaStream_t s) {
+    sg_field_energy_kernel<T><<<1, 256, 0, s>>>(u, comp, n0, n1, hx, hv, scratch, out);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Launch<T>::restrict_landau(const GridDesc& g, double a, double kx, cudaStream_t s) {
+    sg_restrict_landau_kernel<T><<<detail::grid_for(g.npts, 256), 256, 0, s>>>(g, a, kx);
     return cudaGetLastError();
 }
 
@@ -220,13 +242,15 @@ cudaError_t Launch<T>::prolong_axis2(const T* in, T* out, long long below, int m
 
 template <class T>
 cudaError_t Launch<T>::combine_last_axis(const CombineGrid* tab, int G, double* uhat, long long below, int nf,
-                                         int exact_coeffs,
+                                         int exact_coeffs, int zero_last,
                                          double eps, int lagrange, cudaStream_t s) {
     constexpr int J = 8;
     dim3 grid((unsigned)std::min<long long>((below + 255) / 256, 65535),
               (unsigned)std::min<long long>((nf + J - 1) / J, 65535));
-    if (exact_coeffs) sg_combine_last_axis_kernel<T, J, true><<<grid, 256, 0, s>>>(tab, G, uhat, below, nf, eps, lagrange);
-    else sg_combine_last_axis_kernel<T, J, false><<<grid, 256, 0, s>>>(tab, G, uhat, below, nf, eps, lagrange);
+    if (exact_coeffs)
+        sg_combine_last_axis_kernel<T, J, true><<<grid, 256, 0, s>>>(tab, G, uhat, below, nf, eps, lagrange, zero_last);
+    else
+        sg_combine_last_axis_kernel<T, J, false><<<grid, 256, 0, s>>>(tab, G, uhat, below, nf, eps, lagrange, zero_last);
     return cudaGetLastError();
 }
 

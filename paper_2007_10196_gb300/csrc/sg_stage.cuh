@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
     const int tid = threadIdx.x;
     const PhysParams& ph = A.phys;
     const bool burgers = ph.pde == 1;
+    const bool vlasov = ph.pde == 2;  // d = 2: axis 0 = x (speed v_j), axis 1 = v (speed E_i, 0 beyond the ends)
     const T eps12 = (T)(12.0 * ph.eps);
     const T adv0 = (T)ph.adv[0], adv1 = (T)ph.adv[1], adv2 = (T)ph.adv[2];
 
@@ -306,10 +307,15 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
                     const int z = r / 6, h = r - z * 6;
                     const int y = h < 3 ? h - 3 : e[1] + h - 3;
                     int gy = org[1] + y;
+                    const int bidx = (x + 3) + B0 * ((y + 3) + B1 * (z + (D >= 3 ? 3 : 0)));
+                    if (vlasov && (gy < 0 || gy >= n[1])) {  // zero inflow in v
+                        bp[bidx] = T(0);
+                        continue;
+                    }
                     if (gy < 0) gy += n[1];
                     else if (gy >= n[1]) gy -= n[1];
                     const long long g = (org[0] + x) + gs[1] * gy + gs[2] * (org[2] + z);
-                    put((x + 3) + B0 * ((y + 3) + B1 * (z + (D >= 3 ? 3 : 0))), g);
+                    put(bidx, g);
                 }
             }
             if (D >= 3) {
@@ -335,9 +341,15 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
         const int NF1 = D >= 2 ? e[0] * (e[1] + 1) * e[2] : 0;
         const int NF2 = D >= 3 ? e[0] * e[1] * (e[2] + 1) : 0;
         const int NF = NF0 + NF1 + NF2;
+        // Vlasov-Poisson: the LF alpha along x is max_j |v_j| of the grid (an end node)
+        T ax = T(0);
+        if (vlasov) {
+            const T v0 = (T)G->lo[1], v1 = (T)G->lo[1] + (T)(n[1] - 1) * (T)G->h[1];
+            ax = sg_max(sg_abs(v0), sg_abs(v1));
+        }
         for (int q = tid; q < NF; q += SG_NT) {
             int b, Sx;
-            T ak;
+            T ak, al;
             if (q < NF0) {
                 Sx = 1;
                 ak = adv0;
@@ -349,6 +361,8 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
                     y = r - z * e[1];
                 }
                 b = i + B0 * ((y + (D >= 2 ? 3 : 0)) + B1 * (z + (D >= 3 ? 3 : 0)));
+                if (vlasov) ak = (T)G->lo[1] + (T)(org[1] + y) * (T)G->h[1];  // v_j of the line
+                al = vlasov ? ax : sg_abs(ak);
             } else if (D >= 2 && q < NF0 + NF1) {
                 Sx = B0;
                 ak = adv1;
@@ -358,6 +372,8 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
                 const int z = (int)fp1.div((unsigned)r);
                 const int i = r - z * (e[1] + 1);
                 b = (x + 3) + B0 * (i + B1 * (z + (D >= 3 ? 3 : 0)));
+                if (vlasov) ak = ((const T*)G->ef)[org[0] + x];  // E_i of the line
+                al = vlasov ? alpha_b : sg_abs(ak);
             } else {
                 Sx = B0 * B1;
                 ak = adv2;
@@ -367,21 +383,20 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
                 const int i = (int)fe1.div((unsigned)r);
                 const int y = r - i * e[1];
                 b = (x + 3) + B0 * ((y + 3) + B1 * i);
+                al = sg_abs(ak);
             }
             T F;
             if constexpr (sizeof(T) == 8) {
                 if (burgers) {
                     F = Weno<double>::interface_split((const double*)bp + b, (const double*)bm + b, Sx, ph);
                 } else {
-                    const double a = (double)ak;
-                    F = Weno<double>::interface((const double*)bp + b, Sx, a < 0.0 ? -a : a, a, ph);
+                    F = Weno<double>::interface((const double*)bp + b, Sx, (double)al, (double)ak, ph);
                 }
             } else {
                 if (burgers) {
                     F = Weno<float>::interface_split((const float*)bp + b, (const float*)bm + b, Sx, eps12, ph.scheme);
                 } else {
-                    const float a = (float)ak;  // already float: no conversion
-                    F = Weno<float>::interface((const float*)bp + b, Sx, fabsf(a), a, ph, eps12);
+                    F = Weno<float>::interface((const float*)bp + b, Sx, (float)al, (float)ak, ph, eps12);
                 }
             }
             fb[q] = F;

@@ -1,0 +1,144 @@
+"""The 1D1V Vlasov-Poisson workload (Landau damping) on the GPU against the FP64 oracle.
+
+Not in the paper: the kinetic system run on the same sparse-grid WENO5 method (x periodic, v
+zero beyond its ends, each grid with its own field).  FP64: bit for bit after several CFL
+steps (plain and batched execution, several tiles) and through the combination (one pass
+and grid by grid); FP32 within derived tolerances; the field energy reduction; and the full
+configuration (N_r = 16, N_L = 5, finest 512^2, to t = 40) damping at the rate of linear
+theory.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_2007_10196_gb300 as P
+
+from _helpers import make, read_grids
+
+pytestmark = pytest.mark.gpu
+
+TWO_PI = 2 * math.pi
+LO = [0.0, -TWO_PI, 0.0, 0.0, 0.0, 0.0]
+HI = [2 * TWO_PI, TWO_PI, 1.0, 1.0, 1.0, 1.0]
+U32 = 2.0 ** -24
+
+
+def _levels(h):
+    G = P.sg_num_grids(h)
+    info = [P.sg_grid_info(h, g, 2) for g in range(G)]
+    return [i[0] for i in info], [i[1] for i in info], [i[2] for i in info]
+
+
+def _vp(orc, nr, nl):
+    return orc.problem(2, nr, nl, pde=orc.VLASOV, eps=1e-3, lo=LO[:2], hi=HI[:2])
+
+
+def _landau_grids(orc, p, lev, a=0.05, k=0.5):
+    return [orc.restrict_landau(p, l, a, k) for l in lev]
+
+
+def _run(orc, nr, nl, prec, exe, tp, nsteps, a=0.05):
+    h = make(2, nr, nl, P.SG_PDE_VLASOV, precision=prec, exec=exe, tile_points=tp, lo=LO, hi=HI,
+             dt_rule=P.SG_DT_CFL, cfl=0.4)
+    try:
+        lev, shp, co = _levels(h)
+        p = _vp(orc, nr, nl)
+        g0 = _landau_grids(orc, p, lev, a)
+        if prec == P.SG_F32:
+            g0 = [g.astype(np.float32).astype(np.float64) for g in g0]
+        P.sg_init_grids(h, np.concatenate(g0))
+        t = P.sg_step(h, 100.0, nsteps)
+        got = read_grids(h, [int(np.prod(s)) for s in shp])
+        P.sg_prolong_combine(h)
+        uh = P.sg_read(h, P.SG_WHICH_COMBINED, count=(nr << nl) ** 2)
+        fe = [P.sg_reduce(h, g, P.SG_REDUCE_FIELD_ENERGY) for g in range(len(lev))]
+        fe_c = P.sg_reduce(h, P.SG_WHICH_COMBINED, P.SG_REDUCE_FIELD_ENERGY)
+        steps = P.sg_time(h)[1]
+    finally:
+        P.sg_destroy(h)
+    ref, osteps, ot = orc.solve(p, lev, g0, 100.0, max_steps=nsteps, rule=orc.DT_CFL, cfl=0.4)
+    return dict(lev=lev, co=co, p=p, got=got, uh=uh, fe=fe, fe_c=fe_c, t=t, steps=steps, ref=ref,
+                osteps=osteps, ot=ot)
+
+
+CASES = [(8, 2, P.SG_PLAIN, 256), (8, 2, P.SG_BATCHED, 512), (10, 2, P.SG_BATCHED, 1024),
+         (6, 3, P.SG_PLAIN, 0), (16, 1, P.SG_BATCHED, 0)]
+
+
+@pytest.mark.parametrize("nr,nl,exe,tp", CASES, ids=lambda c: str(c))
+def test_vlasov_steps_and_combination_fp64_bitwise(sg, orc, nr, nl, exe, tp):
+    r = _run(orc, nr, nl, P.SG_F64, exe, tp, 4)
+    assert r["steps"] == r["osteps"] == 4 and r["t"] == r["ot"]
+    for g, ref in zip(r["got"], r["ref"]):
+        assert np.array_equal(g, ref), np.max(np.abs(g - ref))
+    expect = orc.combine(r["p"], r["lev"], r["co"], r["ref"])
+    assert np.array_equal(r["uh"], expect), np.max(np.abs(r["uh"] - expect))
+    for l, g, fe in zip(r["lev"], r["ref"], r["fe"]):
+        assert fe == orc.field_energy(r["p"], l, g)
+    nf = r["p"].nr << r["p"].nl
+    assert r["fe_c"] == orc.field_energy(orc.problem(2, nf, 0, pde=orc.VLASOV, eps=1e-3, lo=LO[:2], hi=HI[:2]),
+                                         [0, 0], expect)
+
+
+def test_vlasov_combination_grid_by_grid_fp64_bitwise(sg, orc):
+    nr, nl = 8, 3
+    h = make(2, nr, nl, P.SG_PDE_VLASOV, lo=LO, hi=HI, dt_rule=P.SG_DT_CFL, cfl=0.4, combine_budget_gb=-1.0)
+    try:
+        lev, shp, co = _levels(h)
+        p = _vp(orc, nr, nl)
+        g0 = _landau_grids(orc, p, lev)
+        P.sg_init_grids(h, np.concatenate(g0))
+        P.sg_step(h, 100.0, 2)
+        P.sg_prolong_combine(h)
+        uh = P.sg_read(h, P.SG_WHICH_COMBINED, count=(nr << nl) ** 2)
+    finally:
+        P.sg_destroy(h)
+    ref, _, _ = orc.solve(p, lev, g0, 100.0, max_steps=2, rule=orc.DT_CFL, cfl=0.4)
+    assert np.array_equal(uh, orc.combine(p, lev, co, ref))
+
+
+@pytest.mark.parametrize("nr,nl,exe,tp", CASES[:3], ids=lambda c: str(c))
+def test_vlasov_steps_fp32_within_tolerance(sg, orc, nr, nl, exe, tp):
+    r = _run(orc, nr, nl, P.SG_F32, exe, tp, 4)
+    assert r["steps"] == r["osteps"]
+    # |f| <= 0.42: 64 float roundings per stage on the state scale, three stages per step
+    tol = 64 * U32 * 3 * r["steps"] * 0.5
+    for g, ref in zip(r["got"], r["ref"]):
+        assert np.max(np.abs(g.astype(np.float64) - ref)) <= tol
+    expect = orc.combine(r["p"], r["lev"], r["co"], r["ref"])
+    assert np.max(np.abs(r["uh"] - expect)) <= 2 * tol
+
+
+def test_vlasov_landau_damping_full_configuration(sg):
+    """N_r = 16, N_L = 5 (finest 512^2), a = 0.01, k = 0.5, to t = 40 in FP32 (batched): the
+    field energy of the combined solution decays at the linear-theory rate 0.1533 (amplitude)
+    and the combined mass is conserved."""
+    import time
+    h = make(2, 16, 5, P.SG_PDE_VLASOV, precision=P.SG_F32, exec=P.SG_BATCHED, lo=LO, hi=HI,
+             dt_rule=P.SG_DT_CFL, cfl=0.4)
+    ts, amp = [], []
+    try:
+        P.sg_init(h, P.SG_IC_LANDAU, (0.01, 0.5))
+        P.sg_prolong_combine(h)
+        m0 = P.sg_reduce(h, -1, P.SG_REDUCE_MASS)
+        t, t_step = 0.0, 0.0
+        while t < 40.0 - 1e-12:
+            t0 = time.perf_counter()
+            t = P.sg_step(h, min(40.0, t + 0.5))
+            t_step += time.perf_counter() - t0
+            P.sg_prolong_combine(h)
+            ts.append(t)
+            amp.append(0.5 * math.log(P.sg_reduce(h, -1, P.SG_REDUCE_FIELD_ENERGY)))
+        m1 = P.sg_reduce(h, -1, P.SG_REDUCE_MASS)
+        steps = P.sg_time(h)[1]
+        G = P.sg_num_grids(h)
+        pts = sum(int(np.prod(s)) for s in _levels(h)[1])
+    finally:
+        P.sg_destroy(h)
+    pk = [i for i in range(1, len(amp) - 1) if amp[i] > amp[i - 1] and amp[i] > amp[i + 1] and ts[i] <= 25.0]
+    rate = -np.polyfit(np.array(ts)[pk], np.array(amp)[pk], 1)[0]
+    print("vlasov landau: %d grids, %d points, %d steps, stepping %.2f s, rate %.4f (linear theory 0.1533), "
+          "mass drift %.2e" % (G, pts, steps, t_step, rate, (m1 - m0) / m0))
+    assert abs(m1 - m0) < 1e-6 * m0
+    assert abs(rate - 0.1533) < 0.1 * 0.1533, rate
