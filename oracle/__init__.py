@@ -50,10 +50,11 @@ class Problem(C.Structure):
         ("dim", C.c_int), ("nr", C.c_int), ("nl", C.c_int), ("pde", C.c_int),
         ("scheme", C.c_int), ("prolong", C.c_int), ("eps", C.c_double),
         ("lo", C.c_double * MAXD), ("hi", C.c_double * MAXD), ("adv", C.c_double * MAXD),
+        ("theta", C.c_double), ("tau", C.c_double),
     ]
 
 
-ADVECTION, BURGERS, VLASOV = 0, 1, 2
+ADVECTION, BURGERS, VLASOV, VLASOV_BOLTZMANN = 0, 1, 2, 3
 WENO5, LINEAR5 = 0, 1
 PROLONG_WENO5, PROLONG_LAGRANGE5 = 0, 1
 DT_POW53, DT_CFL = 0, 1
@@ -90,6 +91,10 @@ def lib():
             "orc_efield": (None, [P, _ip, _dp, _dp]),
             "orc_restrict_landau": (None, [P, _ip, C.c_double, C.c_double, _dp]),
             "orc_field_energy": (C.c_double, [P, _ip, _dp]),
+            "orc_vb_density": (None, [P, _ip, _dp, _dp]),
+            "orc_relax_norm": (C.c_double, [P]),
+            "orc_restrict_relax": (None, [P, _ip, C.c_double, _dp]),
+            "orc_relax_entropy": (None, [P, _ip, _dp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "orc_exact_sine": (C.c_double, [P] + [C.c_double] * 4 + [_dp, C.c_double]),
             "orc_error_norms": (None, [P, _dp] + [C.c_double] * 5
                                 + [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -103,10 +108,11 @@ def lib():
 
 
 def problem(dim, nr, nl, pde=ADVECTION, scheme=WENO5, prolong=PROLONG_WENO5, eps=1e-6,
-            lo=0.0, hi=4.0, adv=1.0) -> Problem:
+            lo=0.0, hi=4.0, adv=1.0, theta=1.0, tau=1.0) -> Problem:
     p = Problem()
     p.dim, p.nr, p.nl, p.pde = dim, nr, nl, pde
     p.scheme, p.prolong, p.eps = scheme, prolong, eps
+    p.theta, p.tau = theta, tau
     lo = np.broadcast_to(np.asarray(lo, dtype=np.float64), (dim,))
     hi = np.broadcast_to(np.asarray(hi, dtype=np.float64), (dim,))
     adv = np.broadcast_to(np.asarray(adv, dtype=np.float64), (dim,))
@@ -270,3 +276,35 @@ def restrict_landau(p: Problem, levels, a, k):
 
 def field_energy(p: Problem, levels, u) -> float:
     return float(lib().orc_field_energy(C.byref(p), _lev(levels), np.ascontiguousarray(u, np.float64)))
+
+
+def vb_density(p: Problem, levels, u):
+    """rho(x) of one grid of the Vlasov-Boltzmann model (pde VLASOV_BOLTZMANN), flattened
+    over the space axes."""
+    n = shape(p, levels)
+    rho = np.empty(int(np.prod(n[:p.dim // 2])), dtype=np.float64)
+    lib().orc_vb_density(C.byref(p), _lev(levels), np.ascontiguousarray(u, np.float64), rho)
+    return rho
+
+
+def relax_norm(p: Problem) -> float:
+    """Normalisation s of the Example 5 initial condition (integral over the domain)."""
+    return float(lib().orc_relax_norm(C.byref(p)))
+
+
+def restrict_relax(p: Problem, levels, s_norm=None):
+    """Example 5 initial condition on one grid (pde VLASOV_BOLTZMANN, dim 2 or 4)."""
+    if s_norm is None:
+        s_norm = relax_norm(p)
+    u = np.empty(int(np.prod(shape(p, levels))), dtype=np.float64)
+    lib().orc_restrict_relax(C.byref(p), _lev(levels), float(s_norm), u)
+    return u
+
+
+def relax_entropy(p: Problem, levels, u):
+    """(H_2, H_log) of Example 5 over one grid's nodes (the finest grid for the combined
+    solution: levels all N_L)."""
+    h2, hl = C.c_double(), C.c_double()
+    lib().orc_relax_entropy(C.byref(p), _lev(levels), np.ascontiguousarray(u, np.float64),
+                            C.byref(h2), C.byref(hl))
+    return float(h2.value), float(hl.value)

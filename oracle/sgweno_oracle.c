@@ -41,6 +41,16 @@
  *    then the mean of E is subtracted (periodic E with zero mean);
  *  - E is recomputed from the input of every RK stage; the LF alpha of axis 0 is
  *    max_j |v_j| of the grid, of axis 1 max_i |E_i|.
+ * Vlasov-Boltzmann relaxation model (pde 3; Example 5), dim = 2 d with space axes 0..d-1
+ * and velocity axes d..2d-1:
+ *  - every axis has nodes lo_k + j h_k, j = 0..n_k-1, and f is zero outside them (the
+ *    zero boundary condition): stencils and interpolation read 0 beyond either end;
+ *  - the transport speed along x_k is the line's v_k, along v_k it is E_k = -x_k (the
+ *    potential |x|^2/2); the LF alpha of an axis is the largest |speed| over the grid;
+ *  - rho(x) = (h_{v_1} ... h_{v_d}) sum_v f(x, v), the velocity nodes in ascending
+ *    flattened order; mu_inf(v) = exp(-(|v|^2 / (2 theta))) / (2 pi theta)^{d/2} with |v|^2
+ *    summed in axis order; the relaxation term (mu_inf rho - f) / tau is added to the
+ *    transport operator after all axes, from the same stage input.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -54,12 +64,14 @@ typedef struct {
     int nl;            /* N_L, finest level */
     int pde;           /* 0: linear advection f_k = a_k u;  1: Burgers f_k = u^2/2;
                           2: Vlasov-Poisson (d = 2, axis 0 = x, axis 1 = v): f_x = v u,
-                          f_v = E(x) u, E from the grid's own density (see orc_efield) */
+                          f_v = E(x) u, E from the grid's own density (see orc_efield);
+                          3: Vlasov-Boltzmann relaxation (dim = 2d, see vb_operator) */
     int scheme;        /* 0: WENO5-JS weights (5);  1: fifth-order linear scheme, w_r = d_r */
     int prolong;       /* 0: WENO5 interpolation (11);  1: fifth-order Lagrange (8) */
     double eps;        /* epsilon of (5) and (9) */
     double lo[ORC_MAXD], hi[ORC_MAXD];
     double adv[ORC_MAXD];   /* a_k for linear advection */
+    double theta, tau;      /* pde 3: temperature and relaxation time of L(f) */
 } orc_problem;
 
 /* ------------------------------------------------------------------------------------
@@ -196,6 +208,27 @@ static double vnode(const orc_problem *P, long j, long nv)
     return P->lo[1] + (double)j * spacing(P, 1, nv);
 }
 
+/* Vlasov-Boltzmann (pde 3): the velocity axis of space axis k and vice versa. */
+static int vb_partner(const orc_problem *P, int k)
+{
+    int d = P->dim / 2;
+    return k < d ? k + d : k - d;
+}
+
+/* Node j of axis k on a grid with nk nodes on that axis. */
+static double node(const orc_problem *P, int k, long j, long nk)
+{
+    return P->lo[k] + (double)j * spacing(P, k, nk);
+}
+
+/* Transport speed along axis k on the lines through node jp of the partner axis:
+ * v_k along x_k, E_k = -x_k along v_k. */
+static double vb_speed(const orc_problem *P, int k, long jp, long np)
+{
+    double c = node(P, vb_partner(P, k), jp, np);
+    return k < P->dim / 2 ? c : -c;
+}
+
 /* Flux of one axis, Eq. (1): f_k(u) = a_k u (advection) or u^2/2 (Burgers). */
 static double flux(const orc_problem *P, int k, double u)
 {
@@ -230,6 +263,14 @@ double orc_lf_alpha(const orc_problem *P, const int *levels, const double *u, in
                 if (s > a) a = s;
             }
             free(E);
+        }
+        return a;
+    }
+    if (P->pde == 3) {  /* the largest |speed| of the axis: |v_k| or |x_k| at the nodes */
+        int pk = vb_partner(P, k);
+        for (p = 0; p < n[pk]; ++p) {
+            double s = fabs(vb_speed(P, k, p, n[pk]));
+            if (s > a) a = s;
         }
         return a;
     }
@@ -304,6 +345,95 @@ static void vp_operator(const orc_problem *P, const int *levels, const double *u
     free(F);
 }
 
+/* Density of one grid (pde 3): rho[ix] = (h_{v_1} ... h_{v_d}) sum_jv f[ix + nx jv] over the
+ * flattened velocity index jv in ascending order; ix is the flattened space index. */
+void orc_vb_density(const orc_problem *P, const int *levels, const double *u, double *rho)
+{
+    long n[ORC_MAXD], nx = 1, nv = 1, ix, jv;
+    double hv = 1.0;
+    int k, d = P->dim / 2;
+    grid_points(P, levels, n);
+    for (k = 0; k < d; ++k) nx *= n[k];
+    for (k = d; k < P->dim; ++k) {
+        nv *= n[k];
+        hv = hv * spacing(P, k, n[k]);
+    }
+    for (ix = 0; ix < nx; ++ix) {
+        double s = 0.0;
+        for (jv = 0; jv < nv; ++jv) s = s + u[ix + nx * jv];
+        rho[ix] = hv * s;
+    }
+}
+
+/* Absolute Maxwellian mu_inf at the flattened velocity node jv (pde 3). */
+double orc_vb_maxwellian(const orc_problem *P, const long *n, long jv)
+{
+    int k, d = P->dim / 2;
+    double s = 0.0;
+    for (k = d; k < P->dim; ++k) {
+        double v = node(P, k, jv % n[k], n[k]);
+        jv /= n[k];
+        s = s + v * v;
+    }
+    return exp(-(s / (2.0 * P->theta))) / pow(2.0 * 3.14159265358979323846 * P->theta, 0.5 * (double)d);
+}
+
+/* Vlasov-Boltzmann operator (pde 3): for axes 0, 1, ... the LF-split WENO5 flux difference
+ * of f_k = speed * u, the speed constant on each line (v_k along x_k, -x_k along v_k),
+ * values zero beyond both ends (n_k + 1 interfaces per line); then
+ * L += (mu_inf(v) rho(x) - u) / tau. */
+static void vb_operator(const orc_problem *P, const int *levels, const double *u, const long *n,
+                        double *L)
+{
+    long stride[ORC_MAXD], N = 1, nmax = 0, nx = 1, p;
+    int k, d = P->dim / 2;
+    double *fp, *fm, *F, *rho;
+    for (k = 0; k < P->dim; ++k) {
+        stride[k] = N;
+        N *= n[k];
+        if (n[k] > nmax) nmax = n[k];
+    }
+    for (k = 0; k < d; ++k) nx *= n[k];
+    fp = (double *)malloc(sizeof(double) * (nmax + 6));
+    fm = (double *)malloc(sizeof(double) * (nmax + 6));
+    F = (double *)malloc(sizeof(double) * (nmax + 1));
+    for (k = 0; k < P->dim; ++k) {
+        int pk = vb_partner(P, k);
+        long nk = n[k], sk = stride[k], nlines = N / nk, line, m;
+        double alpha = orc_lf_alpha(P, levels, u, k);
+        double rdx = 1.0 / spacing(P, k, nk);
+        for (line = 0; line < nlines; ++line) {
+            long below = line % sk, above = line / sk;
+            long base = below + above * sk * nk;
+            double a = vb_speed(P, k, (base / stride[pk]) % n[pk], n[pk]);
+            /* fp/fm hold nodes -3..nk+2 at offset 3; interface m + 1/2 (m = -1..nk-1) at F[m + 1] */
+            for (m = -3; m < nk + 3; ++m) {
+                double uj = (m < 0 || m >= nk) ? 0.0 : u[base + m * sk];
+                double fj = a * uj;
+                fp[m + 3] = 0.5 * (fj + alpha * uj);
+                fm[m + 3] = 0.5 * (fj - alpha * uj);
+            }
+            for (m = -1; m < nk; ++m) {
+                const double *P5 = fp + m + 3, *M5 = fm + m + 3;
+                double fplus = orc_weno5_side(P5[-2], P5[-1], P5[0], P5[1], P5[2], P->eps, P->scheme == 1);
+                double fminus = orc_weno5_side(M5[3], M5[2], M5[1], M5[0], M5[-1], P->eps, P->scheme == 1);
+                F[m + 1] = fplus + fminus;
+            }
+            for (m = 0; m < nk; ++m) L[base + m * sk] = L[base + m * sk] - (F[m + 1] - F[m]) * rdx;
+        }
+    }
+    rho = (double *)malloc(sizeof(double) * nx);
+    orc_vb_density(P, levels, u, rho);
+    for (p = 0; p < N; ++p) {
+        double mu = orc_vb_maxwellian(P, n, p / nx);
+        L[p] = L[p] + (mu * rho[p % nx] - u[p]) / P->tau;
+    }
+    free(rho);
+    free(fp);
+    free(fm);
+    free(F);
+}
+
 /* ------------------------------------------------------------------------------------
  * Spatial operator L(u) = - sum_k (fhat_{i+1/2} - fhat_{i-1/2}) / h_k, Eq. (2) applied
  * dimension by dimension (Section 2.1), with the LF split (7) and fhat = fhat^+ + fhat^-.
@@ -319,6 +449,10 @@ void orc_spatial_operator(const orc_problem *P, const int *levels, const double 
     for (p = 0; p < N; ++p) L[p] = 0.0;
     if (P->pde == 2) {
         vp_operator(P, levels, u, n, L);
+        return;
+    }
+    if (P->pde == 3) {
+        vb_operator(P, levels, u, n, L);
         return;
     }
 
@@ -506,6 +640,91 @@ double orc_field_energy(const orc_problem *P, const int *levels, const double *u
     return 0.5 * s * spacing(P, 0, n[0]);
 }
 
+/* Example 5 initial condition, without its normalisation: the factor of space axis k,
+ * g_0(x) = sin(x^2/2)^2 exp(-x^2/2), g_1(x) = cos(x^2/2)^2 exp(-x^2/2), and of a velocity
+ * axis, exp(-v^2/2). */
+static double relax_factor(const orc_problem *P, int k, double x)
+{
+    double e = exp(-0.5 * (x * x));
+    if (k >= P->dim / 2) return e;
+    if (k == 0) {
+        double sn = sin(0.5 * (x * x));
+        return (sn * sn) * e;
+    } else {
+        double cs = cos(0.5 * (x * x));
+        return (cs * cs) * e;
+    }
+}
+
+/* Normalisation s of Example 5: the integral over the domain of the product of the factors
+ * above, one composite Simpson rule per axis (the integrand is a product of one-axis
+ * functions), 2 * 10^5 intervals per axis. */
+double orc_relax_norm(const orc_problem *P)
+{
+    const long m = 200000;
+    double s = 1.0;
+    int k;
+    for (k = 0; k < P->dim; ++k) {
+        double a = P->lo[k], b = P->hi[k], h = (b - a) / (double)m, acc;
+        long i;
+        acc = relax_factor(P, k, a) + relax_factor(P, k, b);
+        for (i = 1; i < m; ++i) acc = acc + (i % 2 ? 4.0 : 2.0) * relax_factor(P, k, a + (double)i * h);
+        s = s * (acc * h / 3.0);
+    }
+    return s;
+}
+
+/* Example 5 initial condition at the nodes of one grid (pde 3, dim 2 or 4):
+ * f_0 = (1/s) prod_k factor_k(x_k). */
+void orc_restrict_relax(const orc_problem *P, const int *levels, double s_norm, double *u)
+{
+    long n[ORC_MAXD];
+    long N = grid_points(P, levels, n), p;
+    int k;
+    for (p = 0; p < N; ++p) {
+        long r = p;
+        double f = 1.0;
+        for (k = 0; k < P->dim; ++k) {
+            f = f * relax_factor(P, k, node(P, k, r % n[k], n[k]));
+            r /= n[k];
+        }
+        u[p] = f / s_norm;
+    }
+}
+
+/* Entropy functionals of Example 5 on one grid's nodes (pde 3):
+ *   H_2 = sum f^2 / M dV,  H_log = sum f log(f / M) dV (nodes with f <= 0 add 0),
+ * with the stationary state M = exp(-(|v|^2/2 + |x|^2/2)/theta) / ((2 pi theta)^{d/2} Z),
+ * Z = prod_k int_{lo_k}^{hi_k} exp(-x^2 / (2 theta)) dx = prod_k sqrt(pi theta / 2)
+ * (erf(hi_k / sqrt(2 theta)) - erf(lo_k / sqrt(2 theta))), and dV the cell volume. */
+void orc_relax_entropy(const orc_problem *P, const int *levels, const double *u, double *h2,
+                       double *hlog)
+{
+    long n[ORC_MAXD];
+    long N = grid_points(P, levels, n), p;
+    int k, d = P->dim / 2;
+    double Z = 1.0, vol = 1.0, c, s2 = 0.0, sl = 0.0;
+    double rt = sqrt(2.0 * P->theta);
+    for (k = 0; k < d; ++k)
+        Z = Z * (sqrt(3.14159265358979323846 * P->theta / 2.0) * (erf(P->hi[k] / rt) - erf(P->lo[k] / rt)));
+    for (k = 0; k < P->dim; ++k) vol = vol * spacing(P, k, n[k]);
+    c = pow(2.0 * 3.14159265358979323846 * P->theta, 0.5 * (double)d) * Z;
+    for (p = 0; p < N; ++p) {
+        long r = p;
+        double q = 0.0, M, f = u[p];
+        for (k = 0; k < P->dim; ++k) {
+            double x = node(P, k, r % n[k], n[k]);
+            r /= n[k];
+            q = q + 0.5 * (x * x);
+        }
+        M = exp(-(q / P->theta)) / c;
+        s2 = s2 + (f * f) / M;
+        if (f > 0.0) sl = sl + f * log(f / M);
+    }
+    *h2 = s2 * vol;
+    *hlog = sl * vol;
+}
+
 /* ------------------------------------------------------------------------------------
  * One-dimensional fifth-order interpolation at x = x_i + s h, s in [-1/2, 1/2),
  * Section 2.2.1, Eqs. (8)-(11).  (a..e) = (u_{i-2}, ..., u_{i+2}).
@@ -542,6 +761,13 @@ double orc_weno5_interp(double a, double b, double c, double d, double e, double
         w2 = C2 / ((eps + b2) * (eps + b2));
         return (w0 * P0 + w1 * P1 + w2 * P2) / (w0 + w1 + w2);
     }
+}
+
+/* Axes with zero values beyond the ends: v of the Vlasov-Poisson workload, every axis of
+ * the Vlasov-Boltzmann model; the others are periodic. */
+static int zero_axis(const orc_problem *P, int k)
+{
+    return (P->pde == 2 && k == 1) || P->pde == 3;
 }
 
 /* Coarse centre and offset of fine node jf on an axis refined by ratio r = 2^{N_L - l}:
@@ -599,7 +825,7 @@ void orc_prolong_grid(const orc_problem *P, const int *levels, const double *u, 
                 long ic;
                 double s;
                 fine_to_coarse(jf, r, &ic, &s);
-                if (P->pde == 2 && k == 1) {  /* v: zero beyond the ends */
+                if (zero_axis(P, k)) {  /* zero beyond the ends */
                     double v5[5];
                     int t;
                     for (t = 0; t < 5; ++t) {
@@ -682,7 +908,7 @@ static double prolong_rec(const orc_problem *P, const int *levels, const long *n
         return prolong_rec(P, levels, n, u, k - 1, J, ci);
     }
     for (t = 0; t < 5; ++t) {
-        if (P->pde == 2 && k == 1) {  /* v: zero beyond the ends */
+        if (zero_axis(P, k)) {  /* zero beyond the ends */
             long c = ic - 2 + t;
             if (c < 0 || c >= n[k]) {
                 v[t] = 0.0;
