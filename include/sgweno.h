@@ -52,8 +52,18 @@ typedef enum {
  * its own field: rho_i = h_v sum_j f_ij, E from dE/dx = rho - mean(rho) integrated by the
  * trapezoid rule from E_0 = 0 and shifted to zero mean, recomputed at every RK stage; the LF
  * alpha of Eq. (7) is max|v_j| along x and max|E_i| along v. */
-enum { SG_PDE_ADVECTION = 0, SG_PDE_BURGERS = 1, SG_PDE_VLASOV = 2 };
-/* Boundary conditions: periodic (SG_PDE_VLASOV: zero inflow in v, implied). */
+/* SG_PDE_VLASOV_BOLTZMANN: the relaxation model of Example 5,
+ *   f_t + v . grad_x f + E(x) . grad_v f = (mu_inf(v) rho(x) - f) / tau,  E = -x,
+ * dim = 2 d (d = 1, 2 or 3): axes 0..d-1 are x, axes d..2d-1 are v.  Every axis has nodes
+ * lo_k + j h_k, j = 0..n_k-1, with f = 0 beyond them (the zero boundary condition; bc is
+ * ignored).  The flux along x_k is v_k f and along v_k it is -x_k f, with the line's node on
+ * the partner axis; the LF alpha of an axis is the largest |partner node| of the grid.
+ * rho(x) = (h_{v_1} ... h_{v_d}) sum_v f(x, v) is formed from the input of every RK stage;
+ * mu_inf(v) = exp(-(|v|^2 / (2 theta))) / (2 pi theta)^{d/2} at the velocity nodes (theta and
+ * tau from sg_params). */
+enum { SG_PDE_ADVECTION = 0, SG_PDE_BURGERS = 1, SG_PDE_VLASOV = 2, SG_PDE_VLASOV_BOLTZMANN = 3 };
+/* Boundary conditions: periodic (SG_PDE_VLASOV: zero inflow in v, implied;
+ * SG_PDE_VLASOV_BOLTZMANN: zero on every axis, implied). */
 enum { SG_BC_PERIODIC = 0 };
 /* Precision of the component-grid states and the WENO arithmetic.  The combination sum
  * (the finest-grid accumulator) and every reduction are FP64 in both. */
@@ -84,17 +94,25 @@ enum { SG_DT_POW53 = 0, SG_DT_CFL = 1 };
  *                 with a register window; tile_points is ignored. */
 enum { SG_STAGE_AUTO = 0, SG_STAGE_TILED = 1, SG_STAGE_SWEEP = 2 };
 /* Initial condition kinds for sg_init. SG_IC_SINE: u_0(x) = p0 + p1 sin(p2 (x_0+...+x_{d-1}) + p3).
- * SG_IC_LANDAU (SG_PDE_VLASOV only, 2 parameters a, k): f_0 = (1 + a cos(k x)) exp(-v^2/2)/sqrt(2 pi). */
-enum { SG_IC_SINE = 0, SG_IC_LANDAU = 1 };
+ * SG_IC_LANDAU (SG_PDE_VLASOV only, 2 parameters a, k): f_0 = (1 + a cos(k x)) exp(-v^2/2)/sqrt(2 pi).
+ * SG_IC_RELAX (SG_PDE_VLASOV_BOLTZMANN with dim 2 or 4, no parameters): the initial condition
+ * of Example 5, f_0 = (1/s) sin(x_1^2/2)^2 [cos(x_2^2/2)^2] exp(-(|x|^2 + |v|^2)/2), s the
+ * integral of the rest over the domain (so that f_0 has unit mass). */
+enum { SG_IC_SINE = 0, SG_IC_LANDAU = 1, SG_IC_RELAX = 2 };
 /* Reductions (FP64).  MASS = sum u prod h, ENERGY = sum u^2 prod h, MIN/MAX of the values;
  * L1_EXACT = mean |u - u_exact|, LINF_EXACT = max |u - u_exact| against the exact solution of
  * the SG_IC_SINE initial condition at the current time (advection: translation; Burgers:
  * characteristic solution by Newton's method, valid before the shock time). */
 /* FIELD_ENERGY (SG_PDE_VLASOV only): (1/2) sum_i E_i^2 h_x of the field of grid `which` or of
  * the combined solution, E as described for SG_PDE_VLASOV. */
+/* ENTROPY_H2 / ENTROPY_LOG (SG_PDE_VLASOV_BOLTZMANN only): the entropy functionals of
+ * Example 5 over the nodes, sum f^2 / M dV and sum_{f > 0} f log(f / M) dV, with the stationary
+ * state M = exp(-(|x|^2/2 + |v|^2/2) / theta) / ((2 pi theta)^{d/2} Z), Z = the integral of
+ * exp(-|x|^2 / (2 theta)) over the space domain. */
 enum {
     SG_REDUCE_MASS = 0, SG_REDUCE_ENERGY = 1, SG_REDUCE_MIN = 2, SG_REDUCE_MAX = 3,
-    SG_REDUCE_L1_EXACT = 4, SG_REDUCE_LINF_EXACT = 5, SG_REDUCE_FIELD_ENERGY = 6
+    SG_REDUCE_L1_EXACT = 4, SG_REDUCE_LINF_EXACT = 5, SG_REDUCE_FIELD_ENERGY = 6,
+    SG_REDUCE_ENTROPY_H2 = 7, SG_REDUCE_ENTROPY_LOG = 8
 };
 
 #define SG_MAX_DIM 6
@@ -125,6 +143,8 @@ typedef struct {
                                     use for intermediates; above it (or if < 0) uhat is accumulated
                                     grid by grid instead.  0 = default (8 GB) */
     int stage_kernel;            /* SG_STAGE_AUTO (default), SG_STAGE_TILED or SG_STAGE_SWEEP */
+    double theta;                /* SG_PDE_VLASOV_BOLTZMANN: temperature of mu_inf; default 1 */
+    double tau;                  /* SG_PDE_VLASOV_BOLTZMANN: relaxation time (> 0); default 1 */
 } sg_params;
 
 /* Fills *p with the defaults listed above.  SG_ERR_ARG if p is NULL. */

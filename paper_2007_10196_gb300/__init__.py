@@ -21,7 +21,7 @@ MAX_DIM = 6
 # status codes
 SG_OK, SG_ERR_ARG, SG_ERR_STATE, SG_ERR_NOMEM, SG_ERR_CUDA = 0, 1, 2, 3, 4
 SG_ERR_NONFINITE, SG_ERR_TIMEOUT, SG_ERR_UNSUPPORTED = 5, 6, 7
-SG_PDE_ADVECTION, SG_PDE_BURGERS, SG_PDE_VLASOV = 0, 1, 2
+SG_PDE_ADVECTION, SG_PDE_BURGERS, SG_PDE_VLASOV, SG_PDE_VLASOV_BOLTZMANN = 0, 1, 2, 3
 SG_BC_PERIODIC = 0
 SG_F64, SG_F32 = 0, 1
 SG_PLAIN, SG_BATCHED = 0, 1
@@ -29,9 +29,10 @@ SG_WENO5, SG_LINEAR5 = 0, 1
 SG_PROLONG_WENO5, SG_PROLONG_LAGRANGE5 = 0, 1
 SG_DT_POW53, SG_DT_CFL = 0, 1
 SG_STAGE_AUTO, SG_STAGE_TILED, SG_STAGE_SWEEP = 0, 1, 2
-SG_IC_SINE, SG_IC_LANDAU = 0, 1
+SG_IC_SINE, SG_IC_LANDAU, SG_IC_RELAX = 0, 1, 2
 SG_REDUCE_MASS, SG_REDUCE_ENERGY, SG_REDUCE_MIN, SG_REDUCE_MAX = 0, 1, 2, 3
 SG_REDUCE_L1_EXACT, SG_REDUCE_LINF_EXACT, SG_REDUCE_FIELD_ENERGY = 4, 5, 6
+SG_REDUCE_ENTROPY_H2, SG_REDUCE_ENTROPY_LOG = 7, 8
 SG_WHICH_COMBINED, SG_WHICH_ALL_GRIDS = -1, -2
 
 EXPORTED = [
@@ -59,6 +60,7 @@ class sg_params(C.Structure):
         ("eps", C.c_double), ("dt_rule", C.c_int), ("dt_coef", C.c_double), ("cfl", C.c_double),
         ("cuda_stream", C.c_void_p), ("graph_steps", C.c_int), ("tile_points", C.c_int),
         ("combine_budget_gb", C.c_double), ("stage_kernel", C.c_int),
+        ("theta", C.c_double), ("tau", C.c_double),
     ]
 
 

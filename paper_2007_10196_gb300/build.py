@@ -6,6 +6,9 @@ paper_2007_10196_gb300/libsgweno.so:
   sg_kernels_f32.cu  -- FP32 kernels
   sg_api.cu          -- the C ABI
   sg_noalloc.cu      -- sg_step_grid_noalloc and its static scratch, --fmad=false
+Host code of every unit is compiled with -ffp-contract=off: GCC contracts a * b + c into one
+fused multiply-add by default on aarch64, and the host-computed tables (the Maxwellian at the
+velocity nodes) must round like their plain definitions on every machine.
 """
 from __future__ import annotations
 
@@ -55,7 +58,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+                     "-I", INCLUDE, "-I", CSRC]
 
     def compile_one(item):
         src, extra = item

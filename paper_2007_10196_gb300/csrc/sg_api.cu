@@ -151,8 +151,12 @@ struct sg_ctx {
     std::vector<long long> offset;  // element offset of each grid inside a state region
     long long total_pts = 0;
     DevBuf arena;  // state regions u0, u1, u2 (and u3 = C for FP32), each all grids concatenated
-    DevBuf efield; // Vlasov-Poisson: E of every grid (n_0 values each), grids concatenated
+    DevBuf efield; // Vlasov-Poisson: E of every grid (n_0 values each); Vlasov-Boltzmann: rho
+                   // (n_0 ... n_{d/2-1} values each); grids concatenated
     std::vector<long long> ef_offset;
+    DevBuf mutab;  // Vlasov-Boltzmann: mu_inf at the velocity nodes of every grid, concatenated
+    std::vector<long long> mu_offset;
+    long long max_nx = 0;  // Vlasov-Boltzmann: largest space-node count of a grid
     long long box_elems = 0;  // stage kernel: elements of one padded box (d <= 3)
     size_t smem = 0;          // stage kernel: dynamic shared memory per block
     // device tables (single handle or batch)
@@ -208,6 +212,7 @@ PhysParams phys_of(const sg_ctx* h) {
     ph.eps = h->prm.eps;
     for (int k = 0; k < SG_MAXD; ++k) ph.adv[k] = k < h->dim ? h->prm.adv_speed[k] : 0.0;
     ph.alpha_f32 = h->esize == 4;
+    ph.tau = h->prm.tau;
     return ph;
 }
 
@@ -276,8 +281,8 @@ void stage_footprint(sg_ctx* h) {
         flux = std::max(flux, f);
     }
     h->box_elems = box;
-    h->smem = h->esize == 8 ? sg::Launch<double>::stage_smem(h->dim, h->ppt, box, flux)
-                            : sg::Launch<float>::stage_smem(h->dim, h->ppt, box, flux);
+    h->smem = h->esize == 8 ? sg::Launch<double>::stage_smem(h->dim, h->ppt, box, flux, h->variant)
+                            : sg::Launch<float>::stage_smem(h->dim, h->ppt, box, flux, h->variant);
 }
 
 int stage_blocks_per_sm(const sg_ctx* h) {
@@ -298,12 +303,85 @@ void swap_pair(GridDesc* grids, int n) {
     for (int g = 0; g < n; ++g) std::swap(grids[g].u0, grids[g].u1);
 }
 
+// Vlasov-Boltzmann: the density buffers and the table of mu_inf at every grid's velocity
+// nodes, mu_inf(v) = exp(-(|v|^2 / (2 theta))) / (2 pi theta)^{d/2}, |v|^2 summed in axis order,
+// v_k = lo_k + j h_k (evaluated on the host in FP64; the FP32 table holds the rounded values).
+sg_status relax_tables(sg_ctx* h) {
+    const int dx = h->dim / 2;
+    long long ef_total = 0, mu_total = 0;
+    for (int g = 0; g < h->G; ++g) {
+        long long nx = 1, nv = 1;
+        for (int k = 0; k < dx; ++k) nx *= (long long)h->nr << h->levels[g][k];
+        for (int k = dx; k < h->dim; ++k) nv *= (long long)h->nr << h->levels[g][k];
+        h->ef_offset.push_back(ef_total);
+        h->mu_offset.push_back(mu_total);
+        ef_total += nx;
+        mu_total += nv;
+        h->max_nx = std::max(h->max_nx, nx);
+    }
+    SG_TRY(h->efield.alloc((size_t)ef_total * h->esize));
+    SG_TRY(h->mutab.alloc((size_t)mu_total * h->esize));
+    std::vector<double> mu((size_t)mu_total);
+    const double theta = h->prm.theta;
+    const double norm = std::pow(2.0 * 3.14159265358979323846 * theta, 0.5 * (double)dx);
+    for (int g = 0; g < h->G; ++g) {
+        long long nv = 1;
+        int n[SG_MAXD];
+        double hk[SG_MAXD];
+        for (int k = dx; k < h->dim; ++k) {
+            n[k] = h->nr << h->levels[g][k];
+            hk[k] = (h->prm.hi[k] - h->prm.lo[k]) / (double)n[k];
+            nv *= n[k];
+        }
+        for (long long jv = 0; jv < nv; ++jv) {
+            long long r = jv;
+            double s2 = 0.0;
+            for (int k = dx; k < h->dim; ++k) {
+                const double v = h->prm.lo[k] + (double)(r % n[k]) * hk[k];
+                r /= n[k];
+                s2 = s2 + v * v;
+            }
+            mu[(size_t)(h->mu_offset[g] + jv)] = std::exp(-(s2 / (2.0 * theta))) / norm;
+        }
+    }
+    if (h->esize == 8) {
+        SG_CUDA(cudaMemcpy(h->mutab.p, mu.data(), sizeof(double) * mu.size(), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> muf(mu.begin(), mu.end());
+        SG_CUDA(cudaMemcpy(h->mutab.p, muf.data(), sizeof(float) * muf.size(), cudaMemcpyHostToDevice));
+    }
+    return SG_OK;
+}
+
+// Normalisation s of the Example 5 initial condition: the integral over the domain of
+// prod_k factor_k, a product of one-axis integrals, each by the composite Simpson rule on
+// 2 * 10^5 intervals.
+double relax_norm(const sg_ctx* h) {
+    const int dx = h->dim / 2;
+    const long m = 200000;
+    double s = 1.0;
+    for (int k = 0; k < h->dim; ++k) {
+        const double a = h->prm.lo[k], b = h->prm.hi[k], step = (b - a) / (double)m;
+        auto f = [&](double x) {
+            const double e = std::exp(-0.5 * x * x);
+            if (k >= dx) return e;
+            const double t = k == 0 ? std::sin(0.5 * x * x) : std::cos(0.5 * x * x);
+            return t * t * e;
+        };
+        double acc = f(a) + f(b);
+        for (long i = 1; i < m; ++i) acc += (i & 1 ? 4.0 : 2.0) * f(a + (double)i * step);
+        s *= acc * step / 3.0;
+    }
+    return s;
+}
+
 sg_status validate_params(const sg_params* p, int dim) {
     if (p->struct_size != sizeof(sg_params)) return fail(SG_ERR_ARG, "sg_params.struct_size mismatch (use sg_params_init)");
     for (int k = 0; k < dim; ++k) {
         if (!(std::isfinite(p->lo[k]) && std::isfinite(p->hi[k]) && p->hi[k] > p->lo[k]))
             return fail(SG_ERR_ARG, "domain axis %d: need finite lo < hi", k);
-        if (p->bc[k] != SG_BC_PERIODIC) return fail(SG_ERR_UNSUPPORTED, "only periodic boundaries are implemented");
+        if (p->bc[k] != SG_BC_PERIODIC)
+            return fail(SG_ERR_UNSUPPORTED, "only periodic boundaries are implemented (the kinetic PDEs imply theirs)");
         if (!std::isfinite(p->adv_speed[k])) return fail(SG_ERR_ARG, "adv_speed[%d] not finite", k);
     }
     if (p->precision != SG_F64 && p->precision != SG_F32) return fail(SG_ERR_ARG, "precision");
@@ -319,6 +397,8 @@ sg_status validate_params(const sg_params* p, int dim) {
         return fail(SG_ERR_ARG, "stage_kernel");
     if (p->stage_kernel == SG_STAGE_SWEEP && dim != 3)
         return fail(SG_ERR_UNSUPPORTED, "the sweep stage kernel is implemented for d = 3 only");
+    if (!(p->theta > 0.0) || !std::isfinite(p->theta) || !(p->tau > 0.0) || std::isnan(p->tau))
+        return fail(SG_ERR_ARG, "theta must be finite and > 0, tau > 0");
     return SG_OK;
 }
 
@@ -340,7 +420,9 @@ sg_status build_tables(sg_ctx* h) {
         d.u1 = keep.empty() ? base + region + (size_t)h->offset[g] * h->esize : keep[g].second;
         d.u2 = base + 2 * region + (size_t)h->offset[g] * h->esize;
         d.u3 = h->esize == 4 ? base + 3 * region + (size_t)h->offset[g] * h->esize : nullptr;
-        d.ef = h->pde == SG_PDE_VLASOV ? h->efield.as<char>() + (size_t)h->ef_offset[g] * h->esize : nullptr;
+        d.ef = h->pde == SG_PDE_VLASOV || h->pde == SG_PDE_VLASOV_BOLTZMANN
+                   ? h->efield.as<char>() + (size_t)h->ef_offset[g] * h->esize : nullptr;
+        d.mu = h->pde == SG_PDE_VLASOV_BOLTZMANN ? h->mutab.as<char>() + (size_t)h->mu_offset[g] * h->esize : nullptr;
         d.npts = h->npts[g];
         int n[SG_MAXD] = {1, 1, 1, 1, 1, 1};
         for (int k = 0; k < h->dim; ++k) n[k] = h->nr << h->levels[g][k];
@@ -418,6 +500,15 @@ cudaError_t launch_efield(const sg_ctx* h, int stage, int pre_dt) {
                                            h->alpha.as<unsigned long long>(), stage, pre_dt, h->stream);
 }
 
+// Vlasov-Boltzmann: the density of every grid of the handle (or batch) from the stage input.
+cudaError_t launch_density(const sg_ctx* h, int stage) {
+    const int ng = (int)h->hgrids.size();
+    return h->esize == 8 ? sg::Launch<double>::density(h->dgrids.as<GridDesc>(), ng, h->max_nx, h->dinst.as<InstState>(),
+                                                       stage, h->dim, h->stream)
+                         : sg::Launch<float>::density(h->dgrids.as<GridDesc>(), ng, h->max_nx, h->dinst.as<InstState>(),
+                                                      stage, h->dim, h->stream);
+}
+
 // Enqueues `nsteps` time steps (dt control + three RK stages each) on the handle's stream.
 // With profiling on, each stage launch (or per-grid launch group) is bracketed by an event pair.
 sg_status enqueue_steps(sg_ctx* h, int nsteps, long long* kernels) {
@@ -446,6 +537,10 @@ sg_status enqueue_steps(sg_ctx* h, int nsteps, long long* kernels) {
             const int pair = 3 * s + stage;
             if (h->pde == SG_PDE_VLASOV && stage > 0) {
                 SG_CUDA(launch_efield(h, stage, 0));
+                ++nk;
+            }
+            if (h->pde == SG_PDE_VLASOV_BOLTZMANN) {  // rho of the stage input
+                SG_CUDA(launch_density(h, stage));
                 ++nk;
             }
             if (h->profile) SG_CUDA(cudaEventRecordWithFlags(h->ev[2 * pair], h->stream, cudaEventRecordExternal));
@@ -535,6 +630,7 @@ sg_status build_batch_tables(sg_ctx* h) {
             h->hgrids.push_back(d);
         }
         h->max_grid_pts = std::max(h->max_grid_pts, m->max_grid_pts);
+        h->max_nx = std::max(h->max_nx, m->max_nx);
     }
     if (h->dgrids.bytes < sizeof(GridDesc) * h->hgrids.size()) SG_TRY(h->dgrids.alloc(sizeof(GridDesc) * h->hgrids.size()));
     if (h->ditems.bytes < sizeof(WorkItem) * h->hitems.size()) SG_TRY(h->ditems.alloc(sizeof(WorkItem) * h->hitems.size()));
@@ -609,6 +705,7 @@ sg_status time_stage0(sg_ctx* h, double* ms) {
     SG_CUDA(cudaMemcpyAsync(h->dinst.p, h->hinst.p, sizeof(InstState) * h->ninst, cudaMemcpyHostToDevice, h->stream));
     SG_CUDA(cudaMemsetAsync(h->alpha.p, 0, h->alpha.bytes, h->stream));
     if (h->pde == SG_PDE_VLASOV) SG_CUDA(launch_efield(h, 0, 0));
+    if (h->pde == SG_PDE_VLASOV_BOLTZMANN) SG_CUDA(launch_density(h, 0));
     cudaEvent_t e0, e1;
     SG_CUDA(cudaEventCreate(&e0));
     SG_CUDA(cudaEventCreate(&e1));
@@ -668,7 +765,8 @@ sg_status autotune(sg_ctx* h) {
         }
     }
     std::vector<std::pair<int, int>> cand;
-    if (h->dim == 3) cand = {{0, 2}, {1, 2}, {1, 4}};
+    if (h->pde == SG_PDE_VLASOV_BOLTZMANN) cand = {{2, 1}, {2, 2}, {2, 4}};
+    else if (h->dim == 3) cand = {{0, 2}, {1, 2}, {1, 4}};
     else cand = {{0, 1}, {0, 2}, {0, 4}};
     double best = INFINITY;
     std::pair<int, int> pick = cand[0];
@@ -742,6 +840,12 @@ sg_status run_steps(sg_ctx* h) {
     return SG_OK;
 }
 
+// Axes with zero values beyond the ends: v of the Vlasov-Poisson system, every axis of the
+// Vlasov-Boltzmann model; the others are periodic.
+bool zero_axis(const sg_ctx* h, int k) {
+    return (h->pde == SG_PDE_VLASOV && k == 1) || h->pde == SG_PDE_VLASOV_BOLTZMANN;
+}
+
 // Prolongation of every grid onto the finest grid and the combination sum, one grid at a time:
 // the last prolonged axis of each grid adds c_g times its values into uhat (a read-modify-write
 // of uhat per grid).  Used when the fused form's intermediates exceed the memory budget.
@@ -797,7 +901,7 @@ sg_status prolong_combine_rmw_t(sg_ctx* h) {
             T* dst = last ? nullptr : bufs[a & 1];
             SG_CUDA(sg::Launch<T>::prolong_axis(src, dst, last ? acc : nullptr, gd.coeff, below, (int)m[k],
                                                 (int)Nf, above, r, h->prm.eps, h->prm.prolong,
-                                                (h->pde == SG_PDE_VLASOV && k == 1) ? 1 : 0, h->stream));
+                                                zero_axis(h, k) ? 1 : 0, h->stream));
             h->launches += 1;
             m[k] = Nf;
             src = dst;
@@ -868,7 +972,7 @@ sg_status prolong_combine_fused_t(sg_ctx* h, CombineBuffers& cb) {
             for (int j = k + 1; j < d; ++j) hi *= m[j];
             T* dst = a + 1 == axes.size() ? cb.pool.as<T>() + slot[g] : bufs[a & 1];
             SG_CUDA(sg::Launch<T>::prolong_axis_win(src, dst, lo, (int)m[k], (int)Nf, hi, 1 << (h->nl - gd.lev[k]),
-                                                    h->prm.eps, h->prm.prolong, h->stream));
+                                                    h->prm.eps, h->prm.prolong, zero_axis(h, k) ? 1 : 0, h->stream));
             h->launches += 1;
             m[k] = Nf;
             src = dst;
@@ -885,7 +989,7 @@ sg_status prolong_combine_fused_t(sg_ctx* h, CombineBuffers& cb) {
         exact = exact && a >= 1.0 && std::ldexp(1.0, std::ilogb(a)) == a;
     }
     SG_CUDA(sg::Launch<T>::combine_last_axis(cb.tab.as<CombineGrid>(), h->G, h->uhat.as<double>(), below, (int)Nf,
-                                             exact ? 1 : 0, h->pde == SG_PDE_VLASOV ? 1 : 0, h->prm.eps,
+                                             exact ? 1 : 0, zero_axis(h, d - 1) ? 1 : 0, h->prm.eps,
                                              h->prm.prolong, h->stream));
     h->launches += 1;
     SG_CUDA(cudaStreamSynchronize(h->stream));
@@ -973,6 +1077,8 @@ sg_status sg_params_init(sg_params* p) {
     p->tile_points = 0;
     p->combine_budget_gb = 0.0;
     p->stage_kernel = SG_STAGE_AUTO;
+    p->theta = 1.0;
+    p->tau = 1.0;
     return SG_OK;
 }
 
@@ -983,8 +1089,11 @@ sg_status sg_create(int dim, int root_cells, int level, int pde, const sg_params
     if (root_cells < 5) return fail(SG_ERR_ARG, "root_cells must be >= 5 (five distinct stencil points)");
     if (level < 0 || level > 16 || ((long long)root_cells << level) > (1LL << 20))
         return fail(SG_ERR_ARG, "level must be in [0, 16] with root_cells * 2^level <= 2^20");
-    if (pde != SG_PDE_ADVECTION && pde != SG_PDE_BURGERS && pde != SG_PDE_VLASOV) return fail(SG_ERR_ARG, "pde");
+    if (pde != SG_PDE_ADVECTION && pde != SG_PDE_BURGERS && pde != SG_PDE_VLASOV && pde != SG_PDE_VLASOV_BOLTZMANN)
+        return fail(SG_ERR_ARG, "pde");
     if (pde == SG_PDE_VLASOV && dim != 2) return fail(SG_ERR_ARG, "the Vlasov-Poisson system is 1D1V: dim must be 2");
+    if (pde == SG_PDE_VLASOV_BOLTZMANN && dim != 2 && dim != 4 && dim != 6)
+        return fail(SG_ERR_ARG, "the Vlasov-Boltzmann model has d space and d velocity axes: dim must be 2, 4 or 6");
     sg_params prm;
     if (params) prm = *params;
     else sg_params_init(&prm);
@@ -1001,6 +1110,13 @@ sg_status sg_create(int dim, int root_cells, int level, int pde, const sg_params
         // d = 3: variant 0 is the sweep kernel, 1 the padded box; other dimensions have one
         const bool autotuned = prm.stage_kernel == SG_STAGE_AUTO && prm.tile_points == 0;
         h->variant = dim == 3 && (autotuned || prm.stage_kernel == SG_STAGE_SWEEP) ? 0 : (dim == 3 ? 1 : 0);
+        if (pde == SG_PDE_VLASOV_BOLTZMANN) {  // the line-buffer kernel carries the kinetic terms
+            if (prm.stage_kernel == SG_STAGE_SWEEP) {
+                delete h;
+                return fail(SG_ERR_UNSUPPORTED, "the Vlasov-Boltzmann model runs on the tiled kernel");
+            }
+            h->variant = 2;
+        }
         h->tuned = !autotuned;
         // grid set: |l| = N_L - q, q = 0..d-1, coefficient (-1)^q C(d-1, q)
         for (int q = 0; q < dim && level - q >= 0; ++q) {
@@ -1044,6 +1160,7 @@ sg_status sg_create(int dim, int root_cells, int level, int pde, const sg_params
             }
             st = h->efield.alloc((size_t)ef_total * h->esize);
         }
+        if (st == SG_OK && pde == SG_PDE_VLASOV_BOLTZMANN) st = relax_tables(h);
         if (st == SG_OK) st = build_tables(h);
         if (st == SG_OK) st = alloc_step_buffers(h, h->G, 1);
         if (st != SG_OK) {
@@ -1070,6 +1187,24 @@ sg_status sg_init(sg_handle h, int ic_kind, const double* p, int n_params) {
         for (int g = 0; g < h->G; ++g) {
             if (h->esize == 8) SG_CUDA(sg::Launch<double>::restrict_landau(h->hgrids[g], p[0], p[1], h->stream));
             else SG_CUDA(sg::Launch<float>::restrict_landau(h->hgrids[g], p[0], p[1], h->stream));
+            h->launches += 1;
+        }
+        SG_CUDA(cudaStreamSynchronize(h->stream));
+        h->ic_sine = false;
+        h->initialized = true;
+        h->combined = false;
+        h->t = 0.0;
+        h->steps = 0;
+        return SG_OK;
+    }
+    if (ic_kind == SG_IC_RELAX) {
+        if (h->pde != SG_PDE_VLASOV_BOLTZMANN || (h->dim != 2 && h->dim != 4))
+            return fail(SG_ERR_ARG, "SG_IC_RELAX needs the Vlasov-Boltzmann model with dim 2 or 4");
+        if (n_params != 0) return fail(SG_ERR_ARG, "SG_IC_RELAX takes no parameters");
+        const double s_norm = relax_norm(h);
+        for (int g = 0; g < h->G; ++g) {
+            if (h->esize == 8) SG_CUDA(sg::Launch<double>::restrict_relax(h->hgrids[g], h->dim, s_norm, h->stream));
+            else SG_CUDA(sg::Launch<float>::restrict_relax(h->hgrids[g], h->dim, s_norm, h->stream));
             h->launches += 1;
         }
         SG_CUDA(cudaStreamSynchronize(h->stream));
@@ -1286,7 +1421,11 @@ sg_status sg_reduce(sg_handle h, int which, int kind, double* out) {
     if (h->is_batch) return fail(SG_ERR_ARG, "sg_reduce applies to batch members");
     if (!out) return fail(SG_ERR_ARG, "NULL output");
     if (kind == SG_REDUCE_FIELD_ENERGY) return field_energy(h, which, out);
-    if (kind < SG_REDUCE_MASS || kind > SG_REDUCE_LINF_EXACT) return fail(SG_ERR_ARG, "unknown reduction %d", kind);
+    const bool entropy = kind == SG_REDUCE_ENTROPY_H2 || kind == SG_REDUCE_ENTROPY_LOG;
+    if ((kind < SG_REDUCE_MASS || kind > SG_REDUCE_LINF_EXACT) && !entropy)
+        return fail(SG_ERR_ARG, "unknown reduction %d", kind);
+    if (entropy && h->pde != SG_PDE_VLASOV_BOLTZMANN)
+        return fail(SG_ERR_ARG, "the entropy functionals need the Vlasov-Boltzmann model");
     ExactSpec X{};
     X.dim = h->dim;
     X.pde = h->pde;
@@ -1301,6 +1440,19 @@ sg_status sg_reduce(sg_handle h, int which, int kind, double* out) {
     X.w = h->ic[2];
     X.phi = h->ic[3];
     X.t = h->t;
+    if (entropy) {  // M = exp(-(|x|^2 + |v|^2)/(2 theta)) / ((2 pi theta)^{d/2} Z), Z over the space domain
+        const double th = h->prm.theta, rt = std::sqrt(2.0 * th);
+        double Z = 1.0;
+        for (int k = 0; k < h->dim / 2; ++k)
+            Z *= std::sqrt(3.14159265358979323846 * th / 2.0) * (std::erf(h->prm.hi[k] / rt) - std::erf(h->prm.lo[k] / rt));
+        X.theta = th;
+        X.mnorm = std::pow(2.0 * 3.14159265358979323846 * th, 0.5 * (double)(h->dim / 2)) * Z;
+        for (int k = 0; k < SG_MAXD; ++k) {
+            const bool in = k < h->dim;
+            X.n[k] = !in ? 1 : (which == SG_WHICH_COMBINED ? X.nf : (which >= 0 && which < h->G ? h->hgrids[which].n[k] : 1));
+            if (in && which >= 0 && which < h->G) X.h[k] = h->hgrids[which].h[k];
+        }
+    }
     const bool exact = kind == SG_REDUCE_L1_EXACT || kind == SG_REDUCE_LINF_EXACT;
     double* dres = h->partial.as<double>() + 1024;
     long long n;
@@ -1328,7 +1480,9 @@ sg_status sg_reduce(sg_handle h, int which, int kind, double* out) {
     SG_CUDA(cudaStreamSynchronize(h->stream));
     switch (kind) {
         case SG_REDUCE_MASS:
-        case SG_REDUCE_ENERGY: r = r * vol; break;
+        case SG_REDUCE_ENERGY:
+        case SG_REDUCE_ENTROPY_H2:
+        case SG_REDUCE_ENTROPY_LOG: r = r * vol; break;
         case SG_REDUCE_L1_EXACT: r = r / (double)n; break;
         default: break;
     }
@@ -1372,8 +1526,8 @@ sg_status sg_batch_create(const sg_handle* hs, int n, sg_handle* out) {
         const sg_ctx* b = hs[i];
         if (b->dim != a->dim || b->pde != a->pde || b->esize != a->esize || b->prm.scheme != a->prm.scheme ||
             b->prm.eps != a->prm.eps || b->prm.tile_points != a->prm.tile_points ||
-            b->prm.stage_kernel != a->prm.stage_kernel)
-            return fail(SG_ERR_ARG, "member %d differs in dim, pde, precision, scheme, eps or stage kernel", i);
+            b->prm.stage_kernel != a->prm.stage_kernel || b->prm.tau != a->prm.tau)
+            return fail(SG_ERR_ARG, "member %d differs in dim, pde, precision, scheme, eps, tau or stage kernel", i);
         for (int k = 0; k < a->dim; ++k)
             if (b->prm.adv_speed[k] != a->prm.adv_speed[k]) return fail(SG_ERR_ARG, "member %d differs in adv_speed", i);
     }

@@ -63,6 +63,18 @@ static __global__ void sg_dt_kernel(InstState* inst, int ninst, const GridDesc* 
                             a = fmax(a, fmax(fabs(v0), fabs(v1)));
                         }
                     }
+                } else if (ph.pde == 3) {  // Vlasov-Boltzmann: max |coordinate| of the partner axis
+                    const int pk = k < ph.dim / 2 ? k + ph.dim / 2 : k - ph.dim / 2;
+                    for (int g = s.grid0; g < s.grid0 + s.ngrids; ++g) {
+                        const GridDesc& G = grids[g];
+                        if (ph.alpha_f32) {
+                            const float c0 = (float)G.lo[pk], c1 = (float)G.lo[pk] + (float)(G.n[pk] - 1) * (float)G.h[pk];
+                            a = fmax(a, (double)fmaxf(fabsf(c0), fabsf(c1)));
+                        } else {
+                            const double c0 = G.lo[pk], c1 = G.lo[pk] + (double)(G.n[pk] - 1) * G.h[pk];
+                            a = fmax(a, fmax(fabs(c0), fabs(c1)));
+                        }
+                    }
                 } else {
                     a = ph.adv[k] < 0.0 ? -ph.adv[k] : ph.adv[k];
                 }
@@ -121,6 +133,73 @@ __global__ void sg_restrict_landau_kernel(GridDesc G, double a, double kx) {
         const double f = (1.0 + a * cos(kx * x)) * m;
         ((T*)G.u0)[p] = (T)f;
         if (sizeof(T) == 4) ((T*)G.u3)[p] = (T)(f - (double)(T)f);
+    }
+}
+
+// Example 5 initial condition of the Vlasov-Boltzmann model (dim = 2 d, d = 1 or 2):
+// f_0 = (1/s) prod_k factor_k(x_k), factor_0 = sin(x^2/2)^2 exp(-x^2/2), factor_1 =
+// cos(x^2/2)^2 exp(-x^2/2) on the space axes, exp(-v^2/2) on the velocity axes.
+template <class T>
+__global__ void sg_restrict_relax_kernel(GridDesc G, int dim, double s_norm) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < G.npts;
+         p += (long long)gridDim.x * blockDim.x) {
+        long long r = p;
+        double f = 1.0;
+        for (int k = 0; k < dim; ++k) {
+            const long long j = r % G.n[k];
+            r /= G.n[k];
+            const double x = G.lo[k] + (double)j * G.h[k];
+            const double e = exp(-0.5 * (x * x));
+            double fac = e;
+            if (k < dim / 2) {
+                const double t = k == 0 ? sin(0.5 * (x * x)) : cos(0.5 * (x * x));
+                fac = (t * t) * e;
+            }
+            f = f * fac;
+        }
+        const double v = f / s_norm;
+        ((T*)G.u0)[p] = (T)v;
+        if (sizeof(T) == 4) ((T*)G.u3)[p] = (T)(v - (double)(T)v);
+    }
+}
+
+// Vlasov-Boltzmann density of every grid from the input of RK stage `stage`, into G->ef:
+// rho[ix] = (h_{v_1} ... h_{v_d}) sum_jv f[ix + n_x jv], the flattened velocity index jv
+// ascending (the order of the definition), one thread per space node ix, FP64 sum (FP32
+// grids store the rounded density).  The loads of eight consecutive jv are issued before
+// their adds; the adds keep their order.
+template <class T>
+__global__ void __launch_bounds__(256) sg_density_kernel(const GridDesc* grids, int ngrids, const InstState* inst,
+                                                         int stage, int dim) {
+    const int dx = dim / 2;
+    for (int g = blockIdx.y; g < ngrids; g += gridDim.y) {
+        const GridDesc* G = grids + g;
+        const InstState* S = inst + G->inst;
+        if (!S->active) continue;  // uniform over the block
+        StageIO<T> io;
+        io.setup(G, stage, stage_parity<T>(S));
+        long long nx = 1, nv = 1;
+        double hv = 1.0;
+        for (int k = 0; k < dx; ++k) nx *= G->n[k];
+        for (int k = dx; k < dim; ++k) {
+            nv *= G->n[k];
+            hv = hv * G->h[k];
+        }
+        T* rho = (T*)G->ef;
+        for (long long ix = blockIdx.x * (long long)blockDim.x + threadIdx.x; ix < nx;
+             ix += (long long)gridDim.x * blockDim.x) {
+            double sum = 0.0;
+            long long jv = 0;
+            for (; jv + 8 <= nv; jv += 8) {
+                T v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = io.load(ix + nx * (jv + q));
+#pragma unroll
+                for (int q = 0; q < 8; ++q) sum = sum + (double)v[q];
+            }
+            for (; jv < nv; ++jv) sum = sum + (double)io.load(ix + nx * jv);
+            rho[ix] = (T)(hv * sum);
+        }
     }
 }
 
@@ -536,10 +615,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) sg_combine_last_a
 // centre (InterpWin::prepare), so the r fine nodes that share a centre pay only for eval().
 // Axis with stride `below` > 1: threads run along `below`, blockIdx.y over (above, chunk of J
 // fine nodes).  below == 1: threads run over the chunks of a row, blockIdx.y over `above`.
+// zero_bc: values beyond the ends of the axis are 0 (else periodic).
 template <class T, int J>
 __global__ void __launch_bounds__(256) sg_prolong_axis_win_kernel(const T* __restrict__ in, T* __restrict__ out,
                                                                   long long below, int n, int nf, long long above,
-                                                                  int r, double eps, int lagrange) {
+                                                                  int r, double eps, int lagrange, int zero_bc) {
     const T e12 = (T)(12.0 * eps);
     const int nchunks = (nf + J - 1) / J;
     const int lr = __ffs(r) - 1;
@@ -558,17 +638,16 @@ __global__ void __launch_bounds__(256) sg_prolong_axis_win_kernel(const T* __res
         int cur;
         T s0;
         centre(j0, cur, s0);
+        auto at = [&](int c) -> T {  // c in [-2, n + 2]
+            if (zero_bc && (c < 0 || c >= n)) return T(0);
+            return col[wrap_index(c, n) * stride];
+        };
         InterpWin<T> W;
-        int c = wrap_index(cur - 2, n);
-        W.w0 = col[c * stride];
-        if (++c == n) c = 0;
-        W.w1 = col[c * stride];
-        if (++c == n) c = 0;
-        W.w2 = col[c * stride];
-        if (++c == n) c = 0;
-        W.w3 = col[c * stride];
-        if (++c == n) c = 0;
-        W.w4 = col[c * stride];
+        W.w0 = at(cur - 2);
+        W.w1 = at(cur - 1);
+        W.w2 = at(cur);
+        W.w3 = at(cur + 1);
+        W.w4 = at(cur + 2);
         W.prepare(e12, lagrange);
 #pragma unroll 1
         for (int j = 0; j < J; ++j) {
@@ -582,9 +661,7 @@ __global__ void __launch_bounds__(256) sg_prolong_axis_win_kernel(const T* __res
                 W.w1 = W.w2;
                 W.w2 = W.w3;
                 W.w3 = W.w4;
-                int cn = ic + 2;
-                if (cn >= n) cn -= n;
-                W.w4 = col[cn * stride];
+                W.w4 = at(ic + 2);
                 W.prepare(e12, lagrange);
                 cur = ic;
             }
@@ -627,8 +704,23 @@ __global__ void sg_gather_kernel(const T* __restrict__ u, const long long* __res
 
 // ------------------------------------------------------------------------------------
 // FP64 reductions, deterministic two-pass (fixed grid, fixed order).
-// kind: 0 sum u, 1 sum u^2, 2 min, 3 max, 4 sum |u - exact|, 5 max |u - exact|
+// kind: 0 sum u, 1 sum u^2, 2 min, 3 max, 4 sum |u - exact|, 5 max |u - exact|,
+// 7 sum u^2 / M, 8 sum over u > 0 of u log(u / M) (M the Vlasov-Boltzmann stationary state)
 // ------------------------------------------------------------------------------------
+
+// Stationary state of the Vlasov-Boltzmann model at node p of an array shaped X.n:
+// M = exp(-(sum_k x_k^2 / 2) / theta) / ((2 pi theta)^{d/2} Z).
+__device__ __forceinline__ double sg_relax_state(const ExactSpec& X, long long p) {
+    double q = 0.0;
+    long long r = p;
+    for (int k = 0; k < X.dim; ++k) {
+        const long long j = r % X.n[k];
+        r /= X.n[k];
+        const double x = X.lo[k] + (double)j * X.h[k];
+        q = q + 0.5 * (x * x);
+    }
+    return exp(-(q / X.theta)) / X.mnorm;
+}
 
 
 __device__ __forceinline__ double sg_exact(const ExactSpec& X, long long p) {
@@ -671,6 +763,8 @@ __global__ void __launch_bounds__(256) sg_reduce_pass1(const T* __restrict__ u, 
             case 1: y = x * x; break;
             case 4:
             case 5: y = fabs(x - sg_exact(X, i)); break;
+            case 7: y = (x * x) / sg_relax_state(X, i); break;
+            case 8: y = x > 0.0 ? x * log(x / sg_relax_state(X, i)) : 0.0; break;
             default: y = x; break;
         }
         if (is_min) v = fmin(v, y);

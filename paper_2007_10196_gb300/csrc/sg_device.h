@@ -25,7 +25,9 @@ struct GridDesc {
     void* u1;
     void* u2;
     void* u3;
-    void* ef;            // Vlasov-Poisson: E_i of the current stage input, n[0] values (else null)
+    void* ef;            // Vlasov-Poisson: E_i of the current stage input, n[0] values;
+                         // Vlasov-Boltzmann: rho(x) of the stage input, n_0 ... n_{d-1} values
+    const void* mu;      // Vlasov-Boltzmann: mu_inf at the velocity nodes (flattened), else null
     long long npts;
     int n[SG_MAXD];      // nodes per axis
     int te[SG_MAXD];     // tile extent per axis
@@ -72,12 +74,13 @@ struct InstState {
 
 struct PhysParams {
     int dim;
-    int pde;                 // 0 advection, 1 Burgers
+    int pde;                 // 0 advection, 1 Burgers, 2 Vlasov-Poisson, 3 Vlasov-Boltzmann
     int scheme;              // 0 WENO5, 1 linear
     int prolong;             // 0 WENO5 interpolation, 1 Lagrange
     double eps;
     double adv[SG_MAXD];
     int alpha_f32;           // alpha slots hold float bits (FP32 state)
+    double tau;              // Vlasov-Boltzmann: relaxation time of (mu rho - f) / tau
 };
 
 struct StageArgs {
@@ -98,6 +101,10 @@ struct ExactSpec {
     int dim, pde, nf;
     double lo[SG_MAXD], h[SG_MAXD], adv[SG_MAXD];
     double b, a, w, phi, t;
+    // entropy functionals of the Vlasov-Boltzmann model: node counts per axis of the reduced
+    // array, temperature and the normalisation (2 pi theta)^{d/2} Z of the stationary state
+    int n[SG_MAXD];
+    double theta, mnorm;
 };
 
 // One grid's entry for the fused last-axis prolongation + combination kernel.

@@ -20,11 +20,12 @@ void sweep_tile(const int* n, int* te);
 template <class T>
 struct Launch {
     // Dynamic shared memory (bytes) of the stage kernel: d <= 3 uses the padded-box kernel
-    // (2 box + flux elements), d >= 4 the line-buffer kernel (fixed by ppt).
-    static size_t stage_smem(int dim, int ppt, long long box, long long flux);
+    // (2 box + flux elements), d >= 4 and variant 2 the line-buffer kernel (fixed by ppt).
+    static size_t stage_smem(int dim, int ppt, long long box, long long flux, int variant = 0);
     // Raises the kernel's shared-memory limit and returns resident blocks per SM (0 if the
     // configuration cannot run).  variant: 0 = the default kernel of the dimension (d = 3:
-    // line sweep), 1 = the padded-box kernel for d = 3.
+    // line sweep), 1 = the padded-box kernel for d = 3, 2 = the line-buffer kernel for d = 2
+    // (the Vlasov-Boltzmann model; d = 4 and 6 use it by default).
     static int stage_prepare(int dim, int ppt, size_t smem, int variant = 0);
     // One RK stage over work items [a.item_begin, a.item_end) with `nblocks` blocks.
     static cudaError_t stage(int dim, int ppt, const StageArgs& a, int nblocks, size_t smem, cudaStream_t s,
@@ -36,7 +37,8 @@ struct Launch {
     // u0 of one grid <- p0 + p1 sin(p2 sum x + p3) (FP32: also the compensation term u3).
     static cudaError_t restrict_sine(const GridDesc& g, int dim, const double* p, cudaStream_t s);
     // One prolongation axis; acc != nullptr fuses "acc += coeff * result"; zero_bc: values
-    // beyond the ends of the axis are 0 (Vlasov-Poisson v), else periodic.
+    // beyond the ends of the axis are 0 (Vlasov-Poisson v, every Vlasov-Boltzmann axis), else
+    // periodic.
     static cudaError_t prolong_axis(const T* in, T* out, double* acc, double coeff, long long below,
                                     int min_, int nf, long long above, int r, double eps,
                                     int lagrange, int zero_bc, cudaStream_t s);
@@ -50,12 +52,18 @@ struct Launch {
                                     double* scratch, double* out, cudaStream_t s);
     // Landau initial condition on one grid.
     static cudaError_t restrict_landau(const GridDesc& g, double a, double kx, cudaStream_t s);
+    // Vlasov-Boltzmann: Example 5 initial condition on one grid (normalisation s_norm).
+    static cudaError_t restrict_relax(const GridDesc& g, int dim, double s_norm, cudaStream_t s);
+    // Vlasov-Boltzmann: rho(x) of every grid from the input of RK stage `stage` into GridDesc.ef.
+    static cudaError_t density(const GridDesc* grids, int ngrids, long long max_nx, const InstState* inst,
+                               int stage, int dim, cudaStream_t s);
     static cudaError_t accumulate(const T* u, double* acc, double coeff, long long n, cudaStream_t s);
     // out[j] = u[idx[j]], j < n (device arrays; indices already checked)
     static cudaError_t gather(const T* u, const long long* idx, T* out, long long n, cudaStream_t s);
-    // One prolongation axis, J = 8 consecutive fine nodes per thread sharing the coarse window.
+    // One prolongation axis, J = 8 consecutive fine nodes per thread sharing the coarse window;
+    // zero_bc as for prolong_axis.
     static cudaError_t prolong_axis_win(const T* in, T* out, long long below, int min_, int nf, long long above,
-                                        int r, double eps, int lagrange, cudaStream_t s);
+                                        int r, double eps, int lagrange, int zero_bc, cudaStream_t s);
     // One prolongation axis (2-D indexed form of prolong_axis without the accumulation).
     static cudaError_t prolong_axis2(const T* in, T* out, long long below, int min_, int nf, long long above,
                                      int r, double eps, int lagrange, cudaStream_t s);

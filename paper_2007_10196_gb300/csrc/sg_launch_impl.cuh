@@ -76,8 +76,8 @@ inline int grid_for(long long n, int threads) {
 }  // namespace detail
 
 template <class T>
-size_t Launch<T>::stage_smem(int dim, int ppt, long long box, long long flux) {
-    if (dim <= 3) return sizeof(T) * (size_t)(2 * box + flux);
+size_t Launch<T>::stage_smem(int dim, int ppt, long long box, long long flux, int variant) {
+    if (dim <= 3 && variant != 2) return sizeof(T) * (size_t)(2 * box + flux);
     return sizeof(T) * (size_t)(LineSmem<1>::LB + LineSmem<1>::FB) * (size_t)ppt;
 }
 
@@ -102,6 +102,32 @@ int prepare_box3(int ppt, size_t smem) {
     }
     return nb;
 }
+// d = 2 with the line-buffer kernel (variant 2)
+template <class T>
+int prepare_line2(int ppt, size_t smem) {
+    const void* kern = ppt == 1 ? (const void*)sg_stage_line_kernel<T, 2, 1>
+                     : ppt == 2 ? (const void*)sg_stage_line_kernel<T, 2, 2> : (const void*)sg_stage_line_kernel<T, 2, 4>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, SG_NT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+template <class T>
+cudaError_t stage_line2(int ppt, const StageArgs& a, int nblocks, size_t smem, cudaStream_t s) {
+    switch (ppt) {
+        case 1: sg_stage_line_kernel<T, 2, 1><<<nblocks, SG_NT, smem, s>>>(a); break;
+        case 2: sg_stage_line_kernel<T, 2, 2><<<nblocks, SG_NT, smem, s>>>(a); break;
+        case 4: sg_stage_line_kernel<T, 2, 4><<<nblocks, SG_NT, smem, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 template <class T>
 cudaError_t stage_box3(int ppt, const StageArgs& a, int nblocks, size_t smem, cudaStream_t s) {
     switch (ppt) {
@@ -117,6 +143,7 @@ cudaError_t stage_box3(int ppt, const StageArgs& a, int nblocks, size_t smem, cu
 template <class T>
 int Launch<T>::stage_prepare(int dim, int ppt, size_t smem, int variant) {
     if (dim == 3 && variant == 1) return detail::prepare_box3<T>(ppt, smem);
+    if (dim == 2 && variant == 2) return detail::prepare_line2<T>(ppt, smem);
     switch (dim) {
         case 1: return detail::prepare_d<T, 1>(ppt, smem);
         case 2: return detail::prepare_d<T, 2>(ppt, smem);
@@ -133,6 +160,7 @@ cudaError_t Launch<T>::stage(int dim, int ppt, const StageArgs& a, int nblocks, 
                              int variant) {
     if (nblocks < 1) return cudaSuccess;
     if (dim == 3 && variant == 1) return detail::stage_box3<T>(ppt, a, nblocks, smem, s);
+    if (dim == 2 && variant == 2) return detail::stage_line2<T>(ppt, a, nblocks, smem, s);
     switch (dim) {
         case 1: return detail::stage_d<T, 1>(ppt, a, nblocks, smem, s);
         case 2: return detail::stage_d<T, 2>(ppt, a, nblocks, smem, s);
@@ -194,6 +222,21 @@ cudaError_t Launch<T>::restrict_landau(const GridDesc& g, double a, double kx, c
 }
 
 template <class T>
+cudaError_t Launch<T>::restrict_relax(const GridDesc& g, int dim, double s_norm, cudaStream_t s) {
+    sg_restrict_relax_kernel<T><<<detail::grid_for(g.npts, 256), 256, 0, s>>>(g, dim, s_norm);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Launch<T>::density(const GridDesc* grids, int ngrids, long long max_nx, const InstState* inst,
+                               int stage, int dim, cudaStream_t s) {
+    if (ngrids < 1) return cudaSuccess;
+    const dim3 grid((unsigned)std::min<long long>((max_nx + 255) / 256, 1024), (unsigned)std::min(ngrids, 65535));
+    sg_density_kernel<T><<<grid, 256, 0, s>>>(grids, ngrids, inst, stage, dim);
+    return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t Launch<T>::accumulate(const T* u, double* acc, double coeff, long long n, cudaStream_t s) {
     sg_accumulate_kernel<T><<<detail::grid_for(n, 256), 256, 0, s>>>(u, acc, coeff, n);
     return cudaGetLastError();
@@ -208,7 +251,7 @@ cudaError_t Launch<T>::gather(const T* u, const long long* idx, T* out, long lon
 
 template <class T>
 cudaError_t Launch<T>::prolong_axis_win(const T* in, T* out, long long below, int min_, int nf, long long above,
-                                        int r, double eps, int lagrange, cudaStream_t s) {
+                                        int r, double eps, int lagrange, int zero_bc, cudaStream_t s) {
     constexpr int J = 8;
     const long long nchunks = (nf + J - 1) / J;
     dim3 grid;
@@ -219,7 +262,7 @@ cudaError_t Launch<T>::prolong_axis_win(const T* in, T* out, long long below, in
         grid.x = (unsigned)std::min<long long>((below + 255) / 256, 65535);
         grid.y = (unsigned)std::min<long long>(above * nchunks, 65535);
     }
-    sg_prolong_axis_win_kernel<T, J><<<grid, 256, 0, s>>>(in, out, below, min_, nf, above, r, eps, lagrange);
+    sg_prolong_axis_win_kernel<T, J><<<grid, 256, 0, s>>>(in, out, below, min_, nf, above, r, eps, lagrange, zero_bc);
     return cudaGetLastError();
 }
 

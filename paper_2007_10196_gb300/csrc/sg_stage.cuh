@@ -883,6 +883,10 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
 // d >= 4 (and any d): line-buffer kernel.  For each axis k the tile's lines along k plus a
 // 3-point periodic halo are staged in shared memory, every interface flux of the tile along
 // k is computed once, and each thread subtracts (F_{i+1/2} - F_{i-1/2}) / h_k for its points.
+// Vlasov-Boltzmann (pde 3, d = 2 d_x): halos beyond the ends are 0; the flux along space axis
+// k is v_k u and along velocity axis k is -x_k u, v_k (x_k) the line's node on the partner
+// axis; the LF alpha of an axis is the largest |partner node| of the grid; after the flux
+// differences each point adds (mu(v) rho(x) - u) / tau (rho from G->ef, mu from G->mu).
 // ------------------------------------------------------------------------------------
 template <int PPT>
 struct LineSmem {
@@ -903,6 +907,8 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
     const int tid = threadIdx.x;
     const PhysParams& ph = A.phys;
     const float eps12f = (float)(12.0 * ph.eps);
+    const bool vb = ph.pde == 3;
+    constexpr int DX = D / 2;  // Vlasov-Boltzmann: space axes 0..DX-1, velocity axes DX..D-1
 
     for (int it = A.item_begin + blockIdx.x; it < A.item_end; it += gridDim.x) {
         const WorkItem w = A.items[it];
@@ -956,12 +962,25 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
             const int lines = P / ek;
             const int ls = (ek + 6) | 1;  // odd strides avoid bank conflicts
             const int fs = (ek + 1) | 1;
-            const T alpha = ph.pde == 1 ? alpha_slot : (T)sg_abs(ph.adv[k]);
+            T alpha = ph.pde == 1 ? alpha_slot : (T)sg_abs(ph.adv[k]);
             const T ak = (T)ph.adv[k];
             FDiv fl, fr, ff;
             fl.init((unsigned)lines);
             fr.init((unsigned)(ek + 6));
             ff.init((unsigned)(ek + 1));
+            // Vlasov-Boltzmann: partner axis, LF alpha (an end node), and the divisor that takes
+            // a line index (axes j != k, fastest first) to its partner-axis coordinate
+            const int pk = k < DX ? k + DX : k - DX;
+            FDiv fmp;
+            if (vb) {
+                const T c0 = (T)G->lo[pk], c1 = (T)G->lo[pk] + (T)(nn[pk] - 1) * (T)G->h[pk];
+                alpha = sg_max(sg_abs(c0), sg_abs(c1));
+                int mulp = 1;
+#pragma unroll
+                for (int j = 0; j < D; ++j)
+                    if (j != k && j < pk) mulp *= ext[j];
+                fmp.init((unsigned)mulp);
+            }
 
             const int NL = lines * (ek + 6);
             for (int e = tid; e < NL; e += SG_NT) {
@@ -984,6 +1003,10 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
                     g += (long long)(org[j] + cj) * gstr[j];
                 }
                 int ck = org[k] + i - 3;
+                if (vb && (ck < 0 || ck >= nn[k])) {  // zero boundary values
+                    lb[line * ls + i] = T(0);
+                    continue;
+                }
                 if (ck < 0) ck += nn[k];
                 else if (ck >= nn[k]) ck -= nn[k];
                 g += (long long)ck * gstr[k];
@@ -996,10 +1019,17 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
                 const int line = (int)ff.div((unsigned)e);
                 const int i = e - line * (ek + 1);
                 const T* v = lb + line * ls + i;
+                T akl = ak;
+                if (vb) {  // the line's node on the partner axis: v_k along x_k, -x_k along v_k
+                    const unsigned qq = fmp.div((unsigned)line);
+                    const int cpk = (int)(qq - fd[pk].div(qq) * (unsigned)ext[pk]);
+                    const T c = (T)G->lo[pk] + (T)(org[pk] + cpk) * (T)G->h[pk];
+                    akl = k < DX ? c : -c;
+                }
                 if constexpr (sizeof(T) == 8) {
-                    fb[line * fs + i] = Weno<double>::interface((const double*)v, 1, (double)alpha, (double)ak, ph);
+                    fb[line * fs + i] = Weno<double>::interface((const double*)v, 1, (double)alpha, (double)akl, ph);
                 } else {
-                    fb[line * fs + i] = Weno<float>::interface((const float*)v, 1, (float)alpha, (float)ak, ph,
+                    fb[line * fs + i] = Weno<float>::interface((const float*)v, 1, (float)alpha, (float)akl, ph,
                                                                eps12f);
                 }
             }
@@ -1020,6 +1050,28 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
                 acc[q] = acc[q] - (F[1] - F[0]) * rdx;
             }
             __syncthreads();
+        }
+
+        if (vb) {  // relaxation (mu(v) rho(x) - u) / tau, after every axis
+            const T* rho = (const T*)G->ef;
+            const T* mu = (const T*)G->mu;
+            const T tau = (T)ph.tau;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                if (!own[q]) continue;
+                long long ix = 0, iv = 0, sv = 1;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    if (k < DX) {
+                        ix += (long long)(org[k] + cp[q][k]) * gstr[k];
+                    } else {
+                        iv += (long long)(org[k] + cp[q][k]) * sv;
+                        sv *= nn[k];
+                    }
+                }
+                const T u = io.load(ix + gstr[DX] * iv);
+                acc[q] = acc[q] + (mu[iv] * rho[ix] - u) / tau;
+            }
         }
 
         T mx = T(0);
