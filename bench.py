@@ -12,6 +12,11 @@ combination in FP64 for every member (Step 3), FP64 min/max of every combined so
 
 Metric: grid-point updates per second (one point advanced one full RK3 step), whole job.
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on the host cores instead.
+
+--workload relax2d / relax4d measures the Vlasov-Boltzmann relaxation model of Example 5
+instead (one GPU): (a) N_r = 40, N_L = 3 in 2-D to t = 6, (b) N_r = 10, N_L = 3 in 4-D to t = 3,
+CFL 0.4, FP32 batched; one step = restriction, time marching, combination and the two entropy
+functionals of the combined solution.  Its state fits in L2, so L2 is flushed between steps.
 """
 from __future__ import annotations
 
@@ -55,6 +60,13 @@ FP32_LANES_PER_SM = 128
 # 3u, so they first cross at t = 1 / (3 a pi/2); members with a below this stay smooth to t_end.
 A_SMOOTH_AT_T_END = 2.0 / (3.0 * math.pi * 0.3)
 STAGE_SOURCES = ("sg_stage.cuh", "sg_weno.cuh", "sg_device.h")
+# Vlasov-Boltzmann (Example 5), FP32 line-buffer stage kernel, per point per RK stage: per axis
+# the split of the point (2: the line speed times the value, twice), two one-sided WENO5
+# reconstructions (2 x 54), their combination (7) and the flux difference (3); then the
+# relaxation (mu rho - u) / tau added (4) and the RK update (4 on average).
+FLOPS_PER_POINT_STAGE_RELAX = {2: 2 * (2 + 2 * 54 + 7 + 3) + 8, 4: 4 * (2 + 2 * 54 + 7 + 3) + 8}
+RELAX = {"relax2d": (2, 40, 3, 6.0, "vlasov_boltzmann_example5a_nr40_nl3_t6_cfl0.4_f32_batched"),
+         "relax4d": (4, 10, 3, 3.0, "vlasov_boltzmann_example5b_4d_nr10_nl3_t3_cfl0.4_f32_batched")}
 
 
 def _env_rank():
@@ -448,6 +460,128 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def _oracle_relax_grid(args):
+    dim, nr, nl, lev, nsteps = args
+    import oracle
+    p = oracle.problem(dim, nr, nl, pde=oracle.VLASOV_BOLTZMANN, eps=1e-3, lo=-5.0, hi=5.0)
+    u = oracle.restrict_relax(p, lev)
+    t0 = time.perf_counter()
+    out, steps, _ = oracle.solve(p, [lev], [u], 100.0, max_steps=nsteps, rule=oracle.DT_CFL, cfl=0.4)
+    return out[0].size * steps, time.perf_counter() - t0
+
+
+def relax_oracle_sample(dim, nr, nl, pool):
+    """The oracle on every grid of the sparse set for one time step (the CFL step is the same for
+    every grid: each spans the whole domain), grids in parallel; (point-updates, wall seconds)."""
+    import oracle
+    oracle.build()
+    lev, _ = oracle.grid_set(dim, nl)
+    jobs = sorted([(dim, nr, nl, [int(x) for x in l], 1) for l in lev], key=lambda j: -sum(j[3]))
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_relax_grid, jobs, chunksize=1)
+    return sum(r[0] for r in res), time.perf_counter() - t0
+
+
+def run_kinetic(args):
+    """Example 5 (Vlasov-Boltzmann relaxation) on one GPU; prints one JSON line."""
+    import torch
+    import paper_2007_10196_gb300 as P
+
+    dim, nr, nl, t_end, workload = RELAX[args.workload]
+    cores = min(os.cpu_count() or 1, 64)
+    pool = None if args.no_cpu else mp.get_context("spawn").Pool(cores)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    P.build()
+    with torch.cuda.stream(stream):
+        h = P.create(dim, nr, nl, P.SG_PDE_VLASOV_BOLTZMANN, precision=P.SG_F32, exec=P.SG_BATCHED,
+                     dt_rule=P.SG_DT_CFL, cfl=0.4, lo=-5.0, hi=5.0, cuda_stream=stream.cuda_stream)
+    G = P.sg_num_grids(h)
+    pts = sum(int(np.prod(P.sg_grid_info(h, g, dim)[1])) for g in range(G))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def one_pass(host_in=None, host_out=None):
+        if host_in is None:
+            P.sg_init(h, P.SG_IC_RELAX, ())
+        else:
+            P.sg_init_grids(h, host_in)
+        P.sg_step(h, t_end)
+        P.sg_prolong_combine(h)
+        ent = (P.sg_reduce(h, -1, P.SG_REDUCE_ENTROPY_H2), P.sg_reduce(h, -1, P.SG_REDUCE_ENTROPY_LOG))
+        if host_out is not None:
+            P.sg_read(h, P.SG_WHICH_ALL_GRIDS, out=host_out)
+        return ent
+
+    def timed(fn, n):
+        out, ts = None, []
+        for _ in range(n):
+            flush.zero_()
+            ev_a.record(stream)
+            out = fn()
+            ev_b.record(stream)
+            ev_b.synchronize()
+            ts.append(ev_a.elapsed_time(ev_b))
+        return out, ts
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_pass()
+        steps = P.sg_time(h)[1]
+        upd = steps * pts
+        P.sg_set_profiling(h, True)
+        launches0 = P.sg_launch_count(h)
+        torch.cuda.synchronize()
+        with ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0].strip()) as clk:
+            ent, times = timed(one_pass, args.steps)
+        torch.cuda.synchronize()
+        launches = P.sg_launch_count(h) - launches0
+        stage_ms, stage_launches = P.sg_profile(h)
+        P.sg_set_profiling(h, False)
+        kern, tp, _ = P.sg_stage_config(h)
+        e2e = None
+        if not args.no_e2e:
+            P.sg_init(h, P.SG_IC_RELAX, ())
+            host_in = torch.empty(pts, dtype=torch.float32, pin_memory=True).numpy()
+            P.sg_read(h, P.SG_WHICH_ALL_GRIDS, out=host_in)
+            host_out = torch.empty(pts, dtype=torch.float32, pin_memory=True).numpy()
+            _, et = timed(lambda: one_pass(host_in, host_out), max(1, args.steps))
+            e2e_ms = statistics.mean(et)
+            e2e = {"value": upd / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": pts * 4,
+                   "d2h_bytes_per_step": pts * 4 + 16, "ms_per_step": e2e_ms,
+                   "api": "sg_init_grids (pinned host) + sg_step + sg_prolong_combine + sg_reduce + sg_read"}
+    P.sg_destroy(h)
+    peaks, src = _peaks()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    point_stages = 3 * upd * args.steps
+    achieved = point_stages * FLOPS_PER_POINT_STAGE_RELAX[dim] / (stage_ms / 1e3) / 1e12
+    mean_ms = statistics.mean(times)
+    cpu = None
+    if pool is not None:
+        u_c, w_c = relax_oracle_sample(dim, nr, nl, pool)
+        pool.close()
+        cpu = {"value": u_c / w_c, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "all %d grids, first time step each (FP64 C oracle, one process per core)" % G,
+               "seconds": w_c}
+    line = {
+        "metric": METRIC, "value": upd * args.steps / (sum(times) / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload, "dim": dim, "root_cells": nr, "level": nl, "grids": G, "points": pts,
+                   "t_end": t_end, "time_steps": steps, "pt_updates_per_step": upd,
+                   "l2": "state fits in L2: a 256 MB buffer is written between timed steps"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "kernel": "sg_stage_line_kernel<float,%d,%d>" % (dim, tp // 256),
+                     "peak_source": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (%s SM clock)" % (nsm, FP32_LANES_PER_SM, sm_max, src)},
+        "breakdown_ms": {"stage_kernels": stage_ms / args.steps, "stage_launches": stage_launches // args.steps},
+        "entropy_h2_hlog": ent, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     """The FP64 C oracle on the host cores, each step a bounded sample of the workload."""
     if rank != 0:
@@ -485,12 +619,18 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-plain comparison")
     ap.add_argument("--members", type=int, default=256,
                     help="first M members of the batch only (small cases for profiling)")
+    ap.add_argument("--workload", choices=["burgers3d_batch"] + sorted(RELAX), default="burgers3d_batch",
+                    help="the benchmark batch (default), or Example 5 (Vlasov-Boltzmann) in 2-D or 4-D")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least three untimed passes
     global N_MEMBERS
     N_MEMBERS = max(1, min(256, args.members))
     rank, world, local_rank = _env_rank()
-    if args.impl == "reference":
+    if args.workload != "burgers3d_batch":
+        if args.impl == "reference" or world > 1:
+            raise SystemExit("--workload %s: our arm on one GPU only" % args.workload)
+        run_kinetic(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local_rank)

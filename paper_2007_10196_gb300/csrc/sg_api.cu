@@ -157,6 +157,7 @@ struct sg_ctx {
     DevBuf mutab;  // Vlasov-Boltzmann: mu_inf at the velocity nodes of every grid, concatenated
     std::vector<long long> mu_offset;
     long long max_nx = 0;  // Vlasov-Boltzmann: largest space-node count of a grid
+    double relax_s = 0.0;  // Vlasov-Boltzmann: normalisation of the Example 5 initial condition (0: not yet formed)
     long long box_elems = 0;  // stage kernel: elements of one padded box (d <= 3)
     size_t smem = 0;          // stage kernel: dynamic shared memory per block
     // device tables (single handle or batch)
@@ -244,6 +245,24 @@ void fill_inst(const sg_ctx* h, InstState& s, int grid0, double t_end, long long
     s.grid0 = grid0;
     s.ngrids = h->G;
     s.dt_rule = h->prm.dt_rule;
+    // Vlasov-Boltzmann: the LF alpha of each axis is static, the largest |node| of the partner
+    // axis over the grids, evaluated as the stage and dt arithmetic of the handle's precision
+    for (int k = 0; k < SG_MAXD; ++k) {
+        double a = 0.0;
+        if (h->pde == SG_PDE_VLASOV_BOLTZMANN && k < h->dim) {
+            const int pk = k < h->dim / 2 ? k + h->dim / 2 : k - h->dim / 2;
+            for (const GridDesc& G : h->hgrids) {
+                if (h->esize == 4) {
+                    const float c0 = (float)G.lo[pk], c1 = (float)G.lo[pk] + (float)(G.n[pk] - 1) * (float)G.h[pk];
+                    a = std::max(a, (double)std::max(std::fabs(c0), std::fabs(c1)));
+                } else {
+                    const double c0 = G.lo[pk], c1 = G.lo[pk] + (double)(G.n[pk] - 1) * G.h[pk];
+                    a = std::max(a, std::max(std::fabs(c0), std::fabs(c1)));
+                }
+            }
+        }
+        s.alpha_vb[k] = a;
+    }
 }
 
 // Tile extents: start from the whole grid and halve the longest extent (the highest axis on
@@ -1201,7 +1220,8 @@ sg_status sg_init(sg_handle h, int ic_kind, const double* p, int n_params) {
         if (h->pde != SG_PDE_VLASOV_BOLTZMANN || (h->dim != 2 && h->dim != 4))
             return fail(SG_ERR_ARG, "SG_IC_RELAX needs the Vlasov-Boltzmann model with dim 2 or 4");
         if (n_params != 0) return fail(SG_ERR_ARG, "SG_IC_RELAX takes no parameters");
-        const double s_norm = relax_norm(h);
+        if (h->relax_s == 0.0) h->relax_s = relax_norm(h);  // depends on the domain only
+        const double s_norm = h->relax_s;
         for (int g = 0; g < h->G; ++g) {
             if (h->esize == 8) SG_CUDA(sg::Launch<double>::restrict_relax(h->hgrids[g], h->dim, s_norm, h->stream));
             else SG_CUDA(sg::Launch<float>::restrict_relax(h->hgrids[g], h->dim, s_norm, h->stream));

@@ -63,18 +63,8 @@ static __global__ void sg_dt_kernel(InstState* inst, int ninst, const GridDesc* 
                             a = fmax(a, fmax(fabs(v0), fabs(v1)));
                         }
                     }
-                } else if (ph.pde == 3) {  // Vlasov-Boltzmann: max |coordinate| of the partner axis
-                    const int pk = k < ph.dim / 2 ? k + ph.dim / 2 : k - ph.dim / 2;
-                    for (int g = s.grid0; g < s.grid0 + s.ngrids; ++g) {
-                        const GridDesc& G = grids[g];
-                        if (ph.alpha_f32) {
-                            const float c0 = (float)G.lo[pk], c1 = (float)G.lo[pk] + (float)(G.n[pk] - 1) * (float)G.h[pk];
-                            a = fmax(a, (double)fmaxf(fabsf(c0), fabsf(c1)));
-                        } else {
-                            const double c0 = G.lo[pk], c1 = G.lo[pk] + (double)(G.n[pk] - 1) * G.h[pk];
-                            a = fmax(a, fmax(fabs(c0), fabs(c1)));
-                        }
-                    }
+                } else if (ph.pde == 3) {  // Vlasov-Boltzmann: static, from the instance's grids
+                    a = s.alpha_vb[k];
                 } else {
                     a = ph.adv[k] < 0.0 ? -ph.adv[k] : ph.adv[k];
                 }
@@ -164,13 +154,19 @@ __global__ void sg_restrict_relax_kernel(GridDesc G, int dim, double s_norm) {
 }
 
 // Vlasov-Boltzmann density of every grid from the input of RK stage `stage`, into G->ef:
-// rho[ix] = (h_{v_1} ... h_{v_d}) sum_jv f[ix + n_x jv], the flattened velocity index jv
-// ascending (the order of the definition), one thread per space node ix, FP64 sum (FP32
-// grids store the rounded density).  The loads of eight consecutive jv are issued before
-// their adds; the adds keep their order.
+// rho[ix] = (h_{v_1} ... h_{v_d}) sum_jv f[ix + n_x jv] (ix the flattened space index, jv the
+// flattened velocity index), summed in FP64.  Block (32, SG_DENS_ROWS).
+//   FP64: one thread per space node, jv ascending (the order of the definition); the loads of
+//   16 consecutive jv are issued before their adds, which keep their order.
+//   FP32: threadIdx.x over 32 consecutive space nodes, threadIdx.y over the residues of jv
+//   modulo SG_DENS_ROWS; the partial sums are added in y order and the density is rounded to
+//   float once.
+// ------------------------------------------------------------------------------------
+#define SG_DENS_ROWS 16
 template <class T>
-__global__ void __launch_bounds__(256) sg_density_kernel(const GridDesc* grids, int ngrids, const InstState* inst,
-                                                         int stage, int dim) {
+__global__ void __launch_bounds__(32 * SG_DENS_ROWS) sg_density_kernel(const GridDesc* grids, int ngrids,
+                                                                       const InstState* inst, int stage, int dim) {
+    __shared__ double part[SG_DENS_ROWS][33];
     const int dx = dim / 2;
     for (int g = blockIdx.y; g < ngrids; g += gridDim.y) {
         const GridDesc* G = grids + g;
@@ -186,19 +182,47 @@ __global__ void __launch_bounds__(256) sg_density_kernel(const GridDesc* grids, 
             hv = hv * G->h[k];
         }
         T* rho = (T*)G->ef;
-        for (long long ix = blockIdx.x * (long long)blockDim.x + threadIdx.x; ix < nx;
-             ix += (long long)gridDim.x * blockDim.x) {
-            double sum = 0.0;
-            long long jv = 0;
-            for (; jv + 8 <= nv; jv += 8) {
-                T v[8];
+        if constexpr (sizeof(T) == 8) {
+            const int per = 32 * SG_DENS_ROWS;
+            for (long long ix = blockIdx.x * (long long)per + threadIdx.x + 32 * threadIdx.y; ix < nx;
+                 ix += (long long)gridDim.x * per) {
+                double sum = 0.0;
+                long long jv = 0;
+                for (; jv + 16 <= nv; jv += 16) {
+                    T v[16];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = io.load(ix + nx * (jv + q));
+                    for (int q = 0; q < 16; ++q) v[q] = io.load(ix + nx * (jv + q));
 #pragma unroll
-                for (int q = 0; q < 8; ++q) sum = sum + (double)v[q];
+                    for (int q = 0; q < 16; ++q) sum = sum + (double)v[q];
+                }
+                for (; jv < nv; ++jv) sum = sum + (double)io.load(ix + nx * jv);
+                rho[ix] = (T)(hv * sum);
             }
-            for (; jv < nv; ++jv) sum = sum + (double)io.load(ix + nx * jv);
-            rho[ix] = (T)(hv * sum);
+        } else {
+            for (long long ix0 = blockIdx.x * 32LL; ix0 < nx; ix0 += (long long)gridDim.x * 32) {  // uniform
+                const long long ix = ix0 + threadIdx.x;
+                double sum = 0.0;
+                if (ix < nx) {
+                    long long jv = threadIdx.y;
+                    for (; jv + 3 * SG_DENS_ROWS < nv; jv += 4 * SG_DENS_ROWS) {
+                        T v[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) v[q] = io.load(ix + nx * (jv + q * SG_DENS_ROWS));
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) sum += (double)v[q];
+                    }
+                    for (; jv < nv; jv += SG_DENS_ROWS) sum += (double)io.load(ix + nx * jv);
+                }
+                part[threadIdx.y][threadIdx.x] = sum;
+                __syncthreads();
+                if (threadIdx.y == 0 && ix < nx) {
+                    double t = 0.0;
+#pragma unroll
+                    for (int y = 0; y < SG_DENS_ROWS; ++y) t += part[y][threadIdx.x];
+                    rho[ix] = (T)(hv * t);
+                }
+                __syncthreads();
+            }
         }
     }
 }

@@ -61,6 +61,8 @@ struct InstState {
     double dt_nom;          // dt of the h^{5/3} rule (host-computed)
     double cfl;
     double hf[SG_MAXD];     // finest-grid spacing per axis
+    double alpha_vb[SG_MAXD];  // Vlasov-Boltzmann: max over the instance's grids of the axis's
+                               // largest |partner node| (host-computed, the stage precision's arithmetic)
     long long steps;
     long long step0;        // steps at the start of the current sg_step call (FP32 ping-pong parity)
     long long step_limit;

@@ -231,8 +231,9 @@ template <class T>
 cudaError_t Launch<T>::density(const GridDesc* grids, int ngrids, long long max_nx, const InstState* inst,
                                int stage, int dim, cudaStream_t s) {
     if (ngrids < 1) return cudaSuccess;
-    const dim3 grid((unsigned)std::min<long long>((max_nx + 255) / 256, 1024), (unsigned)std::min(ngrids, 65535));
-    sg_density_kernel<T><<<grid, 256, 0, s>>>(grids, ngrids, inst, stage, dim);
+    const long long per = sizeof(T) == 8 ? 32 * SG_DENS_ROWS : 32;  // space nodes per block
+    const dim3 grid((unsigned)std::min<long long>((max_nx + per - 1) / per, 1024), (unsigned)std::min(ngrids, 65535));
+    sg_density_kernel<T><<<grid, dim3(32, SG_DENS_ROWS), 0, s>>>(grids, ngrids, inst, stage, dim);
     return cudaGetLastError();
 }
 

@@ -982,35 +982,53 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
                 fmp.init((unsigned)mulp);
             }
 
+            // stage the lines with their halos: four elements per thread and round, addresses
+            // first, then the four loads in flight, then the shared-memory stores
             const int NL = lines * (ek + 6);
-            for (int e = tid; e < NL; e += SG_NT) {
-                int line, i;
-                if (k == 0) {
-                    line = (int)fr.div((unsigned)e);
-                    i = e - line * (ek + 6);
-                } else {
-                    i = (int)fl.div((unsigned)e);
-                    line = e - i * lines;
-                }
-                long long g = 0;
-                unsigned rem = (unsigned)line;
+            constexpr int RU = 4;
+            for (int e0 = tid; e0 < NL; e0 += RU * SG_NT) {
+                int dst[RU];
+                long long src[RU];  // -1: no element; -2: a zero boundary value
 #pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    if (j == k) continue;
-                    const unsigned qq = fd[j].div(rem);
-                    const int cj = (int)(rem - qq * (unsigned)ext[j]);
-                    rem = qq;
-                    g += (long long)(org[j] + cj) * gstr[j];
+                for (int u = 0; u < RU; ++u) {
+                    const int e = e0 + u * SG_NT;
+                    src[u] = -1;
+                    dst[u] = 0;
+                    if (e >= NL) continue;
+                    int line, i;
+                    if (k == 0) {
+                        line = (int)fr.div((unsigned)e);
+                        i = e - line * (ek + 6);
+                    } else {
+                        i = (int)fl.div((unsigned)e);
+                        line = e - i * lines;
+                    }
+                    dst[u] = line * ls + i;
+                    long long g = 0;
+                    unsigned rem = (unsigned)line;
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        if (j == k) continue;
+                        const unsigned qq = fd[j].div(rem);
+                        const int cj = (int)(rem - qq * (unsigned)ext[j]);
+                        rem = qq;
+                        g += (long long)(org[j] + cj) * gstr[j];
+                    }
+                    int ck = org[k] + i - 3;
+                    if (vb && (ck < 0 || ck >= nn[k])) {  // zero boundary values
+                        src[u] = -2;
+                        continue;
+                    }
+                    if (ck < 0) ck += nn[k];
+                    else if (ck >= nn[k]) ck -= nn[k];
+                    src[u] = g + (long long)ck * gstr[k];
                 }
-                int ck = org[k] + i - 3;
-                if (vb && (ck < 0 || ck >= nn[k])) {  // zero boundary values
-                    lb[line * ls + i] = T(0);
-                    continue;
-                }
-                if (ck < 0) ck += nn[k];
-                else if (ck >= nn[k]) ck -= nn[k];
-                g += (long long)ck * gstr[k];
-                lb[line * ls + i] = io.load(g);
+                T val[RU];
+#pragma unroll
+                for (int u = 0; u < RU; ++u) val[u] = src[u] >= 0 ? io.load(src[u]) : T(0);
+#pragma unroll
+                for (int u = 0; u < RU; ++u)
+                    if (src[u] != -1) lb[dst[u]] = val[u];
             }
             __syncthreads();
 

@@ -195,16 +195,19 @@ def _cut(h, dim, n):
 
 def test_relax_example5b_4d_sparse_vs_single_grid(sg):
     """Example 5 (b): 4-D, N_r = 10, N_L = 3 (finest 80^4) to t = 3, and the 80^4 single grid to
-    t = 0.5 (FP32 batched).  The paper compares 2-D cuts of f: the x1-v1 cuts through x2 = v2 =
-    0 of the two runs differ by the sparse grid's approximation error (about 10% of the cut's
-    maximum already in the combined initial condition: the coarsest grids have h = 1 against
-    the oscillation of sin(x^2/2)^2), and that difference does not grow by t = 0.5; H_log of the
-    two agrees within 10%, H_log decays and the mass stays near 1.  (H_2 = sum f^2 / M of the
-    sparse solution is dominated by the combination's small values at the corners, where
-    M ~ e^{-50}, so it is printed but not compared.)"""
+    t = 0.5 (FP32 batched).  The paper compares 2-D cuts of f.  The combined initial condition
+    matches the single grid's to a fraction of a percent, but after the evolution the x1-v1
+    cuts through x2 = v2 = 0 differ by about 10% of the cut's maximum: the component grids are
+    coarse (10 nodes, h = 1, on the axes at level 0) for a solution that rotates in phase
+    space.  A sparse set with finer component grids and the same finest grid (N_r = 20,
+    N_L = 2) comes closer, which attributes the gap to the resolution of the components (the
+    FP64 path matches the oracle bit for bit in 4-D).  H_log agrees within 10%, decays, and the
+    mass stays near 1.  (H_2 = sum f^2 / M of the sparse solution is dominated by the
+    combination's small values at the corners, where M ~ e^{-50}: printed, not compared.)"""
     times = [0.5, 1.0, 2.0, 3.0]
     res = {}
-    for name, nr, nl, ts in (("sparse", 10, 3, times), ("single", 80, 0, times[:1])):
+    for name, nr, nl, ts in (("sparse", 10, 3, times), ("sparse_nr20_nl2", 20, 2, times[:1]),
+                             ("single", 80, 0, times[:1])):
         h = _make(4, nr, nl, P.SG_F32, P.SG_BATCHED)
         out = []
         try:
@@ -230,12 +233,14 @@ def test_relax_example5b_4d_sparse_vs_single_grid(sg):
             print("example5b %s t=%.1f H2 %.6g Hlog %.6f mass %.6f (%.3f s, %d steps)" % ((name, t) + a))
         print("example5b %s points %d" % (name, pts))
     sp, si = res["sparse"][0], res["single"][0]
-    rels = []
-    for j in (3, 2):
-        cs, cg = res["sparse"][j], res["single"][j]
-        rels.append(np.max(np.abs(cs - cg)) / np.max(np.abs(cg)))
-    print("example5b x1-v1 cut: max|sparse - single| / max|single| = %.4f at t = 0, %.4f at t = 0.5" % tuple(rels))
-    assert rels[1] < 0.2 and rels[1] < 1.5 * rels[0] + 0.02
+    def rel(name, j):
+        cs, cg = res[name][j], res["single"][j]
+        return np.max(np.abs(cs - cg)) / np.max(np.abs(cg))
+
+    r0, r5, rf = rel("sparse", 3), rel("sparse", 2), rel("sparse_nr20_nl2", 2)
+    print("example5b x1-v1 cut: max|sparse - single| / max|single| = %.4f at t = 0, %.4f at t = 0.5; "
+          "N_r = 20, N_L = 2: %.4f at t = 0.5" % (r0, r5, rf))
+    assert r0 < 0.01 and r5 < 0.2 and rf < r5
     assert all(y[1] < x[1] for x, y in zip(sp, sp[1:]))
     assert all(abs(x[2] - 1.0) < 2e-3 for x in sp + si)
     assert abs(sp[0][1] - si[0][1]) <= 0.1 * abs(si[0][1])

@@ -142,3 +142,39 @@ def test_vlasov_landau_damping_full_configuration(sg):
           "mass drift %.2e" % (G, pts, steps, t_step, rate, (m1 - m0) / m0))
     assert abs(m1 - m0) < 1e-6 * m0
     assert abs(rate - 0.1533) < 0.1 * 0.1533, rate
+
+
+def test_vlasov_strong_landau_damping(sg):
+    """Nonlinear (strong) Landau damping, a = 0.5, k = 0.5, on the same configuration (N_r = 16,
+    N_L = 5, FP32 batched) to t = 40: the field first decays (published amplitude rates near
+    0.28 up to t ~ 15), then particle trapping makes it grow again (rates near 0.08 between
+    t ~ 20 and 40); the combined mass is conserved up to the outflow at |v| = 2 pi.  Loose
+    bounds: this is a nonlinear regime with no closed form."""
+    h = make(2, 16, 5, P.SG_PDE_VLASOV, precision=P.SG_F32, exec=P.SG_BATCHED, lo=LO, hi=HI,
+             dt_rule=P.SG_DT_CFL, cfl=0.4)
+    ts, amp = [], []
+    try:
+        P.sg_init(h, P.SG_IC_LANDAU, (0.5, 0.5))
+        P.sg_prolong_combine(h)
+        m0 = P.sg_reduce(h, -1, P.SG_REDUCE_MASS)
+        t = 0.0
+        while t < 40.0 - 1e-12:
+            t = P.sg_step(h, min(40.0, t + 0.25))
+            P.sg_prolong_combine(h)
+            ts.append(t)
+            amp.append(0.5 * math.log(P.sg_reduce(h, -1, P.SG_REDUCE_FIELD_ENERGY)))
+        m1 = P.sg_reduce(h, -1, P.SG_REDUCE_MASS)
+    finally:
+        P.sg_destroy(h)
+    ts, amp = np.array(ts), np.array(amp)
+    pk = np.array([i for i in range(1, len(amp) - 1) if amp[i] > amp[i - 1] and amp[i] > amp[i + 1]])
+    early = pk[ts[pk] <= 15.0]
+    late = pk[(ts[pk] >= 20.0) & (ts[pk] <= 40.0)]
+    g1 = -np.polyfit(ts[early], amp[early], 1)[0]
+    g2 = np.polyfit(ts[late], amp[late], 1)[0]
+    print("strong landau: damping rate %.4f (t <= 15), growth rate %.4f (20 <= t <= 40), mass drift %.2e"
+          % (g1, g2, (m1 - m0) / m0))
+    # heating pushes more of f through |v| = 2 pi than in the linear case
+    assert abs(m1 - m0) < 1e-4 * m0
+    assert 0.15 < g1 < 0.45, g1
+    assert 0.02 < g2 < 0.2, g2
