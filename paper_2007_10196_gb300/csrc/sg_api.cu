@@ -158,7 +158,7 @@ struct sg_ctx {
     std::vector<long long> mu_offset;
     long long max_nx = 0;  // Vlasov-Boltzmann: largest space-node count of a grid
     double relax_s = 0.0;  // Vlasov-Boltzmann: normalisation of the Example 5 initial condition (0: not yet formed)
-    long long box_elems = 0;  // stage kernel: elements of one padded box (d <= 3)
+    long long box_elems = 0;  // stage kernel: elements of one padded box (d <= 3) or of the line buffer
     size_t smem = 0;          // stage kernel: dynamic shared memory per block
     // device tables (single handle or batch)
     std::vector<GridDesc> hgrids;
@@ -295,6 +295,7 @@ void stage_footprint(sg_ctx* h) {
     for (const GridDesc& d : h->hgrids) {
         long long b, f;
         if (h->dim == 3 && h->variant == 0) sg::sweep_footprint(d.te, &b, &f);
+        else if (h->dim >= 4 || h->variant == 2) sg::line_footprint(h->dim, d.te, &b, &f);
         else sg::box_footprint(h->dim, d.te, &b, &f);
         box = std::max(box, b);
         flux = std::max(flux, f);

@@ -2,6 +2,7 @@
 // expression is evaluated as written (no fused multiply-add): the FP64 path then performs
 // the same IEEE-754 operations, in the same order, as a plain sequential evaluation of the
 // paper's formulas.  Also holds the precision-independent launchers.
+#include <algorithm>
 #include "sg_launch_impl.cuh"
 
 namespace sg {
@@ -25,6 +26,15 @@ void box_footprint(int d, const int* te, long long* box, long long* flux) {
     for (int k = 0; k < d; ++k) f += p / te[k] * (te[k] + 1);
     *box = b;
     *flux = f;
+}
+
+void line_footprint(int d, const int* te, long long* box, long long* acc) {
+    long long p = 1;
+    for (int k = 0; k < d; ++k) p *= te[k];
+    long long b = 1;
+    for (int k = 0; k < d; ++k) b = std::max(b, p / te[k] * (long long)((te[k] + 6) | 1));
+    *box = b;
+    *acc = p;
 }
 
 void sweep_footprint(const int* te, long long* box, long long* flux) {

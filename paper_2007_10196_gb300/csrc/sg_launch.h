@@ -11,6 +11,10 @@ namespace sg {
 // Shared-memory footprint (elements) of the d <= 3 stage kernel for tile extents te[0..d-1]:
 // two padded boxes (box) and the flux arrays of all axes (flux).
 void box_footprint(int d, const int* te, long long* box, long long* flux);
+// Shared memory (elements) of the line-sweep kernel (d >= 4; d = 2 variant 2) for tile extents
+// te[0..d-1]: the line buffer of the widest axis, lines x ((te_k + 6) | 1) (box), and one
+// accumulator per tile point (acc).
+void line_footprint(int d, const int* te, long long* box, long long* acc);
 // The same for the d = 3 line-sweep kernel (odd x stride; three 512-point difference arrays).
 void sweep_footprint(const int* te, long long* box, long long* flux);
 // Tile extents of the d = 3 line-sweep kernel: <= 8 per axis (at most 512 points, 192 lines),
@@ -19,8 +23,9 @@ void sweep_tile(const int* n, int* te);
 
 template <class T>
 struct Launch {
-    // Dynamic shared memory (bytes) of the stage kernel: d <= 3 uses the padded-box kernel
-    // (2 box + flux elements), d >= 4 and variant 2 the line-buffer kernel (fixed by ppt).
+    // Dynamic shared memory (bytes) of the stage kernel: the padded-box kernel (d <= 3) holds
+    // 2 box + flux elements, the line-sweep kernel (d >= 4; variant 2) box + flux (line buffer
+    // and accumulators, from line_footprint).
     static size_t stage_smem(int dim, int ppt, long long box, long long flux, int variant = 0);
     // Raises the kernel's shared-memory limit and returns resident blocks per SM (0 if the
     // configuration cannot run).  variant: 0 = the default kernel of the dimension (d = 3:

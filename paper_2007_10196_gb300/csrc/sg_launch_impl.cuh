@@ -77,8 +77,9 @@ inline int grid_for(long long n, int threads) {
 
 template <class T>
 size_t Launch<T>::stage_smem(int dim, int ppt, long long box, long long flux, int variant) {
+    (void)ppt;
     if (dim <= 3 && variant != 2) return sizeof(T) * (size_t)(2 * box + flux);
-    return sizeof(T) * (size_t)(LineSmem<1>::LB + LineSmem<1>::FB) * (size_t)ppt;
+    return sizeof(T) * (size_t)(box + flux);
 }
 
 template <class T>

@@ -880,33 +880,31 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
 }
 
 // ------------------------------------------------------------------------------------
-// d >= 4 (and any d): line-buffer kernel.  For each axis k the tile's lines along k plus a
-// 3-point periodic halo are staged in shared memory, every interface flux of the tile along
-// k is computed once, and each thread subtracts (F_{i+1/2} - F_{i-1/2}) / h_k for its points.
+// d >= 4 (and d = 2 for the Vlasov-Boltzmann model): line-sweep kernel over staged lines.
+// Per tile and axis k (in the order 0, 1, ...): the tile's lines along k with a 3-point halo at
+// each end are staged in shared memory (periodic wrap), four global loads in flight per thread;
+// then each thread takes one line and slides the five-point windows of f^+ and f^- along it
+// (SweepSide, as in the d = 3 sweep kernel), so every interface flux is formed once from the
+// split values of its stencil, and subtracts (F_{i+1/2} - F_{i-1/2}) / h_k from the point's
+// accumulator in shared memory: L = ((0 - D_0) - D_1) - ..., the operation order of the FP64
+// definition.  Finally each point takes the RK stage update.
 // Vlasov-Boltzmann (pde 3, d = 2 d_x): halos beyond the ends are 0; the flux along space axis
 // k is v_k u and along velocity axis k is -x_k u, v_k (x_k) the line's node on the partner
 // axis; the LF alpha of an axis is the largest |partner node| of the grid; after the flux
 // differences each point adds (mu(v) rho(x) - u) / tau (rho from G->ef, mu from G->mu).
+// Shared memory: the line buffer (A.box_elems elements: the largest lines x ((e_k + 6) | 1) of
+// any axis of any tile) and the accumulators (one per tile point).
 // ------------------------------------------------------------------------------------
-template <int PPT>
-struct LineSmem {
-    // worst case over tile shapes with P <= SG_NT*PPT points and extents >= 1:
-    // line buffer (ek + 7) * P / ek <= 8 P; flux buffer (ek + 2) * P / ek <= 3 P
-    static constexpr int P = SG_NT * PPT;
-    static constexpr int LB = 8 * P;
-    static constexpr int FB = 3 * P;
-};
-
 template <class T, int D, int PPT>
 __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A) {
     extern __shared__ __align__(16) unsigned char sg_smem_raw[];
     T* lb = reinterpret_cast<T*>(sg_smem_raw);
-    T* fb = lb + LineSmem<PPT>::LB;
-    __shared__ T red[SG_NT / 32];
+    T* accs = lb + A.box_elems;
 
     const int tid = threadIdx.x;
     const PhysParams& ph = A.phys;
-    const float eps12f = (float)(12.0 * ph.eps);
+    const T eps12 = (T)(12.0 * ph.eps);
+    const bool burgers = ph.pde == 1;
     const bool vb = ph.pde == 3;
     constexpr int DX = D / 2;  // Vlasov-Boltzmann: space axes 0..DX-1, velocity axes DX..D-1
 
@@ -919,7 +917,7 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
         StageIO<T> io;
         io.setup(G, A.stage, stage_parity<T>(S));
 
-        int org[D], ext[D], nn[D];
+        int org[D], ext[D], nn[D], tstr[D];
         long long gstr[D];
         FDiv fd[D];
         int P = 1;
@@ -932,58 +930,36 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
                 org[k] = tc[k] * G->te[k];
                 ext[k] = min(G->te[k], nn[k] - org[k]);
                 gstr[k] = k == 0 ? 1LL : gstr[k - 1] * (long long)nn[k - 1];
+                tstr[k] = P;
                 fd[k].init((unsigned)ext[k]);
                 P *= ext[k];
             }
         }
         const T alpha_slot = alpha_dec<T>(A.alpha[w.grid * 3 + A.stage]);
+        const T half_alpha = (T)0.5 * alpha_slot;
 
-        int cp[PPT][D];
-        bool own[PPT];
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-            const int p = tid + q * SG_NT;
-            own[q] = p < P;
-            unsigned r = (unsigned)(own[q] ? p : 0);
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const unsigned qq = fd[k].div(r);
-                cp[q][k] = (int)(r - qq * (unsigned)ext[k]);
-                r = qq;
-            }
-        }
-        T acc[PPT];
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) acc[q] = T(0);
-
-#pragma unroll
+#pragma unroll 1
         for (int k = 0; k < D; ++k) {
-            const int ek = ext[k];
+            // this axis's scalars, selected with compile-time indices (no dynamically indexed arrays)
+            int ek = 1, ok = 0, nk = 1, tk = 1;
+            long long gk = 1;
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+                if (j == k) {
+                    ek = ext[j];
+                    ok = org[j];
+                    nk = nn[j];
+                    tk = tstr[j];
+                    gk = gstr[j];
+                }
             const int lines = P / ek;
-            const int ls = (ek + 6) | 1;  // odd strides avoid bank conflicts
-            const int fs = (ek + 1) | 1;
-            T alpha = ph.pde == 1 ? alpha_slot : (T)sg_abs(ph.adv[k]);
-            const T ak = (T)ph.adv[k];
-            FDiv fl, fr, ff;
+            const int ls = (ek + 6) | 1;  // odd stride against bank conflicts
+            FDiv fl, fr;
             fl.init((unsigned)lines);
             fr.init((unsigned)(ek + 6));
-            ff.init((unsigned)(ek + 1));
-            // Vlasov-Boltzmann: partner axis, LF alpha (an end node), and the divisor that takes
-            // a line index (axes j != k, fastest first) to its partner-axis coordinate
-            const int pk = k < DX ? k + DX : k - DX;
-            FDiv fmp;
-            if (vb) {
-                const T c0 = (T)G->lo[pk], c1 = (T)G->lo[pk] + (T)(nn[pk] - 1) * (T)G->h[pk];
-                alpha = sg_max(sg_abs(c0), sg_abs(c1));
-                int mulp = 1;
-#pragma unroll
-                for (int j = 0; j < D; ++j)
-                    if (j != k && j < pk) mulp *= ext[j];
-                fmp.init((unsigned)mulp);
-            }
 
-            // stage the lines with their halos: four elements per thread and round, addresses
-            // first, then the four loads in flight, then the shared-memory stores
+            // ---- stage the lines with their halos: four elements per thread and round,
+            // addresses first, then the four loads in flight, then the shared-memory stores
             const int NL = lines * (ek + 6);
             constexpr int RU = 4;
             for (int e0 = tid; e0 < NL; e0 += RU * SG_NT) {
@@ -1014,14 +990,14 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
                         rem = qq;
                         g += (long long)(org[j] + cj) * gstr[j];
                     }
-                    int ck = org[k] + i - 3;
-                    if (vb && (ck < 0 || ck >= nn[k])) {  // zero boundary values
+                    int ck = ok + i - 3;
+                    if (vb && (ck < 0 || ck >= nk)) {  // zero boundary values
                         src[u] = -2;
                         continue;
                     }
-                    if (ck < 0) ck += nn[k];
-                    else if (ck >= nn[k]) ck -= nn[k];
-                    src[u] = g + (long long)ck * gstr[k];
+                    if (ck < 0) ck += nk;
+                    else if (ck >= nk) ck -= nk;
+                    src[u] = g + (long long)ck * gk;
                 }
                 T val[RU];
 #pragma unroll
@@ -1032,78 +1008,116 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
             }
             __syncthreads();
 
-            const int NF = lines * (ek + 1);
-            for (int e = tid; e < NF; e += SG_NT) {
-                const int line = (int)ff.div((unsigned)e);
-                const int i = e - line * (ek + 1);
-                const T* v = lb + line * ls + i;
-                T akl = ak;
-                if (vb) {  // the line's node on the partner axis: v_k along x_k, -x_k along v_k
-                    const unsigned qq = fmp.div((unsigned)line);
-                    const int cpk = (int)(qq - fd[pk].div(qq) * (unsigned)ext[pk]);
-                    const T c = (T)G->lo[pk] + (T)(org[pk] + cpk) * (T)G->h[pk];
-                    akl = k < DX ? c : -c;
-                }
-                if constexpr (sizeof(T) == 8) {
-                    fb[line * fs + i] = Weno<double>::interface((const double*)v, 1, (double)alpha, (double)akl, ph);
-                } else {
-                    fb[line * fs + i] = Weno<float>::interface((const float*)v, 1, (float)alpha, (float)akl, ph,
-                                                               eps12f);
-                }
-            }
-            __syncthreads();
-
+            // ---- sweep: one line per thread
             const T rdx = grid_rdx<T>(G, k);
+            const int pk = k < DX ? k + DX : k - DX;  // Vlasov-Boltzmann partner axis
+            T ak = T(0);
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                if (!own[q]) continue;
-                int line = 0, mul = 1;
+            for (int j = 0; j < D; ++j)
+                if (j == k) ak = (T)ph.adv[j];
+            T alpha = burgers ? alpha_slot : sg_abs(ak);
+            if (vb) {  // the largest |partner node| of the grid (an end node)
+                const T c0 = (T)G->lo[pk], c1 = (T)G->lo[pk] + (T)(G->n[pk] - 1) * (T)G->h[pk];
+                alpha = sg_max(sg_abs(c0), sg_abs(c1));
+            }
+            for (int line = tid; line < lines; line += SG_NT) {
+                // the line's first point in the tile, and its node on the partner axis
+                int pb = 0, cpk = 0;
+                unsigned rem = (unsigned)line;
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
                     if (j == k) continue;
-                    line += cp[q][j] * mul;
-                    mul *= ext[j];
+                    const unsigned qq = fd[j].div(rem);
+                    const int cj = (int)(rem - qq * (unsigned)ext[j]);
+                    rem = qq;
+                    pb += cj * tstr[j];
+                    if (j == pk) cpk = cj + org[j];
                 }
-                const T* F = fb + line * fs + cp[q][k];
-                acc[q] = acc[q] - (F[1] - F[0]) * rdx;
-            }
-            __syncthreads();
-        }
-
-        if (vb) {  // relaxation (mu(v) rho(x) - u) / tau, after every axis
-            const T* rho = (const T*)G->ef;
-            const T* mu = (const T*)G->mu;
-            const T tau = (T)ph.tau;
-#pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                if (!own[q]) continue;
-                long long ix = 0, iv = 0, sv = 1;
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    if (k < DX) {
-                        ix += (long long)(org[k] + cp[q][k]) * gstr[k];
+                T akl = ak;
+                if (vb) {  // v_k along x_k, -x_k along v_k
+                    const T c = (T)G->lo[pk] + (T)cpk * (T)G->h[pk];
+                    akl = k < DX ? c : -c;
+                }
+                const T cp = (T)0.5 * (akl + alpha), cm = (T)0.5 * (akl - alpha);
+                const T* v = lb + line * ls;
+                auto fplus = [&](int j) -> T {
+                    if constexpr (sizeof(T) == 8) {
+                        double fp, fm;
+                        Weno<double>::split(v[j], alpha, akl, ph.pde, fp, fm);
+                        return fp;
                     } else {
-                        iv += (long long)(org[k] + cp[q][k]) * sv;
-                        sv *= nn[k];
+                        if (burgers) {
+                            float fp, fm;
+                            Weno<float>::split_burgers(v[j], half_alpha, fp, fm);
+                            return fp;
+                        }
+                        return cp * v[j];
                     }
+                };
+                auto fminus = [&](int j) -> T {
+                    if constexpr (sizeof(T) == 8) {
+                        double fp, fm;
+                        Weno<double>::split(v[j], alpha, akl, ph.pde, fp, fm);
+                        return fm;
+                    } else {
+                        if (burgers) {
+                            float fp, fm;
+                            Weno<float>::split_burgers(v[j], half_alpha, fp, fm);
+                            return fm;
+                        }
+                        return cm * v[j];
+                    }
+                };
+                SweepSide<T> Pw, Mw;
+                // interface between local points -1 and 0: f^+ at buffer 0..4, f^- mirrored at 5..1
+                Pw.init(fplus(0), fplus(1), fplus(2), fplus(3), fplus(4), eps12);
+                Mw.init(fminus(5), fminus(4), fminus(3), fminus(2), fminus(1), eps12);
+                T Fprev = sweep_flux(Pw, Mw, ph);
+                T* a = accs + pb;
+#pragma unroll 2
+                for (int i = 1; i <= ek; ++i) {
+                    Pw.push_back(fplus(i + 4), eps12);
+                    Mw.push_front(fminus(i + 5), eps12);
+                    const T F = sweep_flux(Pw, Mw, ph);
+                    const T Dv = (F - Fprev) * rdx;
+                    *a = (k == 0 ? T(0) : *a) - Dv;
+                    a += tk;
+                    Fprev = F;
                 }
-                const T u = io.load(ix + gstr[DX] * iv);
-                acc[q] = acc[q] + (mu[iv] * rho[ix] - u) / tau;
             }
+            __syncthreads();  // accumulators complete; the line buffer is free for the next axis
         }
 
+        // ---- relaxation (Vlasov-Boltzmann), stage update, alpha of the result
         T mx = T(0);
         bool bad = false;
+        const T* rho = (const T*)G->ef;
+        const T* mu = (const T*)G->mu;
+        const T tau = (T)ph.tau;
+        for (int p = tid; p < P; p += SG_NT) {
+            unsigned rem = (unsigned)p;
+            long long g = 0, ix = 0, iv = 0, sv = 1;
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-            if (!own[q]) continue;
-            long long g = 0;
-#pragma unroll
-            for (int k = 0; k < D; ++k) g += (long long)(org[k] + cp[q][k]) * gstr[k];
-            const T o = io.update(g, acc[q], dt);
+            for (int j = 0; j < D; ++j) {
+                const unsigned qq = fd[j].div(rem);
+                const int cj = (int)(rem - qq * (unsigned)ext[j]) + org[j];
+                rem = qq;
+                g += (long long)cj * gstr[j];
+                if (j < DX) {
+                    ix += (long long)cj * gstr[j];
+                } else {
+                    iv += (long long)cj * sv;
+                    sv *= nn[j];
+                }
+            }
+            T L = accs[p];
+            if (vb) L = L + (mu[iv] * rho[ix] - io.load(g)) / tau;
+            const T o = io.update(g, L, dt);
             if (!sg_isfinite(o)) bad = true;
             mx = sg_max(mx, sg_abs(o));
         }
-        stage_epilogue(A, w, G, it, mx, bad, red);
+        // no barrier here: the next tile writes the line buffer (not read in the update) and the
+        // accumulators only after its own staging barrier
+        stage_epilogue_warp(A, w, G, it, mx, bad);
     }
 }
