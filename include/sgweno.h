@@ -154,7 +154,8 @@ sg_status sg_params_init(sg_params *p);
  * stencil needs five distinct points on every periodic line), level = N_L with
  * 0 <= N_L <= 16 and N_r 2^{N_L} <= 2^20, pde one of SG_PDE_*.  Allocates every component
  * grid's three RK arrays on the device.  *out receives the handle.  Errors: SG_ERR_ARG for
- * out-of-range arguments, SG_ERR_UNSUPPORTED for a non-periodic bc, SG_ERR_NOMEM, SG_ERR_CUDA. */
+ * out-of-range arguments, SG_ERR_UNSUPPORTED for a non-periodic bc or a component grid of 2^31
+ * or more points, SG_ERR_NOMEM, SG_ERR_CUDA. */
 sg_status sg_create(int dim, int root_cells, int level, int pde, const sg_params *params,
                     sg_handle *out);
 

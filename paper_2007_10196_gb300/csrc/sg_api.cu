@@ -1152,7 +1152,13 @@ sg_status sg_create(int dim, int root_cells, int level, int pde, const sg_params
         h->total_pts = 0;
         for (int g = 0; g < h->G; ++g) {
             long long n = 1;
-            for (int k = 0; k < dim; ++k) n *= (long long)root_cells << h->levels[g][k];
+            for (int k = 0; k < dim; ++k) {
+                n *= (long long)root_cells << h->levels[g][k];  // < 2^31 * 2^20: no overflow
+                if (n >= (1LL << 31)) {  // the stage kernels index within a grid with 32-bit offsets
+                    delete h;
+                    return fail(SG_ERR_UNSUPPORTED, "component grid %d has 2^31 or more points", g);
+                }
+            }
             h->npts.push_back(n);
             h->offset.push_back(h->total_pts);
             h->total_pts += n;

@@ -86,6 +86,15 @@ def test_argument_errors_without_gpu(built):
     with pytest.raises(P.SgError) as e:
         P.sg_create(3, 10, 3, P.SG_PDE_ADVECTION, P.sg_params_init(tile_points=300))
     assert e.value.status == P.SG_ERR_ARG
+    with pytest.raises(P.SgError) as e:  # 1300^3 > 2^31 points in one grid (32-bit offsets)
+        P.sg_create(3, 1300, 0, P.SG_PDE_ADVECTION)
+    assert e.value.status == P.SG_ERR_UNSUPPORTED and "2^31" in P.sg_last_error()
+    with pytest.raises(P.SgError) as e:  # six axes of 2^20 nodes: the count must not overflow
+        P.sg_create(6, 1 << 20, 0, P.SG_PDE_ADVECTION)
+    assert e.value.status == P.SG_ERR_UNSUPPORTED
+    with pytest.raises(P.SgError) as e:  # the Vlasov-Boltzmann model has d space and d velocity axes
+        P.sg_create(3, 10, 1, P.SG_PDE_VLASOV_BOLTZMANN)
+    assert e.value.status == P.SG_ERR_ARG
     assert P.lib().sg_destroy(None) == 0
 
 
