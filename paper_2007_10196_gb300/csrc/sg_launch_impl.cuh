@@ -79,7 +79,7 @@ template <class T>
 size_t Launch<T>::stage_smem(int dim, int ppt, long long box, long long flux, int variant) {
     (void)ppt;
     if (dim <= 3 && variant != 2) return sizeof(T) * (size_t)(2 * box + flux);
-    return sizeof(T) * (size_t)(box + flux);
+    return sizeof(T) * (size_t)(box + flux) + sizeof(int) * (size_t)flux;  // + per-line offsets
 }
 
 template <class T>

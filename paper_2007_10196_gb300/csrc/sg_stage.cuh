@@ -893,10 +893,12 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
 // axis; the LF alpha of an axis is the largest |partner node| of the grid; after the flux
 // differences each point adds (mu(v) rho(x) - u) / tau (rho from G->ef, mu from G->mu).
 // Shared memory: the line buffer (A.box_elems elements: the largest lines x ((e_k + 6) | 1) of
-// any axis of any tile) and the accumulators (one per tile point).
+// any axis of any tile), the accumulators (one per tile point) and, per axis, each line's
+// offset from the tile origin (one int per tile point at most).  Offsets within a grid are
+// 32-bit, relative to the tile origin (grids hold fewer than 2^31 points).
 // ------------------------------------------------------------------------------------
 template <class T, int D, int PPT>
-__global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A) {
+__global__ void __launch_bounds__(SG_NT, sizeof(T) == 4 ? 4 : 1) sg_stage_line_kernel(const StageArgs A) {
     extern __shared__ __align__(16) unsigned char sg_smem_raw[];
     T* lb = reinterpret_cast<T*>(sg_smem_raw);
     T* accs = lb + A.box_elems;
@@ -917,32 +919,35 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
         StageIO<T> io;
         io.setup(G, A.stage, stage_parity<T>(S));
 
-        int org[D], ext[D], nn[D], tstr[D];
-        long long gstr[D];
+        int org[D], ext[D], nn[D], tstr[D], gstr[D];
         FDiv fd[D];
         int P = 1;
         {
             int tc[D];
             tile_coords<D>(G, (unsigned)w.tile, tc);
+            long long o = 0, st = 1;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 nn[k] = G->n[k];
                 org[k] = tc[k] * G->te[k];
                 ext[k] = min(G->te[k], nn[k] - org[k]);
-                gstr[k] = k == 0 ? 1LL : gstr[k - 1] * (long long)nn[k - 1];
+                gstr[k] = (int)st;  // < 2^31: the grid holds fewer points
+                o += (long long)org[k] * st;
+                st *= nn[k];
                 tstr[k] = P;
                 fd[k].init((unsigned)ext[k]);
                 P *= ext[k];
             }
+            io.shift(o);  // offsets below are relative to the tile's first point
         }
+        int* lbase = reinterpret_cast<int*>(accs + P);  // per-line offsets of the current axis
         const T alpha_slot = alpha_dec<T>(A.alpha[w.grid * 3 + A.stage]);
         const T half_alpha = (T)0.5 * alpha_slot;
 
 #pragma unroll 1
         for (int k = 0; k < D; ++k) {
             // this axis's scalars, selected with compile-time indices (no dynamically indexed arrays)
-            int ek = 1, ok = 0, nk = 1, tk = 1;
-            long long gk = 1;
+            int ek = 1, ok = 0, nk = 1, tk = 1, gk = 1;
 #pragma unroll
             for (int j = 0; j < D; ++j)
                 if (j == k) {
@@ -958,18 +963,34 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
             fl.init((unsigned)lines);
             fr.init((unsigned)(ek + 6));
 
+            // ---- each line's offset from the tile origin (axes j != k), once per line
+            for (int line = tid; line < lines; line += SG_NT) {
+                int g = 0;
+                unsigned rem = (unsigned)line;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    if (j == k) continue;
+                    const unsigned qq = fd[j].div(rem);
+                    g += (int)(rem - qq * (unsigned)ext[j]) * gstr[j];
+                    rem = qq;
+                }
+                lbase[line] = g;
+            }
+            __syncthreads();
+
             // ---- stage the lines with their halos: four elements per thread and round,
             // addresses first, then the four loads in flight, then the shared-memory stores
             const int NL = lines * (ek + 6);
             constexpr int RU = 4;
             for (int e0 = tid; e0 < NL; e0 += RU * SG_NT) {
-                int dst[RU];
-                long long src[RU];  // -1: no element; -2: a zero boundary value
+                int dst[RU], src[RU];
+                unsigned char kind[RU];  // 0: no element; 1: load; 2: a zero boundary value
 #pragma unroll
                 for (int u = 0; u < RU; ++u) {
                     const int e = e0 + u * SG_NT;
-                    src[u] = -1;
+                    kind[u] = 0;
                     dst[u] = 0;
+                    src[u] = 0;
                     if (e >= NL) continue;
                     int line, i;
                     if (k == 0) {
@@ -980,31 +1001,22 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
                         line = e - i * lines;
                     }
                     dst[u] = line * ls + i;
-                    long long g = 0;
-                    unsigned rem = (unsigned)line;
-#pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        if (j == k) continue;
-                        const unsigned qq = fd[j].div(rem);
-                        const int cj = (int)(rem - qq * (unsigned)ext[j]);
-                        rem = qq;
-                        g += (long long)(org[j] + cj) * gstr[j];
-                    }
                     int ck = ok + i - 3;
                     if (vb && (ck < 0 || ck >= nk)) {  // zero boundary values
-                        src[u] = -2;
+                        kind[u] = 2;
                         continue;
                     }
                     if (ck < 0) ck += nk;
                     else if (ck >= nk) ck -= nk;
-                    src[u] = g + (long long)ck * gk;
+                    kind[u] = 1;
+                    src[u] = lbase[line] + (ck - ok) * gk;
                 }
                 T val[RU];
 #pragma unroll
-                for (int u = 0; u < RU; ++u) val[u] = src[u] >= 0 ? io.load(src[u]) : T(0);
+                for (int u = 0; u < RU; ++u) val[u] = kind[u] == 1 ? io.load(src[u]) : T(0);
 #pragma unroll
                 for (int u = 0; u < RU; ++u)
-                    if (src[u] != -1) lb[dst[u]] = val[u];
+                    if (kind[u]) lb[dst[u]] = val[u];
             }
             __syncthreads();
 
@@ -1096,18 +1108,20 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_line_kernel(const StageArgs A)
         const T tau = (T)ph.tau;
         for (int p = tid; p < P; p += SG_NT) {
             unsigned rem = (unsigned)p;
-            long long g = 0, ix = 0, iv = 0, sv = 1;
+            int g = 0, ix = 0, iv = 0, sv = 1;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 const unsigned qq = fd[j].div(rem);
-                const int cj = (int)(rem - qq * (unsigned)ext[j]) + org[j];
+                const int cj = (int)(rem - qq * (unsigned)ext[j]);
                 rem = qq;
-                g += (long long)cj * gstr[j];
-                if (j < DX) {
-                    ix += (long long)cj * gstr[j];
-                } else {
-                    iv += (long long)cj * sv;
-                    sv *= nn[j];
+                g += cj * gstr[j];
+                if (vb) {
+                    if (j < DX) {
+                        ix += (cj + org[j]) * gstr[j];
+                    } else {
+                        iv += (cj + org[j]) * sv;
+                        sv *= nn[j];
+                    }
                 }
             }
             T L = accs[p];
