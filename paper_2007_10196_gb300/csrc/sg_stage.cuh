@@ -883,9 +883,10 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
 // d >= 4 (and d = 2 for the Vlasov-Boltzmann model): line-sweep kernel over staged lines.
 // Per tile and axis k (in the order 0, 1, ...): the tile's lines along k with a 3-point halo at
 // each end are staged in shared memory (periodic wrap), four global loads in flight per thread;
-// then each thread takes one line and slides the five-point windows of f^+ and f^- along it
-// (SweepSide, as in the d = 3 sweep kernel), so every interface flux is formed once from the
-// split values of its stencil, and subtracts (F_{i+1/2} - F_{i-1/2}) / h_k from the point's
+// then each thread takes a segment of at most 8 points of one line and slides the five-point
+// windows of f^+ and f^- along it (SweepSide, as in the d = 3 sweep kernel), so every interface
+// flux is formed once (twice at a segment boundary) from the split values of its stencil, and
+// subtracts (F_{i+1/2} - F_{i-1/2}) / h_k from the point's
 // accumulator in shared memory: L = ((0 - D_0) - D_1) - ..., the operation order of the FP64
 // definition.  Finally each point takes the RK stage update.
 // Vlasov-Boltzmann (pde 3, d = 2 d_x): halos beyond the ends are 0; the flux along space axis
@@ -963,20 +964,24 @@ __global__ void __launch_bounds__(SG_NT, sizeof(T) == 4 ? 4 : 1) sg_stage_line_k
             fl.init((unsigned)lines);
             fr.init((unsigned)(ek + 6));
 
-            // ---- each line's offset from the tile origin (axes j != k), once per line
-            for (int line = tid; line < lines; line += SG_NT) {
-                int g = 0;
-                unsigned rem = (unsigned)line;
+            // ---- each line's offset from the tile origin (axes j != k), once per line (d >= 4;
+            // with one other axis the staging below decomposes the line index itself)
+            constexpr bool kLineTable = D >= 4;
+            if (kLineTable) {
+                for (int line = tid; line < lines; line += SG_NT) {
+                    int g = 0;
+                    unsigned rem = (unsigned)line;
 #pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    if (j == k) continue;
-                    const unsigned qq = fd[j].div(rem);
-                    g += (int)(rem - qq * (unsigned)ext[j]) * gstr[j];
-                    rem = qq;
+                    for (int j = 0; j < D; ++j) {
+                        if (j == k) continue;
+                        const unsigned qq = fd[j].div(rem);
+                        g += (int)(rem - qq * (unsigned)ext[j]) * gstr[j];
+                        rem = qq;
+                    }
+                    lbase[line] = g;
                 }
-                lbase[line] = g;
+                __syncthreads();
             }
-            __syncthreads();
 
             // ---- stage the lines with their halos: four elements per thread and round,
             // addresses first, then the four loads in flight, then the shared-memory stores
@@ -1009,7 +1014,20 @@ __global__ void __launch_bounds__(SG_NT, sizeof(T) == 4 ? 4 : 1) sg_stage_line_k
                     if (ck < 0) ck += nk;
                     else if (ck >= nk) ck -= nk;
                     kind[u] = 1;
-                    src[u] = lbase[line] + (ck - ok) * gk;
+                    int base = 0;
+                    if (kLineTable) {
+                        base = lbase[line];
+                    } else {
+                        unsigned rem = (unsigned)line;
+#pragma unroll
+                        for (int j = 0; j < D; ++j) {
+                            if (j == k) continue;
+                            const unsigned qq = fd[j].div(rem);
+                            base += (int)(rem - qq * (unsigned)ext[j]) * gstr[j];
+                            rem = qq;
+                        }
+                    }
+                    src[u] = base + (ck - ok) * gk;
                 }
                 T val[RU];
 #pragma unroll
@@ -1032,7 +1050,13 @@ __global__ void __launch_bounds__(SG_NT, sizeof(T) == 4 ? 4 : 1) sg_stage_line_k
                 const T c0 = (T)G->lo[pk], c1 = (T)G->lo[pk] + (T)(G->n[pk] - 1) * (T)G->h[pk];
                 alpha = sg_max(sg_abs(c0), sg_abs(c1));
             }
-            for (int line = tid; line < lines; line += SG_NT) {
+            // segments of at most 8 points, so that long lines (d = 2 tiles) still spread over the
+            // block's threads; consecutive threads take consecutive lines.  (Shorter segments to
+            // occupy more threads measured slower: each segment sets up its own windows.)
+            const int nseg = (ek + 7) >> 3;
+            for (int task = tid; task < lines * nseg; task += SG_NT) {
+                const int seg = (int)fl.div((unsigned)task), line = task - seg * lines;
+                const int i0 = seg << 3, i1 = min(ek, i0 + 8);
                 // the line's first point in the tile, and its node on the partner axis
                 int pb = 0, cpk = 0;
                 unsigned rem = (unsigned)line;
@@ -1081,13 +1105,14 @@ __global__ void __launch_bounds__(SG_NT, sizeof(T) == 4 ? 4 : 1) sg_stage_line_k
                     }
                 };
                 SweepSide<T> Pw, Mw;
-                // interface between local points -1 and 0: f^+ at buffer 0..4, f^- mirrored at 5..1
-                Pw.init(fplus(0), fplus(1), fplus(2), fplus(3), fplus(4), eps12);
-                Mw.init(fminus(5), fminus(4), fminus(3), fminus(2), fminus(1), eps12);
+                // interface between local points i0-1 and i0 (buffer index = local + 3): f^+ at
+                // buffer i0..i0+4, f^- mirrored at i0+5..i0+1
+                Pw.init(fplus(i0), fplus(i0 + 1), fplus(i0 + 2), fplus(i0 + 3), fplus(i0 + 4), eps12);
+                Mw.init(fminus(i0 + 5), fminus(i0 + 4), fminus(i0 + 3), fminus(i0 + 2), fminus(i0 + 1), eps12);
                 T Fprev = sweep_flux(Pw, Mw, ph);
-                T* a = accs + pb;
+                T* a = accs + pb + i0 * tk;
 #pragma unroll 2
-                for (int i = 1; i <= ek; ++i) {
+                for (int i = i0 + 1; i <= i1; ++i) {
                     Pw.push_back(fplus(i + 4), eps12);
                     Mw.push_front(fminus(i + 5), eps12);
                     const T F = sweep_flux(Pw, Mw, ph);
