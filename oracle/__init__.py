@@ -14,7 +14,10 @@ with Lagrange prolongation (grid set, coefficients, prolongation, combination), 
 4 and 6 single-grid rows (epsilon and the LF alpha convention), the smoothness-indicator
 integrals of Eq. (10), polynomial exactness of the flux difference and the interpolants,
 the printed 2-D/3-D/4-D combination formulas, mass conservation and the Burgers
-characteristic equation.
+characteristic equation.  The kinetic workloads: the Vlasov-Poisson field solve and Landau
+damping rate (tests/test_oracle_pins.py), and the Vlasov-Boltzmann relaxation model of
+Example 5 (tests/test_oracle_relax_pins.py: phase-space rotation, moment equations,
+stationary state, 4-D separability, entropy closed forms).
 """
 from __future__ import annotations
 

@@ -59,6 +59,7 @@ def test_params_struct_layout_and_defaults(built):
     assert p.eps == 1e-3 and p.precision == P.SG_F64 and p.cfl == 0.4
     assert list(p.hi) == [4.0] * 6
     assert p.tile_points == 0 and p.stage_kernel == P.SG_STAGE_AUTO and p.combine_budget_gb == 0.0
+    assert p.theta == 1.0 and p.tau == 1.0
 
 
 def test_argument_errors_without_gpu(built):
