@@ -59,7 +59,7 @@ FP32_LANES_PER_SM = 128
 # Burgers shock time of u0 = 0.5 + a sin(pi (x+y+z)/2): characteristics in s = x+y+z move at
 # 3u, so they first cross at t = 1 / (3 a pi/2); members with a below this stay smooth to t_end.
 A_SMOOTH_AT_T_END = 2.0 / (3.0 * math.pi * 0.3)
-STAGE_SOURCES = ("sg_stage.cuh", "sg_weno.cuh", "sg_device.h")
+STAGE_SOURCES = ("sg_stage.cuh", "sg_weno.cuh", "sg_device.h")  # the d = 3 sweep kernel and what it includes
 # Vlasov-Boltzmann (Example 5), FP32 line-buffer stage kernel, per point per RK stage: per axis
 # the split of the point (2: the line speed times the value, twice), two one-sided WENO5
 # reconstructions (2 x 54), their combination (7) and the flux difference (3); then the
@@ -178,6 +178,24 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
                 "reasons": sorted(reasons)}
+
+
+def _cpu_model():
+    """The host CPU's model name (lscpu) and the cores this process may run on."""
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        ncpu = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        ncpu = os.cpu_count() or 1
+    return "%s (%d cores available)" % (name or "unknown", ncpu)
 
 
 def _peaks():
@@ -329,6 +347,7 @@ def run_ours(args, rank, world, local_rank):
         P.sg_step(batch, inputs.BATCH_T_END)
         ev_step1.record(stream)
         P.sg_prolong_combine(batch)  # every member, sharing the batch's intermediates
+        ev_comb1.record(stream)
         ext = [(P.sg_reduce(h, -1, P.SG_REDUCE_MIN), P.sg_reduce(h, -1, P.SG_REDUCE_MAX)) for h in hs]
         if host_out is not None:
             for h, buf in zip(hs, host_out):
@@ -340,6 +359,7 @@ def run_ours(args, rank, world, local_rank):
 
     ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev_step0, ev_step1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev_comb1 = torch.cuda.Event(enable_timing=True)
 
     def barrier():
         torch.cuda.synchronize()
@@ -354,6 +374,7 @@ def run_ours(args, rank, world, local_rank):
         P.sg_set_profiling(batch, True)
         launches0 = sum(P.sg_launch_count(h) for h in all_h)
         step_ms = []
+        comb_ms = []
         times = []
         barrier()
         vis = os.environ.get("CUDA_VISIBLE_DEVICES")
@@ -366,6 +387,7 @@ def run_ours(args, rank, world, local_rank):
                 ev_b.synchronize()
                 times.append(ev_a.elapsed_time(ev_b))
                 step_ms.append(ev_step0.elapsed_time(ev_step1))
+                comb_ms.append(ev_step1.elapsed_time(ev_comb1))
         barrier()
         launches = sum(P.sg_launch_count(h) for h in all_h) - launches0
         stage_ms, stage_launches = P.sg_profile(batch)
@@ -430,7 +452,7 @@ def run_ours(args, rank, world, local_rank):
         pool.close()
         cpu = {"value": upd_c / wall_c, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "all %d members, first time step each (FP64 C oracle, one process per core)" % len(members),
-               "seconds": wall_c}
+               "seconds": wall_c, "cpu_model": _cpu_model()}
     line = {
         "metric": METRIC, "value": total_upd / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
@@ -449,7 +471,8 @@ def run_ours(args, rank, world, local_rank):
                 "frac": hbm_gbs / float(peaks.get("hbm_gbs", 6800.0)), "peak_source": src,
                 "bytes_per_point_step": BYTES_PER_POINT_STEP},
         "breakdown_ms": {"step_to_t_end": statistics.mean(step_ms), "stage_kernels": stage_ms / args.steps,
-                         "stage_launches": stage_launches // args.steps},
+                         "stage_launches": stage_launches // args.steps,
+                         "prolong_combine": statistics.mean(comb_ms)},
         "stepping_rate": upd_per_pass / (statistics.mean(step_ms) / 1e3),
         "bound_overshoot": over,
         "fp64_plain_vs_fp32_batched": compare,
@@ -564,7 +587,7 @@ def run_kinetic(args):
         pool.close()
         cpu = {"value": u_c / w_c, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "all %d grids, first time step each (FP64 C oracle, one process per core)" % G,
-               "seconds": w_c}
+               "seconds": w_c, "cpu_model": _cpu_model()}
     line = {
         "metric": METRIC, "value": upd * args.steps / (sum(times) / 1e3), "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
@@ -603,7 +626,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "members": len(members), "seed": 2007},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": _cpu_model()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -10,4 +10,5 @@
 #pragma once
 #include "sg_weno.cuh"
 #include "sg_stage.cuh"
+#include "sg_stage_line.cuh"
 #include "sg_aux.cuh"
