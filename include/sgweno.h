@@ -42,7 +42,7 @@ typedef enum {
     SG_ERR_CUDA = 4,        /* a CUDA runtime call failed */
     SG_ERR_NONFINITE = 5,   /* a NaN or Inf appeared in the solution */
     SG_ERR_TIMEOUT = 6,     /* a bounded wait ran out */
-    SG_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
+    SG_ERR_UNSUPPORTED = 7  /* valid request the library does not implement */
 } sg_status;
 
 /* PDE of Eq. (1): linear advection f_k(u) = a_k u, or Burgers f_k(u) = u^2/2 on every axis.
