@@ -57,7 +57,7 @@ class Problem(C.Structure):
     ]
 
 
-ADVECTION, BURGERS, VLASOV, VLASOV_BOLTZMANN = 0, 1, 2, 3
+ADVECTION, BURGERS, VLASOV, VLASOV_BOLTZMANN, VLASOV_MAXWELL = 0, 1, 2, 3, 4
 WENO5, LINEAR5 = 0, 1
 PROLONG_WENO5, PROLONG_LAGRANGE5 = 0, 1
 DT_POW53, DT_CFL = 0, 1
@@ -95,6 +95,10 @@ def lib():
             "orc_restrict_landau": (None, [P, _ip, C.c_double, C.c_double, _dp]),
             "orc_field_energy": (C.c_double, [P, _ip, _dp]),
             "orc_vb_density": (None, [P, _ip, _dp, _dp]),
+            "orc_state_points": (C.c_long, [P, _ip]),
+            "orc_vm_currents": (None, [P, _ip, _dp, _dp, _dp]),
+            "orc_restrict_vm": (None, [P, _ip] + [C.c_double] * 6 + [_dp]),
+            "orc_vm_energy": (None, [P, _ip, _dp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "orc_relax_norm": (C.c_double, [P]),
             "orc_restrict_relax": (None, [P, _ip, C.c_double, _dp]),
             "orc_relax_entropy": (None, [P, _ip, _dp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -164,6 +168,7 @@ def spatial_operator(p, levels, u):
 
 def rk3_step(p, levels, u, dt):
     u = np.array(u, dtype=np.float64).reshape(-1)
+    assert u.size == state_points(p, levels)
     work = np.empty(3 * u.size, dtype=np.float64)
     lib().orc_rk3_step(C.byref(p), _lev(levels), u, dt, work)
     return u
@@ -181,10 +186,15 @@ def concat(grids):
                                                 for g in grids]))
 
 
+def state_points(p, levels) -> int:
+    """Values of one grid's state (its nodes; Vlasov-Maxwell: and its three field arrays)."""
+    return int(lib().orc_state_points(C.byref(p), _lev(levels)))
+
+
 def split(p, levels, flat):
     out, off = [], 0
     for lv in np.asarray(levels).reshape(-1, p.dim):
-        n = int(np.prod(shape(p, lv)))
+        n = state_points(p, lv)
         out.append(flat[off:off + n].copy())
         off += n
     return out
@@ -311,3 +321,24 @@ def relax_entropy(p: Problem, levels, u):
     lib().orc_relax_entropy(C.byref(p), _lev(levels), np.ascontiguousarray(u, np.float64),
                             C.byref(h2), C.byref(hl))
     return float(h2.value), float(hl.value)
+
+
+def vm_state(p: Problem, levels, beta=0.01, delta=0.5, v1=0.3, v2=0.3, b=0.001, k0=0.2):
+    """Example 6 initial state of one grid (pde VLASOV_MAXWELL): f, then E_1, E_2, B_3."""
+    u = np.empty(state_points(p, levels), dtype=np.float64)
+    lib().orc_restrict_vm(C.byref(p), _lev(levels), beta, delta, v1, v2, b, k0, u)
+    return u
+
+
+def vm_currents(p: Problem, levels, u):
+    nx = int(p.nr) << int(levels[0])
+    j1, j2 = np.empty(nx), np.empty(nx)
+    lib().orc_vm_currents(C.byref(p), _lev(levels), np.ascontiguousarray(u, np.float64), j1, j2)
+    return j1, j2
+
+
+def vm_energy(p: Problem, levels, u):
+    """(kinetic, field) energy of one Vlasov-Maxwell grid."""
+    k, f = C.c_double(), C.c_double()
+    lib().orc_vm_energy(C.byref(p), _lev(levels), np.ascontiguousarray(u, np.float64), C.byref(k), C.byref(f))
+    return float(k.value), float(f.value)

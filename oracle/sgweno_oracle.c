@@ -51,6 +51,17 @@
  *    flattened order; mu_inf(v) = exp(-(|v|^2 / (2 theta))) / (2 pi theta)^{d/2} with |v|^2
  *    summed in axis order; the relaxation term (mu_inf rho - f) / tau is added to the
  *    transport operator after all axes, from the same stage input.
+ * Vlasov-Maxwell (pde 4; Example 6), dim = 3: axis 0 = x_2 (periodic), axes 1, 2 = xi_1, xi_2
+ * (periodic, as the example states):
+ *  - the state of a grid is f followed by its own fields E_1, E_2, B_3 on its x_2 nodes;
+ *  - f: transport speed xi_2 along x_2, E_1 + xi_2 B_3 along xi_1, E_2 - xi_1 B_3 along xi_2,
+ *    each constant on a grid line; LF alpha of an axis = the largest |speed| over the grid;
+ *  - currents j_m = (h_1 h_2) sum_xi f xi_m (velocity nodes in ascending flattened order);
+ *  - Maxwell: w+ = E_1 + B_3 moves at speed -1 and w- = E_1 - B_3 at +1, both with source
+ *    -j_1 (the characteristic form of dB_3/dt = dE_1/dx_2, dE_1/dt = dB_3/dx_2 - j_1), each
+ *    by the LF-split WENO5 operator with alpha = 1; then dE_1/dt = (L+ + L-)/2,
+ *    dB_3/dt = (L+ - L-)/2 and dE_2/dt = -j_2; all from the same stage input;
+ *  - the CFL step takes max(max|xi_2|, 1) along x_2 (the fields' speed is 1).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -65,7 +76,8 @@ typedef struct {
     int pde;           /* 0: linear advection f_k = a_k u;  1: Burgers f_k = u^2/2;
                           2: Vlasov-Poisson (d = 2, axis 0 = x, axis 1 = v): f_x = v u,
                           f_v = E(x) u, E from the grid's own density (see orc_efield);
-                          3: Vlasov-Boltzmann relaxation (dim = 2d, see vb_operator) */
+                          3: Vlasov-Boltzmann relaxation (dim = 2d, see vb_operator);
+                          4: Vlasov-Maxwell (dim = 3, see vm_operator) */
     int scheme;        /* 0: WENO5-JS weights (5);  1: fifth-order linear scheme, w_r = d_r */
     int prolong;       /* 0: WENO5 interpolation (11);  1: fifth-order Lagrange (8) */
     double eps;        /* epsilon of (5) and (9) */
@@ -128,6 +140,14 @@ static long grid_points(const orc_problem *P, const int *levels, long *n)
         tot *= n[k];
     }
     return tot;
+}
+
+/* Values of one grid's state: its nodes, and for pde 4 the fields E_1, E_2, B_3 (n_0 each). */
+long orc_state_points(const orc_problem *P, const int *levels)
+{
+    long n[ORC_MAXD];
+    long N = grid_points(P, levels, n);
+    return P->pde == 4 ? N + 3 * n[0] : N;
 }
 
 long orc_grid_points(const orc_problem *P, const int *levels)
@@ -263,6 +283,24 @@ double orc_lf_alpha(const orc_problem *P, const int *levels, const double *u, in
                 if (s > a) a = s;
             }
             free(E);
+        }
+        return a;
+    }
+    if (P->pde == 4) {  /* xi_2 along x_2; E_1 + xi_2 B_3 along xi_1; E_2 - xi_1 B_3 along xi_2 */
+        const double *E1 = u + N, *E2 = E1 + n[0], *B3 = E2 + n[0];
+        long i, j;
+        if (k == 0) {
+            for (j = 0; j < n[2]; ++j) {
+                double s = fabs(node(P, 2, j, n[2]));
+                if (s > a) a = s;
+            }
+        } else {
+            for (i = 0; i < n[0]; ++i)
+                for (j = 0; j < n[3 - k]; ++j) {
+                    double xi = node(P, 3 - k, j, n[3 - k]);
+                    double s = fabs(k == 1 ? E1[i] + xi * B3[i] : E2[i] - xi * B3[i]);
+                    if (s > a) a = s;
+                }
         }
         return a;
     }
@@ -434,6 +472,137 @@ static void vb_operator(const orc_problem *P, const int *levels, const double *u
     free(F);
 }
 
+/* Currents of one Vlasov-Maxwell grid (pde 4): j_m[i] = (h_1 h_2) sum_xi f xi_m over the
+ * velocity nodes in ascending flattened order (xi_1 fastest). */
+void orc_vm_currents(const orc_problem *P, const int *levels, const double *u, double *j1, double *j2)
+{
+    long n[ORC_MAXD], i, a, b;
+    double hv;
+    grid_points(P, levels, n);
+    hv = 1.0;
+    hv = hv * spacing(P, 1, n[1]);
+    hv = hv * spacing(P, 2, n[2]);
+    for (i = 0; i < n[0]; ++i) {
+        double s1 = 0.0, s2 = 0.0;
+        for (b = 0; b < n[2]; ++b)
+            for (a = 0; a < n[1]; ++a) {
+                double fv = u[i + n[0] * (a + n[1] * b)];
+                s1 = s1 + fv * node(P, 1, a, n[1]);
+                s2 = s2 + fv * node(P, 2, b, n[2]);
+            }
+        j1[i] = hv * s1;
+        j2[i] = hv * s2;
+    }
+}
+
+/* -(F_{i+1/2} - F_{i-1/2}) / h of the LF-split WENO5 flux of f = a u on a periodic line of n
+ * values (alpha = |a|), into out. */
+static void weno_periodic_line(const orc_problem *P, const double *u, long n, double a, double rdx,
+                               double *out)
+{
+    double alpha = fabs(a);
+    double *fp = (double *)malloc(sizeof(double) * n);
+    double *fm = (double *)malloc(sizeof(double) * n);
+    double *F = (double *)malloc(sizeof(double) * n);
+    long i;
+    for (i = 0; i < n; ++i) {
+        double fj = a * u[i];
+        fp[i] = 0.5 * (fj + alpha * u[i]);
+        fm[i] = 0.5 * (fj - alpha * u[i]);
+    }
+    for (i = 0; i < n; ++i) {
+        long im2 = (i - 2 + 2 * n) % n, im1 = (i - 1 + n) % n;
+        long ip1 = (i + 1) % n, ip2 = (i + 2) % n, ip3 = (i + 3) % n;
+        double fplus = orc_weno5_side(fp[im2], fp[im1], fp[i], fp[ip1], fp[ip2], P->eps, P->scheme == 1);
+        double fminus = orc_weno5_side(fm[ip3], fm[ip2], fm[ip1], fm[i], fm[im1], P->eps, P->scheme == 1);
+        F[i] = fplus + fminus;
+    }
+    for (i = 0; i < n; ++i) out[i] = 0.0 - (F[i] - F[(i - 1 + n) % n]) * rdx;
+    free(fp);
+    free(fm);
+    free(F);
+}
+
+/* Vlasov-Maxwell operator (pde 4): f by the periodic LF-split WENO5 flux differences of
+ * speed * f along each axis (axis order, L = ((0 - D_0) - D_1) - D_2), the speed constant on
+ * each line; the fields by the characteristic form of Maxwell's equations (see the header). */
+static void vm_operator(const orc_problem *P, const int *levels, const double *u, const long *n,
+                        double *L)
+{
+    long N = n[0] * n[1] * n[2], nx = n[0], stride[3], k, i;
+    const double *E1 = u + N, *E2 = E1 + nx, *B3 = E2 + nx;
+    double *LE1 = L + N, *LE2 = LE1 + nx, *LB3 = LE2 + nx;
+    long nmax = n[0] > n[1] ? n[0] : n[1];
+    double *fp, *fm, *F, *j1, *j2, *wp, *wm, *Lp, *Lm;
+    if (n[2] > nmax) nmax = n[2];
+    stride[0] = 1;
+    stride[1] = n[0];
+    stride[2] = n[0] * n[1];
+    fp = (double *)malloc(sizeof(double) * nmax);
+    fm = (double *)malloc(sizeof(double) * nmax);
+    F = (double *)malloc(sizeof(double) * nmax);
+    for (k = 0; k < 3; ++k) {
+        long nk = n[k], sk = stride[k], nlines = N / nk, line;
+        double alpha = orc_lf_alpha(P, levels, u, (int)k);
+        double rdx = 1.0 / spacing(P, (int)k, nk);
+        for (line = 0; line < nlines; ++line) {
+            long below = line % sk, above = line / sk;
+            long base = below + above * sk * nk;
+            long ix = base % n[0];
+            double a;
+            if (k == 0) a = node(P, 2, (base / stride[2]) % n[2], n[2]);
+            else if (k == 1) a = E1[ix] + node(P, 2, (base / stride[2]) % n[2], n[2]) * B3[ix];
+            else a = E2[ix] - node(P, 1, (base / stride[1]) % n[1], n[1]) * B3[ix];
+            for (i = 0; i < nk; ++i) {
+                double uj = u[base + i * sk];
+                double fj = a * uj;
+                fp[i] = 0.5 * (fj + alpha * uj);
+                fm[i] = 0.5 * (fj - alpha * uj);
+            }
+            for (i = 0; i < nk; ++i) {
+                long im2 = (i - 2 + 2 * nk) % nk, im1 = (i - 1 + nk) % nk;
+                long ip1 = (i + 1) % nk, ip2 = (i + 2) % nk, ip3 = (i + 3) % nk;
+                double fplus = orc_weno5_side(fp[im2], fp[im1], fp[i], fp[ip1], fp[ip2], P->eps, P->scheme == 1);
+                double fminus = orc_weno5_side(fm[ip3], fm[ip2], fm[ip1], fm[i], fm[im1], P->eps, P->scheme == 1);
+                F[i] = fplus + fminus;
+            }
+            for (i = 0; i < nk; ++i) {
+                long il = (i - 1 + nk) % nk;
+                L[base + i * sk] = L[base + i * sk] - (F[i] - F[il]) * rdx;
+            }
+        }
+    }
+    free(fp);
+    free(fm);
+    free(F);
+    /* fields */
+    j1 = (double *)malloc(sizeof(double) * nx);
+    j2 = (double *)malloc(sizeof(double) * nx);
+    wp = (double *)calloc((size_t)nx, sizeof(double));
+    wm = (double *)calloc((size_t)nx, sizeof(double));
+    Lp = (double *)malloc(sizeof(double) * nx);
+    Lm = (double *)malloc(sizeof(double) * nx);
+    orc_vm_currents(P, levels, u, j1, j2);
+    for (i = 0; i < nx; ++i) {
+        wp[i] = E1[i] + B3[i];
+        wm[i] = E1[i] - B3[i];
+    }
+    weno_periodic_line(P, wp, nx, -1.0, 1.0 / spacing(P, 0, nx), Lp);
+    weno_periodic_line(P, wm, nx, 1.0, 1.0 / spacing(P, 0, nx), Lm);
+    for (i = 0; i < nx; ++i) {
+        double lp = Lp[i] - j1[i], lm = Lm[i] - j1[i];
+        LE1[i] = 0.5 * (lp + lm);
+        LE2[i] = 0.0 - j2[i];
+        LB3[i] = 0.5 * (lp - lm);
+    }
+    free(j1);
+    free(j2);
+    free(wp);
+    free(wm);
+    free(Lp);
+    free(Lm);
+}
+
 /* ------------------------------------------------------------------------------------
  * Spatial operator L(u) = - sum_k (fhat_{i+1/2} - fhat_{i-1/2}) / h_k, Eq. (2) applied
  * dimension by dimension (Section 2.1), with the LF split (7) and fhat = fhat^+ + fhat^-.
@@ -453,6 +622,11 @@ void orc_spatial_operator(const orc_problem *P, const int *levels, const double 
     }
     if (P->pde == 3) {
         vb_operator(P, levels, u, n, L);
+        return;
+    }
+    if (P->pde == 4) {
+        for (p = N; p < orc_state_points(P, levels); ++p) L[p] = 0.0;
+        vm_operator(P, levels, u, n, L);
         return;
     }
 
@@ -500,12 +674,11 @@ void orc_spatial_operator(const orc_problem *P, const int *levels, const double 
  *   u1 = u + dt L(u)
  *   u2 = 3/4 u + 1/4 (u1 + dt L(u1))
  *   u  = 1/3 u + 2/3 (u2 + dt L(u2))
- * work must hold 3 * N doubles.
+ * work must hold 3 * N doubles, N the grid's state size (orc_state_points).
  * ---------------------------------------------------------------------------------- */
 void orc_rk3_step(const orc_problem *P, const int *levels, double *u, double dt, double *work)
 {
-    long n[ORC_MAXD];
-    long N = grid_points(P, levels, n), p;
+    long N = orc_state_points(P, levels), p;
     double *u1 = work, *u2 = work + N, *L = work + 2 * N;
     orc_spatial_operator(P, levels, u, L);
     for (p = 0; p < N; ++p) u1[p] = u[p] + dt * L[p];
@@ -544,8 +717,9 @@ double orc_dt(const orc_problem *P, int G, const int *levels, const double *grid
             for (g = 0; g < G; ++g) {
                 double ag = orc_lf_alpha(P, levels + g * P->dim, u, k);
                 if (ag > a) a = ag;
-                u += orc_grid_points(P, levels + g * P->dim);
+                u += orc_state_points(P, levels + g * P->dim);
             }
+            if (P->pde == 4 && k == 0 && a < 1.0) a = 1.0;  /* the fields move at speed 1 */
             s = s + a / fine_spacing(P, k);
         }
         return cfl / s;
@@ -565,7 +739,7 @@ long orc_solve(const orc_problem *P, int G, const int *levels, double *grids, do
     double t = t0;
     double *work;
     for (g = 0; g < G; ++g) {
-        long Ng = orc_grid_points(P, levels + g * P->dim);
+        long Ng = orc_state_points(P, levels + g * P->dim);
         if (Ng > Nmax) Nmax = Ng;
     }
     work = (double *)malloc(sizeof(double) * 3 * Nmax);
@@ -579,7 +753,7 @@ long orc_solve(const orc_problem *P, int G, const int *levels, double *grids, do
         }
         for (g = 0; g < G; ++g) {
             orc_rk3_step(P, levels + g * P->dim, u, dt, work);
-            u += orc_grid_points(P, levels + g * P->dim);
+            u += orc_state_points(P, levels + g * P->dim);
         }
         t = last ? t_end : t + dt;
         ++steps;
@@ -723,6 +897,56 @@ void orc_relax_entropy(const orc_problem *P, const int *levels, const double *u,
     }
     *h2 = s2 * vol;
     *hlog = sl * vol;
+}
+
+/* Example 6 initial state of one Vlasov-Maxwell grid (pde 4): f = exp(-xi_2^2/beta)
+ * (delta exp(-(xi_1 - v1)^2/beta) + (1 - delta) exp(-(xi_1 + v2)^2/beta)) / (pi beta) at the
+ * nodes, E_1 = E_2 = 0, B_3 = b sin(k0 x_2). */
+void orc_restrict_vm(const orc_problem *P, const int *levels, double beta, double delta, double v1,
+                     double v2, double b, double k0, double *u)
+{
+    long n[ORC_MAXD];
+    long N = grid_points(P, levels, n), i, a, c;
+    double *E1 = u + N, *E2 = E1 + n[0], *B3 = E2 + n[0];
+    for (c = 0; c < n[2]; ++c) {
+        double x2 = node(P, 2, c, n[2]);
+        double g2 = exp(-((x2 * x2) / beta));
+        for (a = 0; a < n[1]; ++a) {
+            double x1 = node(P, 1, a, n[1]);
+            double d1 = x1 - v1, d2 = x1 + v2;
+            double g1 = delta * exp(-((d1 * d1) / beta)) + (1.0 - delta) * exp(-((d2 * d2) / beta));
+            double f = (g2 * g1) / (3.14159265358979323846 * beta);
+            for (i = 0; i < n[0]; ++i) u[i + n[0] * (a + n[1] * c)] = f;
+        }
+    }
+    for (i = 0; i < n[0]; ++i) {
+        E1[i] = 0.0;
+        E2[i] = 0.0;
+        B3[i] = b * sin(k0 * node(P, 0, i, n[0]));
+    }
+}
+
+/* Energies of one Vlasov-Maxwell grid (pde 4): kinetic sum f |xi|^2/2 dV and field
+ * sum (E_1^2 + E_2^2 + B_3^2)/2 dx. */
+void orc_vm_energy(const orc_problem *P, const int *levels, const double *u, double *kinetic,
+                   double *field)
+{
+    long n[ORC_MAXD];
+    long N = grid_points(P, levels, n), i, a, c;
+    const double *E1 = u + N, *E2 = E1 + n[0], *B3 = E2 + n[0];
+    double sk = 0.0, sf = 0.0, hx = spacing(P, 0, n[0]);
+    double dV = hx * spacing(P, 1, n[1]) * spacing(P, 2, n[2]);
+    for (c = 0; c < n[2]; ++c) {
+        double x2 = node(P, 2, c, n[2]);
+        for (a = 0; a < n[1]; ++a) {
+            double x1 = node(P, 1, a, n[1]);
+            double e = 0.5 * (x1 * x1 + x2 * x2);
+            for (i = 0; i < n[0]; ++i) sk = sk + u[i + n[0] * (a + n[1] * c)] * e;
+        }
+    }
+    for (i = 0; i < n[0]; ++i) sf = sf + 0.5 * (E1[i] * E1[i] + E2[i] * E2[i] + B3[i] * B3[i]);
+    *kinetic = sk * dV;
+    *field = sf * hx;
 }
 
 /* ------------------------------------------------------------------------------------
@@ -871,7 +1095,7 @@ void orc_combine(const orc_problem *P, int G, const int *levels, const double *c
     for (g = 0; g < G; ++g) {
         orc_prolong_grid(P, levels + g * P->dim, u, pu, pw);
         for (p = 0; p < tot; ++p) uhat[p] = uhat[p] + coeff[g] * pu[p];
-        u += orc_grid_points(P, levels + g * P->dim);
+        u += orc_state_points(P, levels + g * P->dim);
     }
 }
 
@@ -939,7 +1163,7 @@ double orc_combine_point(const orc_problem *P, int G, const int *levels, const d
     int g;
     for (g = 0; g < G; ++g) {
         acc = acc + coeff[g] * orc_prolong_point(P, levels + g * P->dim, u, J);
-        u += orc_grid_points(P, levels + g * P->dim);
+        u += orc_state_points(P, levels + g * P->dim);
     }
     return acc;
 }
