@@ -387,67 +387,6 @@ __global__ void sg_prolong_axis_kernel(const T* __restrict__ in, T* __restrict__
     }
 }
 
-// One prolongation axis with 2-D indexing (no 64-bit division): rows of `below` contiguous
-// values.  below == 1 (axis 0): threads run along the fine axis, blockIdx.y over `above`;
-// otherwise threads run along `below`, blockIdx.y over the (fine index, above) rows.
-// Same arithmetic per output as sg_prolong_axis_kernel.
-template <class T>
-__global__ void sg_prolong_axis2_kernel(const T* __restrict__ in, T* __restrict__ out, long long below, int min_,
-                                        int nf, long long above, int r, double eps, int lagrange,
-                                        unsigned long long nfmag) {
-    const T e12 = (T)(12.0 * eps);
-    if (below == 1) {
-        for (long long hi = blockIdx.y; hi < above; hi += gridDim.y) {
-            const T* line = in + hi * min_;
-            for (int jf = blockIdx.x * blockDim.x + threadIdx.x; jf < nf; jf += gridDim.x * blockDim.x) {
-                int ic;
-                T s;
-                fine_to_coarse<T>(jf, r, ic, s);
-                T v[5];
-#pragma unroll
-                for (int m = 0; m < 5; ++m) {
-                    v[m] = line[wrap_index(ic - 2 + m, min_)];
-                }
-                T res;
-                if constexpr (sizeof(T) == 8) res = Weno<double>::interp(v[0], v[1], v[2], v[3], v[4], s, eps, lagrange);
-                else res = Weno<float>::interp(v[0], v[1], v[2], v[3], v[4], s, (float)e12, lagrange);
-                out[hi * nf + jf] = res;
-            }
-        }
-        return;
-    }
-    const long long rows = (long long)nf * above;
-    for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
-        // nfmag != 0: rows < 2^32, divide by multiplying
-        const long long hi = nfmag ? (long long)div_mag((unsigned)row, (unsigned)nf, nfmag) : row / nf;
-        const int jf = (int)(row - hi * nf);
-        int ic;
-        T s;
-        fine_to_coarse<T>(jf, r, ic, s);
-        int cs[5];
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            cs[m] = wrap_index(ic - 2 + m, min_);
-        }
-        const T* base = in + hi * below * min_;
-        T* obase = out + (hi * nf + jf) * below;
-        for (long long lo = blockIdx.x * (long long)blockDim.x + threadIdx.x; lo < below;
-             lo += (long long)gridDim.x * blockDim.x) {
-            T res;
-            if (s == T(0)) {
-                res = base[lo + (long long)cs[2] * below];
-            } else {
-                T v[5];
-#pragma unroll
-                for (int m = 0; m < 5; ++m) v[m] = base[lo + (long long)cs[m] * below];
-                if constexpr (sizeof(T) == 8) res = Weno<double>::interp(v[0], v[1], v[2], v[3], v[4], s, eps, lagrange);
-                else res = Weno<float>::interp(v[0], v[1], v[2], v[3], v[4], s, (float)e12, lagrange);
-            }
-            obase[lo] = res;
-        }
-    }
-}
-
 // ------------------------------------------------------------------------------------
 // Step 3, last axis fused with the combination: uhat = sum_g c_g P_{d-1} I_g, where I_g is
 // grid g prolonged over axes 0..d-2 (shape (below, n_g) with below = N_f^{d-1}).  Each thread

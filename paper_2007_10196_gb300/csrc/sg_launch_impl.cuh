@@ -269,23 +269,6 @@ cudaError_t Launch<T>::prolong_axis_win(const T* in, T* out, long long below, in
 }
 
 template <class T>
-cudaError_t Launch<T>::prolong_axis2(const T* in, T* out, long long below, int min_, int nf, long long above,
-                                     int r, double eps, int lagrange, cudaStream_t s) {
-    dim3 grid;
-    if (below == 1) {
-        grid.x = (unsigned)std::min<long long>((nf + 255) / 256, 65535);
-        grid.y = (unsigned)std::min<long long>(above, 65535);
-    } else {
-        grid.x = (unsigned)std::min<long long>((below + 255) / 256, 65535);
-        grid.y = (unsigned)std::min<long long>((long long)nf * above, 65535);
-    }
-    const unsigned long long rows = (unsigned long long)nf * (unsigned long long)above;
-    const unsigned long long nfmag = rows < (1ull << 32) ? sg_div_magic64((unsigned)nf) : 0ull;
-    sg_prolong_axis2_kernel<T><<<grid, 256, 0, s>>>(in, out, below, min_, nf, above, r, eps, lagrange, nfmag);
-    return cudaGetLastError();
-}
-
-template <class T>
 cudaError_t Launch<T>::combine_last_axis(const CombineGrid* tab, int G, double* uhat, long long below, int nf,
                                          int exact_coeffs, int zero_last,
                                          double eps, int lagrange, cudaStream_t s) {
