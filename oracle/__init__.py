@@ -53,7 +53,7 @@ class Problem(C.Structure):
         ("dim", C.c_int), ("nr", C.c_int), ("nl", C.c_int), ("pde", C.c_int),
         ("scheme", C.c_int), ("prolong", C.c_int), ("eps", C.c_double),
         ("lo", C.c_double * MAXD), ("hi", C.c_double * MAXD), ("adv", C.c_double * MAXD),
-        ("theta", C.c_double), ("tau", C.c_double),
+        ("theta", C.c_double), ("tau", C.c_double), ("bc", C.c_int * MAXD),
     ]
 
 
@@ -114,8 +114,11 @@ def lib():
     return _lib
 
 
+BC_PERIODIC, BC_ZERO = 0, 1
+
+
 def problem(dim, nr, nl, pde=ADVECTION, scheme=WENO5, prolong=PROLONG_WENO5, eps=1e-6,
-            lo=0.0, hi=4.0, adv=1.0, theta=1.0, tau=1.0) -> Problem:
+            lo=0.0, hi=4.0, adv=1.0, theta=1.0, tau=1.0, bc=BC_PERIODIC) -> Problem:
     p = Problem()
     p.dim, p.nr, p.nl, p.pde = dim, nr, nl, pde
     p.scheme, p.prolong, p.eps = scheme, prolong, eps
@@ -123,8 +126,9 @@ def problem(dim, nr, nl, pde=ADVECTION, scheme=WENO5, prolong=PROLONG_WENO5, eps
     lo = np.broadcast_to(np.asarray(lo, dtype=np.float64), (dim,))
     hi = np.broadcast_to(np.asarray(hi, dtype=np.float64), (dim,))
     adv = np.broadcast_to(np.asarray(adv, dtype=np.float64), (dim,))
+    bc = np.broadcast_to(np.asarray(bc, dtype=np.int64), (dim,))
     for k in range(dim):
-        p.lo[k], p.hi[k], p.adv[k] = lo[k], hi[k], adv[k]
+        p.lo[k], p.hi[k], p.adv[k], p.bc[k] = lo[k], hi[k], adv[k], int(bc[k])
     return p
 
 

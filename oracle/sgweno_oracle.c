@@ -32,6 +32,12 @@
  *  - prolongation runs axis 0, 1, ..., d-1 (Section 2.2.1);
  *  - the combination sums grids in enumeration order (q = 0, 1, ...; lexicographic
  *    levels within each q, l_0 most significant), into an accumulator that starts at 0.
+ *  - zero boundary (bc[k] = 1, advection and Burgers): the nodes are the same, x_j = lo_k +
+ *    j h_k, j = 0..n_k-1, and u is zero beyond them (three ghost nodes on either side in
+ *    the stencils, two in the interpolation), as for the kinetic models' zero boundaries;
+ *  - the flux difference of Eq. (2) multiplies by 1/h_k, formed once per grid and axis,
+ *    instead of dividing by h_k at every node (the product and the quotient differ by at
+ *    most one rounding; both sides of the parity tests use the product).
  * Vlasov-Poisson (pde 2; not in the paper, the 1D1V kinetic workload run on the same
  * method):
  *  - x is periodic as above; v nodes are v_j = lo_1 + j h_v, j = 0..n_v-1, and f is zero
@@ -84,7 +90,10 @@ typedef struct {
     double lo[ORC_MAXD], hi[ORC_MAXD];
     double adv[ORC_MAXD];   /* a_k for linear advection */
     double theta, tau;      /* pde 3: temperature and relaxation time of L(f) */
+    int bc[ORC_MAXD];       /* pde 0 and 1, per axis: 0 periodic, 1 zero beyond the nodes */
 } orc_problem;
+
+static int zero_axis(const orc_problem *P, int k);
 
 /* ------------------------------------------------------------------------------------
  * Grid set, Section 2.2 and combination formula (13):
@@ -634,10 +643,38 @@ void orc_spatial_operator(const orc_problem *P, const int *levels, const double 
         long nk = n[k], sk = stride[k], i, line;
         double alpha = orc_lf_alpha(P, levels, u, k);
         double rdx = 1.0 / spacing(P, k, nk);
-        double *fp = (double *)malloc(sizeof(double) * nk);
-        double *fm = (double *)malloc(sizeof(double) * nk);
-        double *F = (double *)malloc(sizeof(double) * nk);
+        double *fp = (double *)malloc(sizeof(double) * (nk + 6));
+        double *fm = (double *)malloc(sizeof(double) * (nk + 6));
+        double *F = (double *)malloc(sizeof(double) * (nk + 1));
         long nlines = N / nk;
+        if (zero_axis(P, k)) {
+            /* zero boundary: u = 0 at the three ghost nodes beyond either end, so f = 0 and
+               f^+- = 0 there; interfaces m + 1/2, m = -1..n_k-1, at F[m + 1] */
+            for (line = 0; line < nlines; ++line) {
+                long below = line % sk, above = line / sk;
+                long base = below + above * sk * nk, m;
+                for (m = -3; m < nk + 3; ++m) {
+                    double uj = (m < 0 || m >= nk) ? 0.0 : u[base + m * sk];
+                    double fj = flux(P, k, uj);
+                    fp[m + 3] = 0.5 * (fj + alpha * uj);
+                    fm[m + 3] = 0.5 * (fj - alpha * uj);
+                }
+                for (m = -1; m < nk; ++m) {
+                    const double *P5 = fp + m + 3, *M5 = fm + m + 3;
+                    double fplus = orc_weno5_side(P5[-2], P5[-1], P5[0], P5[1], P5[2], P->eps,
+                                                  P->scheme == 1);
+                    double fminus = orc_weno5_side(M5[3], M5[2], M5[1], M5[0], M5[-1], P->eps,
+                                                   P->scheme == 1);
+                    F[m + 1] = fplus + fminus;
+                }
+                for (m = 0; m < nk; ++m)
+                    L[base + m * sk] = L[base + m * sk] - (F[m + 1] - F[m]) * rdx;
+            }
+            free(fp);
+            free(fm);
+            free(F);
+            continue;
+        }
         for (line = 0; line < nlines; ++line) {
             /* base offset of this line: the index with i_k = 0 */
             long below = line % sk, above = line / sk;
@@ -764,8 +801,9 @@ long orc_solve(const orc_problem *P, int G, const int *levels, double *grids, do
 }
 
 /* ------------------------------------------------------------------------------------
- * Step 1: restriction of u_0(x) = b + a sin(w * (x_0 + ... + x_{d-1}) + phi) to a grid
- * ("functions are evaluated at grid points").  The sum runs over axes in order.
+ * Step 1: restriction of u_0(x) = b + a sin(w * (x_0 + ... + x_{d-1}) + phi) to a grid: the
+ * pointwise restriction of Section 2.2.2, Step 1 (u_0 sampled at the nodes).  The sum runs
+ * over axes in order.
  * ---------------------------------------------------------------------------------- */
 void orc_restrict_sine(const orc_problem *P, const int *levels, double b, double a, double w,
                        double phi, double *u)
@@ -991,7 +1029,7 @@ double orc_weno5_interp(double a, double b, double c, double d, double e, double
  * the Vlasov-Boltzmann model; the others are periodic. */
 static int zero_axis(const orc_problem *P, int k)
 {
-    return (P->pde == 2 && k == 1) || P->pde == 3;
+    return (P->pde == 2 && k == 1) || P->pde == 3 || (P->pde <= 1 && P->bc[k] == 1);
 }
 
 /* Coarse centre and offset of fine node jf on an axis refined by ratio r = 2^{N_L - l}:
