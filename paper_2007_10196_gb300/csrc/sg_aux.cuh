@@ -380,7 +380,7 @@ __global__ void sg_prolong_axis_kernel(const T* __restrict__ in, T* __restrict__
         if constexpr (sizeof(T) == 8) {
             res = Weno<double>::interp(v[0], v[1], v[2], v[3], v[4], s, eps, lagrange);
         } else {
-            res = Weno<float>::interp(v[0], v[1], v[2], v[3], v[4], s, (float)(12.0 * eps), lagrange);
+            res = Weno<float>::interp(v[0], v[1], v[2], v[3], v[4], s, sg_eps4<float>(eps), lagrange);
         }
         if (acc) acc[idx] = acc[idx] + coeff * (double)res;
         else out[idx] = res;
@@ -452,15 +452,16 @@ struct InterpWin<float> {
     // weights.  prepare() forms their coefficients once; eval() is two Horner evaluations.
     float w0, w1, w2, w3, w4;
     float n0, n1, n2, n3, d0, d1, d2;
-    __device__ __forceinline__ void prepare(float eps12, int lagrange) {
+    __device__ __forceinline__ void prepare(float eps4, int lagrange) {
         const float d1_ = w1 - w0, d2_ = w2 - w1, d3_ = w3 - w2, d4_ = w4 - w3;
         const float t0 = d2_ - d1_, t1 = d3_ - d2_, t2 = d4_ - d3_;
         const float s0 = fmaf(3.f, d2_, -d1_), s1 = d2_ + d3_, s2 = fmaf(3.f, d3_, -d4_);
         float E0 = 1.f, E1 = 1.f, E2 = 1.f;  // beta_w_k; 1 for Lagrange
-        if (!lagrange) {
-            const float e0 = fmaf(13.f * t0, t0, fmaf(3.f * s0, s0, eps12));
-            const float e1 = fmaf(13.f * t1, t1, fmaf(3.f * s1, s1, eps12));
-            const float e2 = fmaf(13.f * t2, t2, fmaf(3.f * s2, s2, eps12));
+        if (!lagrange) {  // rescaled as in Weno<float>::side: every E in [1, 2^80], D >= 1/16
+            float e0 = fmaf((13.f / 3.f) * t0, t0, fmaf(s0, s0, eps4));
+            float e1 = fmaf((13.f / 3.f) * t1, t1, fmaf(s1, s1, eps4));
+            float e2 = fmaf((13.f / 3.f) * t2, t2, fmaf(s2, s2, eps4));
+            weno_scale3(e0, e1, e2);
             const float q0 = e0 * e0, q1 = e1 * e1, q2 = e2 * e2;
             E0 = q1 * q2;
             E1 = q0 * q2;
@@ -491,7 +492,7 @@ template <class T, int J, bool EXACT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) sg_combine_last_axis_kernel(const CombineGrid* __restrict__ tab, int G,
                                                                     double* __restrict__ uhat, long long below,
                                                                     int nf, double eps, int lagrange, int zero_last) {
-    const T e12 = (T)(12.0 * eps);
+    const T e12 = sg_eps4<T>(eps);
     const int nchunks = (nf + J - 1) / J;
     // centre index and offset s of the chunk's J fine nodes for every refinement ratio
     // r = 2^lr (lr <= 16): the same for all grids with that ratio and all columns of the block
@@ -583,7 +584,7 @@ template <class T, int J>
 __global__ void __launch_bounds__(256) sg_prolong_axis_win_kernel(const T* __restrict__ in, T* __restrict__ out,
                                                                   long long below, int n, int nf, long long above,
                                                                   int r, double eps, int lagrange, int zero_bc) {
-    const T e12 = (T)(12.0 * eps);
+    const T e12 = sg_eps4<T>(eps);
     const int nchunks = (nf + J - 1) / J;
     const int lr = __ffs(r) - 1;
     const T inv_r = pow2_neg<T>(lr);

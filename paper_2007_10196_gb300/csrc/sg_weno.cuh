@@ -5,7 +5,7 @@
 // Weno<double> evaluates the paper's formulas literally; the translation unit that
 // instantiates it is compiled with --fmad=false so each expression is a fixed sequence of
 // IEEE-754 operations.  Weno<float> evaluates the same mathematics in first differences with
-// one reciprocal per interface (see the comment above it).
+// rescaled smoothness terms and one division per side (see the comment above it).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -233,18 +233,45 @@ struct Weno<double> {
 // ------------------------------------------------------------------------------------
 // FP32: the same mathematics in first differences d_j = f_j - f_{j-1}:
 //   q_r - f_i = (5/6 d2 - 1/3 d1, 1/6 d2 + 1/3 d3, 2/3 d3 - 1/6 d4)
-//   12 (eps + beta_r) = 13 t_r^2 + 3 s_r^2 + 12 eps, t = second differences,
+//   e_r = 4 (eps + beta_r) = (13/3) t_r^2 + s_r^2 + 4 eps, t = second differences,
 //   s = (3 d2 - d1, d2 + d3, 3 d3 - d4)
-//   alpha_r / alpha_1 = (d_r / d_1) prod_{j != r} E_j / prod_{j != 1} E_j, E_r = (12(eps+beta_r))^2
-// so one side needs no division and the two sides of an interface share one reciprocal.
-// (The products stay in float range for |f| differences below ~1e4 when eps >= 1e-8.)
+//   alpha_r / alpha_1 = (d_r / d_1) prod_{j != r} E_j / prod_{j != 1} E_j, E_r = e_r^2
+// so a side needs no division of its own beyond num / den.
+//
+// Range.  The weights of Eq. (5) depend on the e_r only through their ratios, so the three
+// are rescaled before they are squared and multiplied (weno_scale3): divided by the power of
+// two at or below the smallest, exactly, which puts the smallest in [1, 2), and capped at
+// 2^20.  A weight whose e was capped lies below 2^-38 of the largest weight before and after
+// the cap, so the cap changes the result by less than 2^-38 of the candidate fluxes' spread.
+// Every product of two E then lies in [1, 2^80]: the arithmetic neither overflows nor
+// underflows for any eps > 0 (4 eps is raised to 2^-100 if smaller: sg_eps4) and split-flux
+// differences below about 10^13; the quotient num / den is taken per side.
 // ------------------------------------------------------------------------------------
+// 4 eps, the eps term of e_r (FP32 kernels; the FP64 ones use eps itself)
+template <class T>
+__device__ __forceinline__ T sg_eps4(double eps);
+template <>
+__device__ __forceinline__ double sg_eps4<double>(double eps) { return 4.0 * eps; }
+template <>
+__device__ __forceinline__ float sg_eps4<float>(double eps) { return fmaxf((float)(4.0 * eps), 0x1p-100f); }
+
+// e_k <- min(e_k 2^-floor(log2 min_j e_j), 2^20); the scale is built from the exponent bits of
+// the smallest e (normal: e >= 4 eps >= 2^-100), so the division is exact.
+__device__ __forceinline__ void weno_scale3(float& e0, float& e1, float& e2) {
+    const float m = fminf(e0, fminf(e1, e2));
+    const float sc = __uint_as_float(0x7f000000u - (__float_as_uint(m) & 0x7f800000u));
+    e0 = fminf(e0 * sc, 0x1p20f);
+    e1 = fminf(e1 * sc, 0x1p20f);
+    e2 = fminf(e2 * sc, 0x1p20f);
+}
+
 template <>
 struct Weno<float> {
     static __device__ __forceinline__ void side(float a, float b, float c, float d, float e,
-                                                float eps12, int linear, float& num, float& den) {
-        // weights proportional to E_1 E_2 / 6, E_0 E_2, E_0 E_1 / 2 with E_k = (12 eps + 12 beta_k)^2
-        // (linear scheme: E_k = 1), num and den formed factored (as SweepSide<float>::value)
+                                                float eps4, int linear, float& num, float& den) {
+        // weights proportional to E_1 E_2 / 6, E_0 E_2, E_0 E_1 / 2 with E_k = e_k^2 (rescaled;
+        // linear scheme: E_k = 1), num and den formed factored (as SweepSide<float>::value);
+        // den >= 5/3, so num / den is in the accurate range of __fdividef
         const float d1 = b - a, d2 = c - b, d3 = d - c, d4 = e - d;
         const float p0s = fmaf(5.f / 36.f, d2, (-1.f / 18.f) * d1);  // p_0 / 6
         const float p1 = fmaf(1.f / 6.f, d2, (1.f / 3.f) * d3);
@@ -253,9 +280,10 @@ struct Weno<float> {
         if (!linear) {
             const float t0 = d2 - d1, t1 = d3 - d2, t2 = d4 - d3;
             const float s0 = fmaf(3.f, d2, -d1), s1 = d2 + d3, s2 = fmaf(3.f, d3, -d4);
-            const float e0 = fmaf(13.f * t0, t0, fmaf(3.f * s0, s0, eps12));
-            const float e1 = fmaf(13.f * t1, t1, fmaf(3.f * s1, s1, eps12));
-            const float e2 = fmaf(13.f * t2, t2, fmaf(3.f * s2, s2, eps12));
+            float e0 = fmaf((13.f / 3.f) * t0, t0, fmaf(s0, s0, eps4));
+            float e1 = fmaf((13.f / 3.f) * t1, t1, fmaf(s1, s1, eps4));
+            float e2 = fmaf((13.f / 3.f) * t2, t2, fmaf(s2, s2, eps4));
+            weno_scale3(e0, e1, e2);
             E0 = e0 * e0;
             E1 = e1 * e1;
             E2 = e2 * e2;
@@ -271,21 +299,23 @@ struct Weno<float> {
         fm = u * fmaf(0.25f, u, -half_alpha);
     }
 
+    // fhat = fhat^+ + fhat^- from the centres and the (num, den) of the two sides; each den lies
+    // in [5/3, 2^81], inside the range where __fdividef is accurate
     static __device__ __forceinline__ float combine(float cp, float cm, float np, float dp, float nm, float dm) {
-        return (cp + cm) + __fdividef(fmaf(np, dm, nm * dp), dp * dm);
+        return (cp + cm) + (__fdividef(np, dp) + __fdividef(nm, dm));
     }
 
-    static __device__ __forceinline__ float interface_split(const float* p, const float* m, int S, float eps12,
+    static __device__ __forceinline__ float interface_split(const float* p, const float* m, int S, float eps4,
                                                             int linear) {
         float np, dp, nm, dm;
-        side(p[0], p[S], p[2 * S], p[3 * S], p[4 * S], eps12, linear, np, dp);
-        side(m[5 * S], m[4 * S], m[3 * S], m[2 * S], m[S], eps12, linear, nm, dm);
+        side(p[0], p[S], p[2 * S], p[3 * S], p[4 * S], eps4, linear, np, dp);
+        side(m[5 * S], m[4 * S], m[3 * S], m[2 * S], m[S], eps4, linear, nm, dm);
         return combine(p[2 * S], m[3 * S], np, dp, nm, dm);
     }
 
     // raw values u_{L-2} .. u_{L+3} (stride S)
     static __device__ __forceinline__ float interface(const float* v, int S, float alpha, float ak,
-                                                      const PhysParams& ph, float eps12) {
+                                                      const PhysParams& ph, float eps4) {
         float fp[6], fm[6];
         if (ph.pde == 1) {
             const float ha = 0.5f * alpha;
@@ -300,13 +330,13 @@ struct Weno<float> {
             }
         }
         float np, dp, nm, dm;
-        side(fp[0], fp[1], fp[2], fp[3], fp[4], eps12, ph.scheme, np, dp);
-        side(fm[5], fm[4], fm[3], fm[2], fm[1], eps12, ph.scheme, nm, dm);
+        side(fp[0], fp[1], fp[2], fp[3], fp[4], eps4, ph.scheme, np, dp);
+        side(fm[5], fm[4], fm[3], fm[2], fm[1], eps4, ph.scheme, nm, dm);
         return combine(fp[2], fm[3], np, dp, nm, dm);
     }
 
     static __device__ __forceinline__ float interp(float a, float b, float c, float d, float e,
-                                                   float s, float eps12, int lagrange) {
+                                                   float s, float eps4, int lagrange) {
         if (s == 0.f) return c;
         const float d1 = b - a, d2 = c - b, d3 = d - c, d4 = e - d;
         const float t0 = d2 - d1, t1 = d3 - d2, t2 = d4 - d3;
@@ -319,10 +349,11 @@ struct Weno<float> {
         const float C0 = fmaf(s, -0.25f, q), C2 = fmaf(s, 0.25f, q);
         const float C1 = fmaf(ss, -1.f / 6.f, 2.f / 3.f);
         float w0 = C0, w1 = C1, w2 = C2;
-        if (!lagrange) {
-            const float e0 = fmaf(13.f * t0, t0, fmaf(3.f * s0, s0, eps12));
-            const float e1 = fmaf(13.f * t1, t1, fmaf(3.f * s1, s1, eps12));
-            const float e2 = fmaf(13.f * t2, t2, fmaf(3.f * s2, s2, eps12));
+        if (!lagrange) {  // weights of Eq. (9), rescaled as in side(): sum >= 1/16
+            float e0 = fmaf((13.f / 3.f) * t0, t0, fmaf(s0, s0, eps4));
+            float e1 = fmaf((13.f / 3.f) * t1, t1, fmaf(s1, s1, eps4));
+            float e2 = fmaf((13.f / 3.f) * t2, t2, fmaf(s2, s2, eps4));
+            weno_scale3(e0, e1, e2);
             const float E0 = e0 * e0, E1 = e1 * e1, E2 = e2 * e2;
             w0 = C0 * (E1 * E2);
             w1 = C1 * (E0 * E2);
