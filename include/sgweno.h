@@ -62,9 +62,14 @@ typedef enum {
  * mu_inf(v) = exp(-(|v|^2 / (2 theta))) / (2 pi theta)^{d/2} at the velocity nodes (theta and
  * tau from sg_params). */
 enum { SG_PDE_ADVECTION = 0, SG_PDE_BURGERS = 1, SG_PDE_VLASOV = 2, SG_PDE_VLASOV_BOLTZMANN = 3 };
-/* Boundary conditions: periodic (SG_PDE_VLASOV: zero inflow in v, implied;
- * SG_PDE_VLASOV_BOLTZMANN: zero on every axis, implied). */
-enum { SG_BC_PERIODIC = 0 };
+/* Boundary conditions per axis, for SG_PDE_ADVECTION and SG_PDE_BURGERS (the kinetic PDEs imply
+ * theirs: SG_PDE_VLASOV zero inflow in v, SG_PDE_VLASOV_BOLTZMANN zero on every axis; bc is
+ * ignored for them).
+ * SG_BC_PERIODIC: n_k periodic nodes x_j = lo_k + j h_k, j = 0..n_k-1.
+ * SG_BC_ZERO: the same nodes, and u = 0 beyond them -- at x_{-3..-1} and x_{n_k..n_k+2} in the
+ *   WENO5 stencils, at the two nodes beyond either end in the interpolation of Eqs. (8)-(11):
+ *   the zero boundary treatment of Example 5 (Section 3.5) applied to Eq. (1). */
+enum { SG_BC_PERIODIC = 0, SG_BC_ZERO = 1 };
 /* Precision of the component-grid states and the WENO arithmetic.  The combination sum
  * (the finest-grid accumulator) and every reduction are FP64 in both. */
 enum { SG_F64 = 0, SG_F32 = 1 };
@@ -102,7 +107,8 @@ enum { SG_IC_SINE = 0, SG_IC_LANDAU = 1, SG_IC_RELAX = 2 };
 /* Reductions (FP64).  MASS = sum u prod h, ENERGY = sum u^2 prod h, MIN/MAX of the values;
  * L1_EXACT = mean |u - u_exact|, LINF_EXACT = max |u - u_exact| against the exact solution of
  * the SG_IC_SINE initial condition at the current time (advection: translation; Burgers:
- * characteristic solution by Newton's method, valid before the shock time). */
+ * characteristic solution by Newton's method, valid before the shock time; both need periodic
+ * boundaries on every axis, SG_ERR_STATE otherwise). */
 /* FIELD_ENERGY (SG_PDE_VLASOV only): (1/2) sum_i E_i^2 h_x of the field of grid `which` or of
  * the combined solution, E as described for SG_PDE_VLASOV. */
 /* ENTROPY_H2 / ENTROPY_LOG (SG_PDE_VLASOV_BOLTZMANN only): the entropy functionals of
@@ -126,7 +132,7 @@ typedef struct {
     size_t struct_size;          /* sizeof(sg_params), set by sg_params_init */
     double lo[SG_MAX_DIM];       /* domain [lo_k, hi_k] per axis; default [0, 4] */
     double hi[SG_MAX_DIM];
-    int bc[SG_MAX_DIM];          /* SG_BC_PERIODIC */
+    int bc[SG_MAX_DIM];          /* SG_BC_PERIODIC (default) or SG_BC_ZERO, per axis */
     double adv_speed[SG_MAX_DIM];/* a_k for linear advection; default 1 */
     int precision;               /* SG_F64 (default) or SG_F32 */
     int exec;                    /* SG_PLAIN (default) or SG_BATCHED */
@@ -154,8 +160,8 @@ sg_status sg_params_init(sg_params *p);
  * stencil needs five distinct points on every periodic line), level = N_L with
  * 0 <= N_L <= 16 and N_r 2^{N_L} <= 2^20, pde one of SG_PDE_*.  Allocates every component
  * grid's three RK arrays on the device.  *out receives the handle.  Errors: SG_ERR_ARG for
- * out-of-range arguments, SG_ERR_UNSUPPORTED for a non-periodic bc or a component grid of 2^31
- * or more points, SG_ERR_NOMEM, SG_ERR_CUDA. */
+ * out-of-range arguments (a bc other than SG_BC_PERIODIC / SG_BC_ZERO among them),
+ * SG_ERR_UNSUPPORTED for a component grid of 2^31 or more points, SG_ERR_NOMEM, SG_ERR_CUDA. */
 sg_status sg_create(int dim, int root_cells, int level, int pde, const sg_params *params,
                     sg_handle *out);
 
@@ -220,7 +226,7 @@ sg_status sg_time(sg_handle h, double *t, long *steps);
 /* Groups n independent problems (each from sg_create) into one batch: sg_step on the batch
  * advances every member, each with its own time step, with one persistent launch per RK
  * stage over all members' grids; members that reach t_end drop out.  Members must share
- * dim, pde, precision, scheme and eps.  The batch does not own its members: destroy the
+ * dim, pde, precision, scheme, eps, adv_speed and bc.  The batch does not own its members: destroy the
  * batch first, then the members.  sg_read / sg_reduce / sg_init apply to members only. */
 sg_status sg_batch_create(const sg_handle *members, int n, sg_handle *batch);
 

@@ -22,7 +22,7 @@ MAX_DIM = 6
 SG_OK, SG_ERR_ARG, SG_ERR_STATE, SG_ERR_NOMEM, SG_ERR_CUDA = 0, 1, 2, 3, 4
 SG_ERR_NONFINITE, SG_ERR_TIMEOUT, SG_ERR_UNSUPPORTED = 5, 6, 7
 SG_PDE_ADVECTION, SG_PDE_BURGERS, SG_PDE_VLASOV, SG_PDE_VLASOV_BOLTZMANN = 0, 1, 2, 3
-SG_BC_PERIODIC = 0
+SG_BC_PERIODIC, SG_BC_ZERO = 0, 1
 SG_F64, SG_F32 = 0, 1
 SG_PLAIN, SG_BATCHED = 0, 1
 SG_WENO5, SG_LINEAR5 = 0, 1
@@ -137,7 +137,7 @@ def sg_params_init(**overrides) -> sg_params:
             arr = getattr(p, k)
             vals = list(np.broadcast_to(np.asarray(v), (MAX_DIM,))) if np.ndim(v) == 0 else list(v)
             for i, x in enumerate(vals[:MAX_DIM]):
-                arr[i] = x
+                arr[i] = int(x) if k == "bc" else float(x)
         else:
             setattr(p, k, v)
     return p

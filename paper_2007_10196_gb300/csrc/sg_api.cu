@@ -214,6 +214,10 @@ PhysParams phys_of(const sg_ctx* h) {
     for (int k = 0; k < SG_MAXD; ++k) ph.adv[k] = k < h->dim ? h->prm.adv_speed[k] : 0.0;
     ph.alpha_f32 = h->esize == 4;
     ph.tau = h->prm.tau;
+    ph.zmask = 0;
+    if (h->pde == SG_PDE_ADVECTION || h->pde == SG_PDE_BURGERS)
+        for (int k = 0; k < h->dim; ++k)
+            if (h->prm.bc[k] == SG_BC_ZERO) ph.zmask |= 1 << k;
     return ph;
 }
 
@@ -400,8 +404,8 @@ sg_status validate_params(const sg_params* p, int dim) {
     for (int k = 0; k < dim; ++k) {
         if (!(std::isfinite(p->lo[k]) && std::isfinite(p->hi[k]) && p->hi[k] > p->lo[k]))
             return fail(SG_ERR_ARG, "domain axis %d: need finite lo < hi", k);
-        if (p->bc[k] != SG_BC_PERIODIC)
-            return fail(SG_ERR_UNSUPPORTED, "only periodic boundaries are implemented (the kinetic PDEs imply theirs)");
+        if (p->bc[k] != SG_BC_PERIODIC && p->bc[k] != SG_BC_ZERO)
+            return fail(SG_ERR_ARG, "bc[%d] must be SG_BC_PERIODIC or SG_BC_ZERO", k);
         if (!std::isfinite(p->adv_speed[k])) return fail(SG_ERR_ARG, "adv_speed[%d] not finite", k);
     }
     if (p->precision != SG_F64 && p->precision != SG_F32) return fail(SG_ERR_ARG, "precision");
@@ -861,9 +865,10 @@ sg_status run_steps(sg_ctx* h) {
 }
 
 // Axes with zero values beyond the ends: v of the Vlasov-Poisson system, every axis of the
-// Vlasov-Boltzmann model; the others are periodic.
+// Vlasov-Boltzmann model, the SG_BC_ZERO axes of advection and Burgers; the others are periodic.
 bool zero_axis(const sg_ctx* h, int k) {
-    return (h->pde == SG_PDE_VLASOV && k == 1) || h->pde == SG_PDE_VLASOV_BOLTZMANN;
+    return (h->pde == SG_PDE_VLASOV && k == 1) || h->pde == SG_PDE_VLASOV_BOLTZMANN ||
+           ((h->pde == SG_PDE_ADVECTION || h->pde == SG_PDE_BURGERS) && h->prm.bc[k] == SG_BC_ZERO);
 }
 
 // Prolongation of every grid onto the finest grid and the combination sum, one grid at a time:
@@ -1487,6 +1492,8 @@ sg_status sg_reduce(sg_handle h, int which, int kind, double* out) {
     if (which == SG_WHICH_COMBINED) {
         if (!h->combined) return fail(SG_ERR_STATE, "no combined solution: call sg_prolong_combine first");
         if (exact && !h->ic_sine) return fail(SG_ERR_STATE, "exact-solution norms need an SG_IC_SINE initial condition");
+        if (exact && phys_of(h).zmask)
+            return fail(SG_ERR_STATE, "exact-solution norms assume periodic boundaries (an axis has SG_BC_ZERO)");
         n = h->fine_pts;
         for (int k = 0; k < h->dim; ++k) vol = vol * fine_spacing(h, k);
         SG_CUDA(sg::Launch<double>::reduce(h->uhat.as<double>(), nullptr, n, kind, X, h->partial.as<double>(), dres, h->stream));
@@ -1555,8 +1562,10 @@ sg_status sg_batch_create(const sg_handle* hs, int n, sg_handle* out) {
             b->prm.eps != a->prm.eps || b->prm.tile_points != a->prm.tile_points ||
             b->prm.stage_kernel != a->prm.stage_kernel || b->prm.tau != a->prm.tau)
             return fail(SG_ERR_ARG, "member %d differs in dim, pde, precision, scheme, eps, tau or stage kernel", i);
-        for (int k = 0; k < a->dim; ++k)
+        for (int k = 0; k < a->dim; ++k) {
             if (b->prm.adv_speed[k] != a->prm.adv_speed[k]) return fail(SG_ERR_ARG, "member %d differs in adv_speed", i);
+            if (b->prm.bc[k] != a->prm.bc[k]) return fail(SG_ERR_ARG, "member %d differs in bc", i);
+        }
     }
     try {
         sg_ctx* h = new sg_ctx();

@@ -83,6 +83,8 @@ struct PhysParams {
     double adv[SG_MAXD];
     int alpha_f32;           // alpha slots hold float bits (FP32 state)
     double tau;              // Vlasov-Boltzmann: relaxation time of (mu rho - f) / tau
+    int zmask;               // advection / Burgers: bit k set = u is 0 beyond the ends of axis k
+                             // (zero boundary), else periodic; the kinetic PDEs imply theirs
 };
 
 struct StageArgs {

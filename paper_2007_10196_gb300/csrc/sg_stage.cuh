@@ -205,7 +205,8 @@ __device__ __forceinline__ void stage_epilogue_warp(const StageArgs& A, const Wo
 
 // ------------------------------------------------------------------------------------
 // d <= 3: padded-box kernel.  Per tile: one load of the tile with a 3-point halo on each face
-// (periodic wrap), the LF split computed once per loaded value (Burgers: the split is the
+// (periodic wrap, or zeros beyond the ends of a zero-boundary axis), the LF split computed once
+// per loaded value (Burgers: the split is the
 // same on every axis); one phase computing every interface flux of every axis once; one
 // phase forming L = -sum_k (F_{i+1/2} - F_{i-1/2}) / h_k and the stage update.
 // Shared memory: two box arrays of box_elems values (f^+, f^-; or u and unused) and the
@@ -227,8 +228,9 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
     const PhysParams& ph = A.phys;
     const bool burgers = ph.pde == 1;
     const bool vlasov = ph.pde == 2;  // d = 2: axis 0 = x (speed v_j), axis 1 = v (speed E_i, 0 beyond the ends)
-    const T eps12 = (T)(12.0 * ph.eps);
+    const T eps4 = sg_eps4<T>(ph.eps);
     const T adv0 = (T)ph.adv[0], adv1 = (T)ph.adv[1], adv2 = (T)ph.adv[2];
+    const int zm = ph.zmask;  // zero boundary per axis (advection / Burgers)
 
     for (int it = A.item_begin + blockIdx.x; it < A.item_end; it += gridDim.x) {
         const WorkItem w = A.items[it];
@@ -283,6 +285,10 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
                 bp[bidx] = v;
             }
         };
+        auto put0 = [&](int bidx) {  // a zero boundary value (its split values are 0 too)
+            bp[bidx] = T(0);
+            if (burgers) bm[bidx] = T(0);
+        };
         {
             const int n0 = B0 * e[1] * e[2];  // interior rows extended by the axis-0 halos
             for (int q = tid; q < n0; q += SG_NT) {
@@ -294,10 +300,15 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
                     y = r - z * e[1];
                 }
                 int gx = org[0] + x - 3;
+                const int bidx = x + B0 * ((y + (D >= 2 ? 3 : 0)) + B1 * (z + (D >= 3 ? 3 : 0)));
+                if ((zm & 1) && (gx < 0 || gx >= n[0])) {
+                    put0(bidx);
+                    continue;
+                }
                 if (gx < 0) gx += n[0];
                 else if (gx >= n[0]) gx -= n[0];
                 const long long g = gx + gs[1] * (org[1] + y) + gs[2] * (org[2] + z);
-                put(x + B0 * ((y + (D >= 2 ? 3 : 0)) + B1 * (z + (D >= 3 ? 3 : 0))), g);
+                put(bidx, g);
             }
             if (D >= 2) {
                 const int n1 = e[0] * 6 * e[2];  // axis-1 halos
@@ -308,8 +319,8 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
                     const int y = h < 3 ? h - 3 : e[1] + h - 3;
                     int gy = org[1] + y;
                     const int bidx = (x + 3) + B0 * ((y + 3) + B1 * (z + (D >= 3 ? 3 : 0)));
-                    if (vlasov && (gy < 0 || gy >= n[1])) {  // zero inflow in v
-                        bp[bidx] = T(0);
+                    if ((vlasov || (zm & 2)) && (gy < 0 || gy >= n[1])) {  // zero inflow in v / zero boundary
+                        put0(bidx);
                         continue;
                     }
                     if (gy < 0) gy += n[1];
@@ -327,10 +338,15 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
                     const int y = r - h * e[1];
                     const int z = h < 3 ? h - 3 : e[2] + h - 3;
                     int gz = org[2] + z;
+                    const int bidx = (x + 3) + B0 * ((y + 3) + B1 * (z + 3));
+                    if ((zm & 4) && (gz < 0 || gz >= n[2])) {
+                        put0(bidx);
+                        continue;
+                    }
                     if (gz < 0) gz += n[2];
                     else if (gz >= n[2]) gz -= n[2];
                     const long long g = (org[0] + x) + gs[1] * (org[1] + y) + gs[2] * gz;
-                    put((x + 3) + B0 * ((y + 3) + B1 * (z + 3)), g);
+                    put(bidx, g);
                 }
             }
         }
@@ -394,9 +410,9 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
                 }
             } else {
                 if (burgers) {
-                    F = Weno<float>::interface_split((const float*)bp + b, (const float*)bm + b, Sx, eps12, ph.scheme);
+                    F = Weno<float>::interface_split((const float*)bp + b, (const float*)bm + b, Sx, eps4, ph.scheme);
                 } else {
-                    F = Weno<float>::interface((const float*)bp + b, Sx, (float)al, (float)ak, ph, eps12);
+                    F = Weno<float>::interface((const float*)bp + b, Sx, (float)al, (float)ak, ph, eps4);
                 }
             }
             fb[q] = F;
@@ -443,7 +459,8 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
 
 // ------------------------------------------------------------------------------------
 // d = 3: line-sweep kernel.  Per tile (extents <= 8 on every axis, so at most 8^3 points and
-// 3 * 64 = 192 lines): one load of the padded box (as above, x stride made odd so that threads
+// 3 * 64 = 192 lines): one load of the padded box (as above, periodic or zero beyond the ends of
+// a zero-boundary axis; x stride made odd so that threads
 // on neighbouring x-lines hit different banks); then every thread takes one line of one axis
 // and sweeps it, keeping the five-point windows of f^+ and f^- in registers, so each new
 // interface costs one shared-memory load per side; the flux difference of each point goes to
@@ -454,7 +471,7 @@ __global__ void __launch_bounds__(SG_NT) sg_stage_box_kernel(const StageArgs A) 
 // in a value at the far end (the positive-wind stencil f_{i-2..i+2}); push_front at the near
 // end (the mirrored negative-wind stencil f_{i+3..i-1}).
 //   double: keeps the raw window and evaluates Eqs. (3)-(6) literally per interface.
-//   float: keeps first differences d1..d4 and T_j = 13 t_j^2 + 12 eps (t = second differences)
+//   float: keeps first differences d1..d4 and T_j = (13/3) t_j^2 + 4 eps (t = second differences)
 //     and updates them incrementally, so consecutive interfaces share them.
 // ------------------------------------------------------------------------------------
 template <class T>
@@ -478,33 +495,33 @@ template <>
 struct SweepSide<float> {
     float w0, w1, c, w3, w4;    // the window (c = centre); shifted, never recomputed
     float d1, d2, d3, d4;       // first differences: the same values a fresh window would give
-    float T0, T1, T2;           // 13 t^2 + 12 eps of the three second differences
-    __device__ __forceinline__ void init(float a, float b, float cc, float d, float e, float eps12) {
+    float T0, T1, T2;           // (13/3) t^2 + 4 eps of the three second differences
+    __device__ __forceinline__ void init(float a, float b, float cc, float d, float e, float eps4) {
         w0 = a; w1 = b; c = cc; w3 = d; w4 = e;
         d1 = b - a; d2 = cc - b; d3 = d - cc; d4 = e - d;
         const float t0 = d2 - d1, t1 = d3 - d2, t2 = d4 - d3;
-        T0 = fmaf(13.f * t0, t0, eps12);
-        T1 = fmaf(13.f * t1, t1, eps12);
-        T2 = fmaf(13.f * t2, t2, eps12);
+        T0 = fmaf((13.f / 3.f) * t0, t0, eps4);
+        T1 = fmaf((13.f / 3.f) * t1, t1, eps4);
+        T2 = fmaf((13.f / 3.f) * t2, t2, eps4);
     }
-    __device__ __forceinline__ void push_back(float v, float eps12) {
+    __device__ __forceinline__ void push_back(float v, float eps4) {
         w0 = w1; w1 = c; c = w3; w3 = w4;
         d1 = d2; d2 = d3; d3 = d4; d4 = v - w4;
         w4 = v;
         T0 = T1; T1 = T2;
         const float t2 = d4 - d3;
-        T2 = fmaf(13.f * t2, t2, eps12);
+        T2 = fmaf((13.f / 3.f) * t2, t2, eps4);
     }
-    __device__ __forceinline__ void push_front(float v, float eps12) {
+    __device__ __forceinline__ void push_front(float v, float eps4) {
         w4 = w3; w3 = c; c = w1; w1 = w0;
         d4 = d3; d3 = d2; d2 = d1; d1 = w0 - v;
         w0 = v;
         T2 = T1; T1 = T0;
         const float t0 = d2 - d1;
-        T0 = fmaf(13.f * t0, t0, eps12);
+        T0 = fmaf((13.f / 3.f) * t0, t0, eps4);
     }
     // numerator and denominator of fhat - c (as in Weno<float>::side)
-    // With E_k = (12 eps + 12 beta_k)^2, the weights are proportional to
+    // With E_k = e_k^2, e_k = 4 (eps + beta_k) rescaled by weno_scale3, the weights are proportional to
     // a_0 = E_1 E_2 / 6, a_1 = E_0 E_2, a_2 = E_0 E_1 / 2 (linear scheme: all E_k = 1, giving
     // 0.1, 0.6, 0.3), and num = sum a_k p_k, den = sum a_k are formed factored:
     // num = E_1 (E_2 p_0/6 + E_0 p_2/2) + E_0 E_2 p_1,  den = E_1 (E_2/6 + E_0/2) + E_0 E_2.
@@ -515,9 +532,10 @@ struct SweepSide<float> {
         float E0 = 1.f, E1 = 1.f, E2 = 1.f;
         if (!linear) {
             const float s0 = fmaf(3.f, d2, -d1), s1 = d2 + d3, s2 = fmaf(3.f, d3, -d4);
-            const float e0 = fmaf(3.f * s0, s0, T0);
-            const float e1 = fmaf(3.f * s1, s1, T1);
-            const float e2 = fmaf(3.f * s2, s2, T2);
+            float e0 = fmaf(s0, s0, T0);
+            float e1 = fmaf(s1, s1, T1);
+            float e2 = fmaf(s2, s2, T2);
+            weno_scale3(e0, e1, e2);  // ratios only: smallest in [1, 2), others capped at 2^20
             E0 = e0 * e0;
             E1 = e1 * e1;
             E2 = e2 * e2;
@@ -559,8 +577,9 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
     const int tid = threadIdx.x;
     const PhysParams& ph = A.phys;
     const bool burgers = ph.pde == 1;
-    const T eps12 = (T)(12.0 * ph.eps);
+    const T eps4 = sg_eps4<T>(ph.eps);
     const T adv[3] = {(T)ph.adv[0], (T)ph.adv[1], (T)ph.adv[2]};
+    const int zm = ph.zmask;  // zero boundary per axis (advection / Burgers)
 
     for (int it = A.item_begin + blockIdx.x; it < A.item_end; it += gridDim.x) {
         const WorkItem w = A.items[it];
@@ -632,8 +651,10 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
             if (vec) {
                 const int nr0 = e[1] * e[2] * 4, nr1 = 12 * e[2], nr2 = 12 * e[1];
                 const int ntask = nr0 + nr1 + nr2;
-                // task t: one float4 chunk; its box index with two flags (drop the chunk's first
-                // value: x = -4; drop its last: x = 11) packed above bit 16
+                // task t: one float4 chunk; its box index with three flags (drop the chunk's first
+                // value: x = -4; drop its last: x = 11; the chunk lies beyond the end of a
+                // zero-boundary axis: all four values are 0) packed above bit 16.  Chunks never
+                // straddle an end (x origins and row lengths are multiples of 4).
                 auto chunk = [&](int t, long long& g) -> int {
                     int gx, gy, gz, bx, y, z, flags = 0;
                     if (t < nr0) {
@@ -643,6 +664,7 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
                         bx = 4 * c - 1;  // box x of the chunk's first value (x = 4c - 4)
                         flags = (c == 0 ? 1 : 0) | (c == 3 ? 2 : 0);
                         gx = org[0] + 4 * c - 4;
+                        if ((zm & 1) && (gx < 0 || gx >= n[0])) flags |= 4;
                         gx = gx < 0 ? gx + n[0] : (gx >= n[0] ? gx - n[0] : gx);
                         gy = org[1] + y;
                         gz = org[2] + z;
@@ -654,6 +676,7 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
                         bx = 4 * c + 3;
                         gx = org[0] + 4 * c;
                         gy = org[1] + y;
+                        if ((zm & 2) && (gy < 0 || gy >= n[1])) flags |= 4;
                         gy = gy < 0 ? gy + n[1] : (gy >= n[1] ? gy - n[1] : gy);
                         gz = org[2] + z;
                     } else {
@@ -665,12 +688,14 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
                         gx = org[0] + 4 * c;
                         gy = org[1] + y;
                         gz = org[2] + z;
+                        if ((zm & 4) && (gz < 0 || gz >= n[2])) flags |= 4;
                         gz = gz < 0 ? gz + n[2] : (gz >= n[2] ? gz - n[2] : gz);
                     }
                     g = (gx - org[0]) + n0 * (gy - org[1]) + n01 * (gz - org[2]);
                     return (bx + 1 + B0 * ((y + 3) + B1 * (z + 3))) | (flags << 16);  // +1: >= 0
                 };
-                auto fetch = [&](long long g) {
+                auto fetch = [&](int code, long long g) {
+                    if (code & (4 << 16)) return make_float4(0.f, 0.f, 0.f, 0.f);  // zero boundary
                     float4 v = *reinterpret_cast<const float4*>(A0 + g);
                     if (A1) {
                         const float4 d = *reinterpret_cast<const float4*>(A1 + g);
@@ -695,15 +720,15 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
                     const int c0 = t0 < ntask ? chunk(t0, g0) : -1;
                     const int c1 = t1 < ntask ? chunk(t1, g1) : -1;
                     float4 v0, v1;
-                    if (c0 >= 0) v0 = fetch(g0);
-                    if (c1 >= 0) v1 = fetch(g1);
+                    if (c0 >= 0) v0 = fetch(c0, g0);
+                    if (c1 >= 0) v1 = fetch(c1, g1);
                     if (c0 >= 0) store(c0, v0);
                     if (c1 >= 0) store(c1, v1);
                 }
                 for (int t = tid + 2 * SG_NT3; t < ntask; t += SG_NT3) {
                     long long g;
                     const int c = chunk(t, g);
-                    store(c, fetch(g));
+                    store(c, fetch(c, g));
                 }
             }
         }
@@ -721,10 +746,11 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
                     const int r = (int)fR0.div(q), x = q - r * R0;
                     const int z = (int)fe1.div(r), y = r - z * e[1];
                     int gx = org[0] + x - 3;
+                    const bool zb = (zm & 1) && (gx < 0 || gx >= n[0]);  // zero boundary value
                     if (gx < 0) gx += n[0];
                     else if (gx >= n[0]) gx -= n[0];
                     bid[j] = x + B0 * ((y + 3) + B1 * (z + 3));
-                    val[j] = io.load((gx - org[0]) + n0 * y + n01 * z);
+                    val[j] = zb ? T(0) : io.load((gx - org[0]) + n0 * y + n01 * z);
                 }
             }
             const int n1 = e[0] * 6 * e[2];
@@ -737,10 +763,11 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
                     const int z = r / 6, h = r - z * 6;
                     const int y = h < 3 ? h - 3 : e[1] + h - 3;
                     int gy = org[1] + y;
+                    const bool zb = (zm & 2) && (gy < 0 || gy >= n[1]);
                     if (gy < 0) gy += n[1];
                     else if (gy >= n[1]) gy -= n[1];
                     bid[M0 + j] = (x + 3) + B0 * ((y + 3) + B1 * (z + 3));
-                    val[M0 + j] = io.load(x + n0 * (gy - org[1]) + n01 * z);
+                    val[M0 + j] = zb ? T(0) : io.load(x + n0 * (gy - org[1]) + n01 * z);
                 }
             }
             const int n2 = e[0] * e[1] * 6;
@@ -753,10 +780,11 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
                     const int h = (int)fe1.div(r), y = r - h * e[1];
                     const int z = h < 3 ? h - 3 : e[2] + h - 3;
                     int gz = org[2] + z;
+                    const bool zb = (zm & 4) && (gz < 0 || gz >= n[2]);
                     if (gz < 0) gz += n[2];
                     else if (gz >= n[2]) gz -= n[2];
                     bid[M0 + M1 + j] = (x + 3) + B0 * ((y + 3) + B1 * (z + 3));
-                    val[M0 + M1 + j] = io.load(x + n0 * y + n01 * (gz - org[2]));
+                    val[M0 + M1 + j] = zb ? T(0) : io.load(x + n0 * y + n01 * (gz - org[2]));
                 }
             }
 #pragma unroll
@@ -815,16 +843,16 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
             };
             SweepSide<T> Pw, Mw;
             // interface 0 (between local points -1 and 0): f^+ at box 0..4, f^- mirrored at box 5..1
-            Pw.init(fplus(0), fplus(1), fplus(2), fplus(3), fplus(4), eps12);
-            Mw.init(fminus(5), fminus(4), fminus(3), fminus(2), fminus(1), eps12);
+            Pw.init(fplus(0), fplus(1), fplus(2), fplus(3), fplus(4), eps4);
+            Mw.init(fminus(5), fminus(4), fminus(3), fminus(2), fminus(1), eps4);
             T* D = Dk + k * SG_DK_AXIS + 9 * line;
             T Fprev = sweep_flux(Pw, Mw, ph);
             // ek <= 8: fully unrolled, so the window shifts are register renames, not moves
 #pragma unroll
             for (int i = 1; i <= 8; ++i) {
                 if (i > ek) break;
-                Pw.push_back(fplus(i + 4), eps12);
-                Mw.push_front(fminus(i + 5), eps12);
+                Pw.push_back(fplus(i + 4), eps4);
+                Mw.push_front(fminus(i + 5), eps4);
                 const T F = sweep_flux(Pw, Mw, ph);
                 D[i - 1] = (F - Fprev) * rdx;
                 Fprev = F;

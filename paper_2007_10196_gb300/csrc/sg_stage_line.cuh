@@ -13,7 +13,9 @@
 // subtracts (F_{i+1/2} - F_{i-1/2}) / h_k from the point's
 // accumulator in shared memory: L = ((0 - D_0) - D_1) - ..., the operation order of the FP64
 // definition.  Finally each point takes the RK stage update.
-// Vlasov-Boltzmann (pde 3, d = 2 d_x): halos beyond the ends are 0; the flux along space axis
+// Zero boundary (advection / Burgers, bit k of zmask; every axis of the Vlasov-Boltzmann model):
+// halo values beyond the ends of axis k are 0.
+// Vlasov-Boltzmann (pde 3, d = 2 d_x): the flux along space axis
 // k is v_k u and along velocity axis k is -x_k u, v_k (x_k) the line's node on the partner
 // axis; the LF alpha of an axis is the largest |partner node| of the grid; after the flux
 // differences each point adds (mu(v) rho(x) - u) / tau (rho from G->ef, mu from G->mu).
@@ -30,7 +32,7 @@ __global__ void __launch_bounds__(SG_NT, sizeof(T) == 4 ? 4 : 1) sg_stage_line_k
 
     const int tid = threadIdx.x;
     const PhysParams& ph = A.phys;
-    const T eps12 = (T)(12.0 * ph.eps);
+    const T eps4 = sg_eps4<T>(ph.eps);
     const bool burgers = ph.pde == 1;
     const bool vb = ph.pde == 3;
     constexpr int DX = D / 2;  // Vlasov-Boltzmann: space axes 0..DX-1, velocity axes DX..D-1
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(SG_NT, sizeof(T) == 4 ? 4 : 1) sg_stage_line_k
                     }
                     dst[u] = line * ls + i;
                     int ck = ok + i - 3;
-                    if (vb && (ck < 0 || ck >= nk)) {  // zero boundary values
+                    if ((vb || ((ph.zmask >> k) & 1)) && (ck < 0 || ck >= nk)) {  // zero boundary values
                         kind[u] = 2;
                         continue;
                     }
@@ -231,14 +233,14 @@ __global__ void __launch_bounds__(SG_NT, sizeof(T) == 4 ? 4 : 1) sg_stage_line_k
                 SweepSide<T> Pw, Mw;
                 // interface between local points i0-1 and i0 (buffer index = local + 3): f^+ at
                 // buffer i0..i0+4, f^- mirrored at i0+5..i0+1
-                Pw.init(fplus(i0), fplus(i0 + 1), fplus(i0 + 2), fplus(i0 + 3), fplus(i0 + 4), eps12);
-                Mw.init(fminus(i0 + 5), fminus(i0 + 4), fminus(i0 + 3), fminus(i0 + 2), fminus(i0 + 1), eps12);
+                Pw.init(fplus(i0), fplus(i0 + 1), fplus(i0 + 2), fplus(i0 + 3), fplus(i0 + 4), eps4);
+                Mw.init(fminus(i0 + 5), fminus(i0 + 4), fminus(i0 + 3), fminus(i0 + 2), fminus(i0 + 1), eps4);
                 T Fprev = sweep_flux(Pw, Mw, ph);
                 T* a = accs + pb + i0 * tk;
 #pragma unroll 2
                 for (int i = i0 + 1; i <= i1; ++i) {
-                    Pw.push_back(fplus(i + 4), eps12);
-                    Mw.push_front(fminus(i + 5), eps12);
+                    Pw.push_back(fplus(i + 4), eps4);
+                    Mw.push_front(fminus(i + 5), eps4);
                     const T F = sweep_flux(Pw, Mw, ph);
                     const T Dv = (F - Fprev) * rdx;
                     *a = (k == 0 ? T(0) : *a) - Dv;

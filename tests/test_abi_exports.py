@@ -72,8 +72,8 @@ def test_argument_errors_without_gpu(built):
         P.sg_create(2, 4, 3, P.SG_PDE_ADVECTION)
     assert e.value.status == P.SG_ERR_ARG
     with pytest.raises(P.SgError) as e:
-        P.sg_create(2, 10, 3, P.SG_PDE_ADVECTION, P.sg_params_init(bc=[1] * 6))
-    assert e.value.status == P.SG_ERR_UNSUPPORTED
+        P.sg_create(2, 10, 3, P.SG_PDE_ADVECTION, P.sg_params_init(bc=[2] * 6))
+    assert e.value.status == P.SG_ERR_ARG and "bc" in P.sg_last_error()
     with pytest.raises(P.SgError) as e:
         P.sg_create(2, 10, 3, P.SG_PDE_ADVECTION, P.sg_params_init(eps=0.0))
     assert e.value.status == P.SG_ERR_ARG
