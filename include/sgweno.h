@@ -287,8 +287,9 @@ sg_status sg_stage_config(sg_handle h, int *kernel, int *tile_points, double *tu
  *   SG_NOALLOC_MAX_POINTS (SG_ERR_ARG otherwise, with a message in sg_last_error);
  *   lo, hi: the domain (node spacing (hi_k - lo_k)/shape[k]); pde, scheme, eps as in
  *   sg_create / sg_params; adv_speed: a_k for advection (NULL = all 1);
- *   u_in, u_out: device pointers to prod shape[k] doubles, axis 0 fastest (they may be the
- *   same pointer); dt: the step; cuda_stream: the cudaStream_t to run on (NULL = default).
+ *   u_in, u_out: device pointers to prod shape[k] doubles, axis 0 fastest: the same pointer
+ *   (stepped in place) or two arrays that do not overlap (SG_ERR_ARG if they overlap otherwise);
+ *   dt: the step; cuda_stream: the cudaStream_t to run on (NULL = default).
  * The call is asynchronous on that stream and calls no cudaMalloc, cudaFree or allocating
  * library routine.  The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any stream

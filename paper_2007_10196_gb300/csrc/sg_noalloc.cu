@@ -11,6 +11,7 @@
 //
 // Compiled with --fmad=false, like the FP64 kernels, so that the result equals sg_step's bit
 // for bit: the same stage kernel runs, on the same tiles.
+#include <cstdint>
 #include <algorithm>
 #include <cstdio>
 #include <mutex>
@@ -160,6 +161,12 @@ extern "C" sg_status sg_step_grid_noalloc(int dim, const long* shape, const doub
         n[k] = (int)shape[k];
         npts *= shape[k];
         if (npts > SG_NOALLOC_MAX_POINTS) return na_fail(SG_ERR_ARG, "grid exceeds SG_NOALLOC_MAX_POINTS points");
+    }
+    {  // u_in and u_out: the same array, or two that do not overlap
+        const uintptr_t a = reinterpret_cast<uintptr_t>(u_in), b = reinterpret_cast<uintptr_t>(u_out);
+        const uintptr_t len = sizeof(double) * (uintptr_t)npts;
+        if (a != b && a < b + len && b < a + len)
+            return na_fail(SG_ERR_ARG, "u_in and u_out overlap without being the same array");
     }
     char* base = nullptr;
     sg_status st = na_setup(&base);

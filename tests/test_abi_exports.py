@@ -109,3 +109,16 @@ def test_workload_inputs_are_seeded():
     f1 = inputs.random_field(3, (5, 7), "mixed")
     f2 = inputs.random_field(3, (5, 7), "mixed")
     assert (f1 == f2).all() and f1.shape == (35,)
+
+
+def test_noalloc_rejects_partly_overlapping_buffers_without_gpu(built):
+    """The no-allocation step takes u_in and u_out as one array or two disjoint ones; a partial
+    overlap is refused before any CUDA call (addresses are only compared, never touched)."""
+    import paper_2007_10196_gb300 as P
+    base = 1 << 20
+    with pytest.raises(P.SgError) as e:
+        P.sg_step_grid_noalloc((8, 8), 0.0, 1.0, P.SG_PDE_ADVECTION, base, base + 8 * 10, 1e-3)
+    assert e.value.status == P.SG_ERR_ARG and "overlap" in P.sg_last_error()
+    with pytest.raises(P.SgError) as e:
+        P.sg_step_grid_noalloc((8, 8), 0.0, 1.0, P.SG_PDE_ADVECTION, base + 8 * 63, base, 1e-3)
+    assert e.value.status == P.SG_ERR_ARG and "overlap" in P.sg_last_error()
