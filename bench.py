@@ -233,25 +233,30 @@ def _stage_traffic(kernel, points_per_launch):
 def kernel_name(P, h):
     kern, tp, _ = P.sg_stage_config(h)
     if kern == P.SG_STAGE_SWEEP:
-        return "sg_stage_sweep3_kernel<float>"
+        return "sg_stage_sweep3_kernel<float, false>"
     return "sg_stage_box_kernel<float,3,%d>" % (tp // 256)
 
 
-def compare_fp64_plain(P, stream, members, nmax=4):
+def compare_fp64_plain(P, stream, members, nmax=4, nshock=2):
     """The plain FP64 path (one launch per grid per RK stage) against the batched FP32 path on
-    the same members: stepping rates to t_end, and the L1 error of the combined solution
-    against the exact (characteristic) solution for both, on members still smooth at t_end."""
+    the same members: stepping rates to t_end, and accuracy.  Members still smooth at t_end: the
+    L1 error of the combined solution against the exact (characteristic) solution for both.
+    Members past their shock (no exact solution): the FP32 combined solution against the FP64
+    one (identical to the oracle's, bit for bit), max and mean difference."""
     import torch
     sel = [m for m in members if m.a < A_SMOOTH_AT_T_END][:nmax]
+    # the smallest shocked members (a full FP64 read of each combined solution)
+    shk = sorted([m for m in members if m.a >= A_SMOOTH_AT_T_END], key=lambda m: m.nr << m.nl)[:nshock]
     if not sel:
         return None
-    ics = [(0.5, m.a, math.pi / 2, 0.0) for m in sel]
-    pts = [n for _, n in _batch_points(sel)]
+    run = sel + shk
+    ics = [(0.5, m.a, math.pi / 2, 0.0) for m in run]
+    pts = [n for _, n in _batch_points(run)]
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     res = {}
     for prec, exe in ((P.SG_F64, P.SG_PLAIN), (P.SG_F32, P.SG_BATCHED)):
         hs = [P.create(3, m.nr, m.nl, P.SG_PDE_BURGERS, precision=prec, exec=exe, dt_rule=P.SG_DT_CFL,
-                       cfl=inputs.BATCH_CFL, cuda_stream=stream.cuda_stream) for m in sel]
+                       cfl=inputs.BATCH_CFL, cuda_stream=stream.cuda_stream) for m in run]
         b = P.sg_batch_create(hs) if exe == P.SG_BATCHED else None
         try:
             ms = 0.0
@@ -268,25 +273,91 @@ def compare_fp64_plain(P, stream, members, nmax=4):
                 ev1.synchronize()
                 ms = ev0.elapsed_time(ev1)
             upd = sum(P.sg_time(h)[1] * n for h, n in zip(hs, pts))
-            l1 = []
-            for h in hs:
+            l1, uh = [], []
+            for h, m in zip(hs, run):
                 P.sg_prolong_combine(h)
-                l1.append(P.sg_reduce(h, -1, P.SG_REDUCE_L1_EXACT))
-            res[prec] = (upd / (ms / 1e3), l1, ms)
+                if len(l1) < len(sel):
+                    l1.append(P.sg_reduce(h, -1, P.SG_REDUCE_L1_EXACT))
+                else:
+                    uh.append(P.sg_read(h, -1, count=(m.nr << m.nl) ** 3))
+            res[prec] = (upd / (ms / 1e3), l1, ms, uh)
         finally:
             if b is not None:
                 P.sg_destroy(b)
             for h in hs:
                 P.sg_destroy(h)
-    r64, l64, ms64 = res[P.SG_F64]
-    r32, l32, ms32 = res[P.SG_F32]
+    r64, l64, ms64, u64 = res[P.SG_F64]
+    r32, l32, ms32, u32 = res[P.SG_F32]
+    shocked = [{"member": (m.nr, m.nl, round(m.a, 4)), "max_abs_diff": float(np.max(np.abs(a - b))),
+                "mean_abs_diff": float(np.mean(np.abs(a - b))), "range_fp64": [float(b.min()), float(b.max())]}
+               for m, a, b in zip(shk, u32, u64)]
     return {"fp64_plain_value": r64, "fp32_batched_value": r32, "unit": UNIT, "speedup": r32 / r64,
             "fp64_plain_hbm_gbs": r64 * BYTES_PER_POINT_STEP_F64 / 1e9,
             "fp64_plain_ms": ms64, "fp32_batched_ms": ms32,
             "members": [(m.nr, m.nl, round(m.a, 4)) for m in sel],
             "l1_exact_fp64": l64, "l1_exact_fp32": l32,
             "l1_ratio_fp32_over_fp64_max": max(a / b for a, b in zip(l32, l64)),
-            "note": "same members, both stepped to t_end and combined; L1 against the exact solution"}
+            "shocked_fp32_vs_fp64": shocked,
+            "note": "rates over smooth and shocked members together, both stepped to t_end and combined; "
+                    "L1 against the exact solution on the smooth members"}
+
+
+def fp64_plain_configs(P, stream, c3_steps=64):
+    """The plain FP64 path and the batched FP32 path on the 2-D advection configuration
+    (adv2d_nr10_nl4: full run to t = 1, L1 against the exact translate) and on the 3-D one
+    (adv3d_nr8_nl6, finest 512^3: a fixed number of steps, rates only): point-updates/s and the
+    FP64 path's algorithmic HBM bytes per second (64 B per point-step)."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    peaks, _ = _peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    out = {}
+    for name, nsteps in (("adv2d_nr10_nl4", None), ("adv3d_nr8_nl6", c3_steps)):
+        w = inputs.WORKLOADS[name]
+        row = {}
+        for prec, exe in ((P.SG_F64, P.SG_PLAIN), (P.SG_F32, P.SG_BATCHED)):
+            h = P.create(w.dim, w.nr, w.nl, w.pde, precision=prec, exec=exe, dt_rule=w.dt_rule,
+                         dt_coef=w.dt_coef, lo=w.lo, hi=w.hi, cuda_stream=stream.cuda_stream)
+            try:
+                G = P.sg_num_grids(h)
+                pts = sum(int(np.prod(P.sg_grid_info(h, g, w.dim)[1])) for g in range(G))
+                ms = 0.0
+                for rep in range(2):  # the first pass autotunes and warms up
+                    P.sg_init(h, P.SG_IC_SINE, w.ic)
+                    ev0.record(stream)
+                    P.sg_step(h, w.t_end, nsteps if nsteps else (1 << 62))
+                    ev1.record(stream)
+                    ev1.synchronize()
+                    ms = ev0.elapsed_time(ev1)
+                steps = P.sg_time(h)[1]
+                rate = steps * pts / (ms / 1e3)
+                r = {"value": rate, "ms": ms, "steps": steps, "points": pts}
+                if prec == P.SG_F64:
+                    gbs = rate * BYTES_PER_POINT_STEP_F64 / 1e9
+                    r.update({"hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak})
+                if nsteps is None:
+                    P.sg_prolong_combine(h)
+                    r["l1_exact"] = P.sg_reduce(h, -1, P.SG_REDUCE_L1_EXACT)
+                row["fp64_plain" if prec == P.SG_F64 else "fp32_batched"] = r
+            finally:
+                P.sg_destroy(h)
+        row["speedup"] = row["fp32_batched"]["value"] / row["fp64_plain"]["value"]
+        out[name] = row
+    return out
+
+
+def oracle_single_thread(members, every=8):
+    """The oracle on one host thread, in this process: every `every`-th member's first time step
+    (a bounded, representative sample of the batch); (point-updates/s, sample description)."""
+    import oracle
+    oracle.build()
+    upd, wall = 0, 0.0
+    sample = members[::every]
+    for m in sample:
+        u, w = _oracle_member((m.nr, m.nl, m.a, 1))
+        upd += u
+        wall += w
+    return upd / wall, "%d members (every %dth), first time step each, one thread" % (len(sample), every), wall
 
 
 def aggregate(local_ms, local_updates, dist=None, device="cpu"):
@@ -428,10 +499,11 @@ def run_ours(args, rank, world, local_rank):
     kname = kernel_name(P, batch)
     for h in [batch] + hs:
         P.sg_destroy(h)
-    compare = None
+    compare = plain_cfg = None
     if rank == 0 and not args.no_compare:  # untimed: after the timed region and the e2e pass
         with torch.cuda.stream(stream):
             compare = compare_fp64_plain(P, stream, members)
+            plain_cfg = fp64_plain_configs(P, stream)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -450,9 +522,11 @@ def run_ours(args, rank, world, local_rank):
     if pool is not None:
         upd_c, wall_c = oracle_sample(members, pool, cores, nsteps=1)
         pool.close()
+        v1, s1, w1 = oracle_single_thread(members)
         cpu = {"value": upd_c / wall_c, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "all %d members, first time step each (FP64 C oracle, one process per core)" % len(members),
-               "seconds": wall_c, "cpu_model": _cpu_model()}
+               "seconds": wall_c, "cpu_model": _cpu_model(),
+               "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": s1, "seconds": w1}}
     line = {
         "metric": METRIC, "value": total_upd / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
@@ -476,6 +550,7 @@ def run_ours(args, rank, world, local_rank):
         "stepping_rate": upd_per_pass / (statistics.mean(step_ms) / 1e3),
         "bound_overshoot": over,
         "fp64_plain_vs_fp32_batched": compare,
+        "fp64_plain_configs": plain_cfg,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
