@@ -88,7 +88,7 @@ struct DevBuf {
 
 // Intermediates of the fused prolongation + combination.
 struct CombineBuffers {
-    DevBuf pool, pa, pb, tab;
+    DevBuf pool, pa, tab;  // phase-1 pool, phase-1 intermediates, grid and task tables
 };
 
 struct PinnedInst {
@@ -875,7 +875,7 @@ bool zero_axis(const sg_ctx* h, int k) {
 // the last prolonged axis of each grid adds c_g times its values into uhat (a read-modify-write
 // of uhat per grid).  Used when the fused form's intermediates exceed the memory budget.
 template <class T>
-sg_status prolong_combine_rmw_t(sg_ctx* h) {
+sg_status prolong_combine_rmw_t(sg_ctx* h, cudaStream_t st, bool sync) {
     const int d = h->dim;
     const long long Nf = (long long)h->nr << h->nl;
     // intermediate buffers: largest array produced by a non-final prolonged axis
@@ -900,7 +900,7 @@ sg_status prolong_combine_rmw_t(sg_ctx* h) {
         SG_TRY(h->pro_b.alloc(sizeof(T) * (size_t)need));
     }
     double* acc = h->uhat.as<double>();
-    SG_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)h->fine_pts, h->stream));
+    SG_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)h->fine_pts, st));
     for (int g = 0; g < h->G; ++g) {
         const GridDesc& gd = h->hgrids[g];
         long long m[SG_MAXD];
@@ -911,7 +911,7 @@ sg_status prolong_combine_rmw_t(sg_ctx* h) {
         }
         const T* src = (const T*)gd.u0;
         if (axes.empty()) {
-            SG_CUDA(sg::Launch<T>::accumulate(src, acc, gd.coeff, gd.npts, h->stream));
+            SG_CUDA(sg::Launch<T>::accumulate(src, acc, gd.coeff, gd.npts, st));
             h->launches += 1;
             continue;
         }
@@ -926,88 +926,185 @@ sg_status prolong_combine_rmw_t(sg_ctx* h) {
             T* dst = last ? nullptr : bufs[a & 1];
             SG_CUDA(sg::Launch<T>::prolong_axis(src, dst, last ? acc : nullptr, gd.coeff, below, (int)m[k],
                                                 (int)Nf, above, r, h->prm.eps, h->prm.prolong,
-                                                zero_axis(h, k) ? 1 : 0, h->stream));
+                                                zero_axis(h, k) ? 1 : 0, st));
             h->launches += 1;
             m[k] = Nf;
             src = dst;
         }
     }
-    SG_CUDA(cudaStreamSynchronize(h->stream));
+    if (sync) SG_CUDA(cudaStreamSynchronize(st));
     h->combined = true;
     return SG_OK;
 }
 
 // Fused form (Step 3): phase 1 prolongs every grid over axes 0..d-2 into a pool slot (the
-// grid itself if none of those axes is coarse); phase 2 prolongs the last axis of all grids
-// and forms sum_g c_g P U_g in one pass that writes uhat once.  Buffers come from `cb` (the
-// handle's own, or a batch's, shared by its members).  Returns SG_ERR_UNSUPPORTED (without
-// touching anything) when the pool would exceed the budget.
+// grid itself if none of those axes is coarse), one launch per axis for all grids (a pass over
+// a task table; a grid's intermediate arrays get slots of their own); phase 2 prolongs the last
+// axis of all grids and forms sum_g c_g P U_g in one pass that writes uhat once.  Buffers come
+// from `cb` (the handle's own, or a batch's, shared by its members).  Returns
+// SG_ERR_UNSUPPORTED (without touching anything) when the intermediates would exceed the
+// budget.
 template <class T>
-sg_status prolong_combine_fused_t(sg_ctx* h, CombineBuffers& cb) {
+sg_status prolong_combine_fused_t(sg_ctx* h, CombineBuffers& cb, cudaStream_t st, bool sync) {
+    constexpr int J = 8;  // fine nodes per unit of a prolongation pass (sg_prolong_multi_kernel)
     const int d = h->dim;
     const long long Nf = (long long)h->nr << h->nl;
+    const long long nch = (Nf + J - 1) / J;
     long long below = 1;
     for (int k = 0; k + 1 < d; ++k) below *= Nf;
-    // sizes: pool slots and the ping-pong buffers of phase 1
-    long long pool = 0, need = 1;
-    std::vector<long long> slot(h->G, -1);
+    // plan: per pass (axis k < d-1) the tasks of the grids coarse on axis k; slots in the pool
+    // (each grid's last prolonged axis) and in the intermediate buffer (the others).  Grids are
+    // taken in groups whose intermediates fit beside the pool in the budget; each group runs
+    // its passes in axis order and reuses the intermediate buffer of the previous group.
+    struct Plan {
+        int g;
+        long long in_off, out_off;  // element offsets: in: -1 = the grid itself, else intermediate;
+        bool out_pool;              // out: pool slot or intermediate
+        long long below, above;
+        int n, r, zero;
+    };
+    const double budget = h->prm.combine_budget_gb == 0.0 ? 8.0e9 : h->prm.combine_budget_gb * 1e9;
+    if (budget < 0.0) return SG_ERR_UNSUPPORTED;
+    long long pool = 0;
+    std::vector<long long> slot(h->G, -1), gint(h->G, 0);  // pool slot, intermediate elements
     for (int g = 0; g < h->G; ++g) {
         const GridDesc& gd = h->hgrids[g];
         long long m[SG_MAXD];
-        std::vector<int> axes;
+        int last = -1;
         for (int k = 0; k < d; ++k) {
             m[k] = gd.n[k];
-            if (k + 1 < d && gd.lev[k] < h->nl) axes.push_back(k);
+            if (k + 1 < d && gd.lev[k] < h->nl) last = k;
         }
-        if (axes.empty()) continue;
+        if (last < 0) continue;
         slot[g] = pool;
         pool += below * m[d - 1];
-        for (size_t a = 0; a + 1 < axes.size(); ++a) {
-            m[axes[a]] = Nf;
+        for (int k = 0; k < last; ++k) {  // every coarse axis before the last one leaves an array
+            if (gd.lev[k] >= h->nl) continue;
+            m[k] = Nf;
             long long tot = 1;
-            for (int k = 0; k < d; ++k) tot *= m[k];
-            need = std::max(need, tot);
+            for (int j = 0; j < d; ++j) tot *= m[j];
+            gint[g] += tot;
         }
     }
-    // bytes of intermediates the fused form may hold
-    const double budget = h->prm.combine_budget_gb == 0.0 ? 8.0e9 : h->prm.combine_budget_gb * 1e9;
-    if (budget < 0.0 || (double)(pool + 2 * need) * sizeof(T) > budget) return SG_ERR_UNSUPPORTED;
+    const double room = budget / sizeof(T) - (double)pool;  // elements left for intermediates
+    long long gmax = 0;
+    for (long long v : gint) gmax = std::max(gmax, v);
+    if (room < (double)gmax) return SG_ERR_UNSUPPORTED;
+    std::vector<std::vector<int>> groups(1);
+    long long interm = 0, cur = 0;
+    for (int g = 0; g < h->G; ++g) {
+        if (slot[g] < 0) continue;
+        if ((double)(cur + gint[g]) > room) {
+            groups.emplace_back();
+            cur = 0;
+        }
+        groups.back().push_back(g);
+        cur += gint[g];
+        interm = std::max(interm, cur);
+    }
+    // passes[group][k]
+    std::vector<std::vector<std::vector<Plan>>> passes(groups.size(), std::vector<std::vector<Plan>>(d > 1 ? d - 1 : 1));
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        long long ioff = 0;
+        for (int g : groups[gi]) {
+            const GridDesc& gd = h->hgrids[g];
+            long long m[SG_MAXD];
+            std::vector<int> axes;
+            for (int k = 0; k < d; ++k) {
+                m[k] = gd.n[k];
+                if (k + 1 < d && gd.lev[k] < h->nl) axes.push_back(k);
+            }
+            long long in_off = -1;
+            for (size_t a = 0; a < axes.size(); ++a) {
+                const int k = axes[a];
+                Plan pl{};
+                pl.g = g;
+                pl.in_off = in_off;
+                pl.below = 1;
+                pl.above = 1;
+                for (int j = 0; j < k; ++j) pl.below *= m[j];
+                for (int j = k + 1; j < d; ++j) pl.above *= m[j];
+                pl.n = (int)m[k];
+                pl.r = 1 << (h->nl - gd.lev[k]);
+                pl.zero = zero_axis(h, k) ? 1 : 0;
+                m[k] = Nf;
+                pl.out_pool = a + 1 == axes.size();
+                if (pl.out_pool) {
+                    pl.out_off = slot[g];
+                } else {
+                    long long tot = 1;
+                    for (int j = 0; j < d; ++j) tot *= m[j];
+                    pl.out_off = ioff;
+                    ioff += tot;
+                }
+                in_off = pl.out_off;
+                passes[gi][k].push_back(pl);
+            }
+        }
+    }
+    // the pass kernel indexes a task's units and columns with 32 bits
+    size_t ntask = 0;
+    for (const auto& gp : passes)
+        for (const auto& ps : gp) {
+            ntask += ps.size();
+            for (const Plan& pl : ps)
+                if ((double)pl.below * (double)nch * (double)pl.above >= 2147483648.0 || pl.below >= (1LL << 31))
+                    return SG_ERR_UNSUPPORTED;
+        }
     if (!h->uhat.p) SG_TRY(h->uhat.alloc(sizeof(double) * (size_t)h->fine_pts));
     if (cb.pool.bytes < sizeof(T) * (size_t)std::max(pool, 1LL)) SG_TRY(cb.pool.alloc(sizeof(T) * (size_t)std::max(pool, 1LL)));
-    if (cb.pa.bytes < sizeof(T) * (size_t)need) {
-        SG_TRY(cb.pa.alloc(sizeof(T) * (size_t)need));
-        SG_TRY(cb.pb.alloc(sizeof(T) * (size_t)need));
-    }
-    if (cb.tab.bytes < sizeof(CombineGrid) * (size_t)h->G) SG_TRY(cb.tab.alloc(sizeof(CombineGrid) * (size_t)h->G));
-    std::vector<CombineGrid> tab(h->G);
-    T* bufs[2] = {cb.pa.as<T>(), cb.pb.as<T>()};
+    if (cb.pa.bytes < sizeof(T) * (size_t)std::max(interm, 1LL)) SG_TRY(cb.pa.alloc(sizeof(T) * (size_t)std::max(interm, 1LL)));
+    const size_t tab_bytes = sizeof(CombineGrid) * (size_t)h->G, ptab_off = (tab_bytes + 255) & ~(size_t)255;
+    const size_t all_bytes = ptab_off + sizeof(ProlongTask) * std::max<size_t>(ntask, 1);
+    if (cb.tab.bytes < all_bytes) SG_TRY(cb.tab.alloc(all_bytes));
+    // host copy of both tables, uploaded with one copy
+    std::vector<unsigned char> host(all_bytes, 0);
+    CombineGrid* tab = reinterpret_cast<CombineGrid*>(host.data());
+    ProlongTask* ptab = reinterpret_cast<ProlongTask*>(host.data() + ptab_off);
+    T* poolp = cb.pool.as<T>();
+    T* intp = cb.pa.as<T>();
+    struct Launch1 {
+        size_t first;
+        int ntasks;
+        long long units;
+    };
+    std::vector<Launch1> launches;  // per group, per pass, in order
+    size_t ti = 0;
+    for (const auto& gp : passes)
+        for (const auto& ps : gp) {  // passes in axis order: a grid's axes run 0, 1, ..., d-2
+            long long unit0 = 0;
+            const size_t first = ti;
+            for (const Plan& pl : ps) {
+                const GridDesc& gd = h->hgrids[pl.g];
+                ProlongTask& t = ptab[ti++];
+                t.in = pl.in_off < 0 ? (const void*)gd.u0 : (const void*)(intp + pl.in_off);
+                t.out = pl.out_pool ? (void*)(poolp + pl.out_off) : (void*)(intp + pl.out_off);
+                t.unit0 = unit0;
+                t.below = (int)pl.below;
+                t.above = (int)pl.above;
+                t.n = pl.n;
+                t.nf = (int)Nf;
+                t.r = pl.r;
+                t.zero_bc = pl.zero;
+                t.below_mag = sg_div_magic64((unsigned)pl.below);
+                t.nch_mag = sg_div_magic64((unsigned)nch);
+                unit0 += pl.below * nch * pl.above;
+            }
+            if (ti > first) launches.push_back({first, (int)(ti - first), unit0});
+        }
     for (int g = 0; g < h->G; ++g) {
         const GridDesc& gd = h->hgrids[g];
-        long long m[SG_MAXD];
-        std::vector<int> axes;
-        for (int k = 0; k < d; ++k) {
-            m[k] = gd.n[k];
-            if (k + 1 < d && gd.lev[k] < h->nl) axes.push_back(k);
-        }
-        const T* src = (const T*)gd.u0;
-        for (size_t a = 0; a < axes.size(); ++a) {
-            const int k = axes[a];
-            long long lo = 1, hi = 1;
-            for (int j = 0; j < k; ++j) lo *= m[j];
-            for (int j = k + 1; j < d; ++j) hi *= m[j];
-            T* dst = a + 1 == axes.size() ? cb.pool.as<T>() + slot[g] : bufs[a & 1];
-            SG_CUDA(sg::Launch<T>::prolong_axis_win(src, dst, lo, (int)m[k], (int)Nf, hi, 1 << (h->nl - gd.lev[k]),
-                                                    h->prm.eps, h->prm.prolong, zero_axis(h, k) ? 1 : 0, h->stream));
-            h->launches += 1;
-            m[k] = Nf;
-            src = dst;
-        }
-        tab[g].src = src;
+        tab[g].src = slot[g] < 0 ? (const void*)gd.u0 : (const void*)(poolp + slot[g]);
         tab[g].n = gd.n[d - 1];
         tab[g].r = 1 << (h->nl - gd.lev[d - 1]);
         tab[g].coeff = gd.coeff;
     }
-    SG_CUDA(cudaMemcpyAsync(cb.tab.p, tab.data(), sizeof(CombineGrid) * tab.size(), cudaMemcpyHostToDevice, h->stream));
+    SG_CUDA(cudaMemcpyAsync(cb.tab.p, host.data(), all_bytes, cudaMemcpyHostToDevice, st));
+    const ProlongTask* dptab = reinterpret_cast<const ProlongTask*>(cb.tab.as<unsigned char>() + ptab_off);
+    for (const Launch1& L : launches) {
+        SG_CUDA(sg::Launch<T>::prolong_multi(dptab + L.first, L.ntasks, L.units, h->prm.eps, h->prm.prolong, st));
+        h->launches += 1;
+    }
     bool exact = true;  // |c| = C(d-1, q) a power of two for every grid (d <= 3)
     for (int g = 0; g < h->G; ++g) {
         const double a = std::fabs(h->coeff[g]);
@@ -1015,18 +1112,18 @@ sg_status prolong_combine_fused_t(sg_ctx* h, CombineBuffers& cb) {
     }
     SG_CUDA(sg::Launch<T>::combine_last_axis(cb.tab.as<CombineGrid>(), h->G, h->uhat.as<double>(), below, (int)Nf,
                                              exact ? 1 : 0, zero_axis(h, d - 1) ? 1 : 0, h->prm.eps,
-                                             h->prm.prolong, h->stream));
+                                             h->prm.prolong, st));
     h->launches += 1;
-    SG_CUDA(cudaStreamSynchronize(h->stream));
+    if (sync) SG_CUDA(cudaStreamSynchronize(st));
     h->combined = true;
     return SG_OK;
 }
 
 template <class T>
-sg_status prolong_combine_t(sg_ctx* h, CombineBuffers& cb) {
-    const sg_status st = prolong_combine_fused_t<T>(h, cb);
-    if (st != SG_ERR_UNSUPPORTED) return st;
-    return prolong_combine_rmw_t<T>(h);
+sg_status prolong_combine_t(sg_ctx* h, CombineBuffers& cb, cudaStream_t st, bool sync) {
+    const sg_status r = prolong_combine_fused_t<T>(h, cb, st, sync);
+    if (r != SG_ERR_UNSUPPORTED) return r;
+    return prolong_combine_rmw_t<T>(h, st, sync);
 }
 
 sg_status check_handle(sg_handle h) {
@@ -1366,15 +1463,23 @@ sg_status sg_step(sg_handle h, double t_end, long max_steps, double* t_reached) 
 sg_status sg_prolong_combine(sg_handle h) {
     SG_TRY(check_handle(h));
     try {
-        if (h->is_batch) {  // members one after another, sharing the batch's intermediates
+        if (h->is_batch) {
+            // members one after another on the batch's stream, sharing its intermediates (stream
+            // order keeps them apart); each member's own stream is drained first, once at the end
+            // the batch's
             for (sg_ctx* m : h->members) {
                 if (!m->initialized) return fail(SG_ERR_STATE, "sg_prolong_combine before sg_init");
-                SG_TRY(m->esize == 8 ? prolong_combine_t<double>(m, h->comb) : prolong_combine_t<float>(m, h->comb));
+                if (m->stream != h->stream) SG_CUDA(cudaStreamSynchronize(m->stream));
             }
+            for (sg_ctx* m : h->members)
+                SG_TRY(m->esize == 8 ? prolong_combine_t<double>(m, h->comb, h->stream, false)
+                                     : prolong_combine_t<float>(m, h->comb, h->stream, false));
+            SG_CUDA(cudaStreamSynchronize(h->stream));
             return SG_OK;
         }
         if (!h->initialized) return fail(SG_ERR_STATE, "sg_prolong_combine before sg_init");
-        return h->esize == 8 ? prolong_combine_t<double>(h, h->comb) : prolong_combine_t<float>(h, h->comb);
+        return h->esize == 8 ? prolong_combine_t<double>(h, h->comb, h->stream, true)
+                             : prolong_combine_t<float>(h, h->comb, h->stream, true);
     } catch (const std::bad_alloc&) {
         return fail(SG_ERR_NOMEM, "host allocation failed");
     }

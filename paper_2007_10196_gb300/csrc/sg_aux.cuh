@@ -648,6 +648,79 @@ __global__ void __launch_bounds__(256) sg_prolong_axis_win_kernel(const T* __res
     }
 }
 
+// One prolongation pass over many grids (Step 3, axes 0..d-2, Section 2.2.1): thread u of
+// the pass takes unit u -- J consecutive fine nodes of one line -- of the task whose unit range
+// holds it, and slides the coarse window along the line as sg_prolong_axis_win_kernel does
+// (the same arithmetic per output).  Consecutive units are consecutive columns (below > 1: the
+// loads of a warp are coalesced) or consecutive chunks of one row (below = 1).
+template <class T, int J>
+__global__ void __launch_bounds__(256) sg_prolong_multi_kernel(const ProlongTask* __restrict__ tasks, int ntasks,
+                                                               long long nunits, double eps, int lagrange) {
+    const T e4 = sg_eps4<T>(eps);
+    for (long long u = blockIdx.x * 256LL + threadIdx.x; u < nunits; u += gridDim.x * 256LL) {
+        int a = 0, b = ntasks - 1;  // the last task with unit0 <= u
+        while (a < b) {
+            const int mid = (a + b + 1) >> 1;
+            if (tasks[mid].unit0 <= u) a = mid;
+            else b = mid - 1;
+        }
+        const ProlongTask& tk = tasks[a];
+        const unsigned v = (unsigned)(u - tk.unit0);
+        const unsigned below = (unsigned)tk.below;
+        const int nchunks = (tk.nf + J - 1) / J;
+        const unsigned q = div_mag(v, below, tk.below_mag);
+        const unsigned lo = v - q * below;
+        const unsigned hi = div_mag(q, (unsigned)nchunks, tk.nch_mag);
+        const int j0 = (int)(q - hi * (unsigned)nchunks) * J;
+        const int n = tk.n, nf = tk.nf, r = tk.r, lr = __ffs(r) - 1;
+        const T inv_r = pow2_neg<T>(lr);
+        const T* col = (const T*)tk.in + (long long)hi * below * n + lo;
+        T* ocol = (T*)tk.out + (long long)hi * below * nf + lo;
+        auto centre = [&](int jf, int& ic, T& s) {  // as fine_to_coarse
+            const int i = jf >> lr, m = jf & (r - 1);
+            if (2 * m < r) {
+                ic = i;
+                s = (T)m * inv_r;
+            } else {
+                ic = i + 1;
+                s = (T)(m - r) * inv_r;
+            }
+        };
+        auto at = [&](int c) -> T {  // c in [-2, n + 2]
+            if (tk.zero_bc && (c < 0 || c >= n)) return T(0);
+            return col[(long long)wrap_index(c, n) * below];
+        };
+        int cur;
+        T s0;
+        centre(j0, cur, s0);
+        InterpWin<T> W;
+        W.w0 = at(cur - 2);
+        W.w1 = at(cur - 1);
+        W.w2 = at(cur);
+        W.w3 = at(cur + 1);
+        W.w4 = at(cur + 2);
+        W.prepare(e4, lagrange);
+#pragma unroll 1
+        for (int j = 0; j < J; ++j) {
+            const int jf = j0 + j;
+            if (jf >= nf) break;
+            int ic;
+            T s;
+            centre(jf, ic, s);
+            if (ic != cur) {  // centres advance by one coarse node at a time (r >= 2)
+                W.w0 = W.w1;
+                W.w1 = W.w2;
+                W.w2 = W.w3;
+                W.w3 = W.w4;
+                W.w4 = at(ic + 2);
+                W.prepare(e4, lagrange);
+                cur = ic;
+            }
+            ocol[(long long)jf * below] = W.eval(s, (T)eps, lagrange);
+        }
+    }
+}
+
 // uhat += coeff * u for a grid that is already the finest grid.
 template <class T>
 __global__ void sg_accumulate_kernel(const T* __restrict__ u, double* __restrict__ acc, double coeff,

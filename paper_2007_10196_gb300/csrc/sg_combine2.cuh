@@ -1,0 +1,190 @@
+// sg_combine2.cuh -- Step 3's last axis and the signed combination sum (Eqs. 12-15) in FP32
+// for two adjacent columns per thread, with GB300's packed two-lane FP32 arithmetic.
+//
+// Every column of a grid's phase-1 array (the grid prolonged over axes 0..d-2) has the same
+// last-axis structure: the same coarse length, refinement ratio, centres and offsets s of the
+// fine nodes.  Two adjacent columns therefore follow one control flow, and each arithmetic
+// instruction can serve both as a packed f32x2 operation: the interpolation of Eqs. (8)-(11)
+// (the window preparation and the per-node evaluation) and the float-pair accumulation of
+// c_g v.  Each coarse row is read as one 8-byte load per column pair.
+//
+// Thread layout: threadIdx.x = 32 column pairs (a warp reads 64 consecutive columns, 256
+// bytes per coarse row), threadIdx.y = CY consecutive chunks of J fine nodes along the last
+// axis; blockIdx.x walks the chunk groups of the last axis, blockIdx.y the column blocks.
+// The warps of a block and the blocks with consecutive blockIdx.x read overlapping windows of
+// the same columns, so the repeated window loads hit L1 or L2 instead of DRAM.
+#pragma once
+#include "sg_aux.cuh"
+
+__device__ __forceinline__ float2 sg_f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sg_neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sg_add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sg_sub2(float2 a, float2 b) { return __fadd2_rn(a, sg_neg2(b)); }
+__device__ __forceinline__ float2 sg_mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 sg_fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// InterpWin<float> for two columns: the same formulas lane by lane (the rescaling of the
+// smoothness terms, weno_scale3, works per lane).
+struct InterpWin2 {
+    float2 w0, w1, w2, w3, w4;
+    float2 n0, n1, n2, n3, d0, d1, d2;
+    __device__ __forceinline__ void prepare(float eps4, int lagrange) {
+        const float2 d1_ = sg_sub2(w1, w0), d2_ = sg_sub2(w2, w1), d3_ = sg_sub2(w3, w2), d4_ = sg_sub2(w4, w3);
+        const float2 t0 = sg_sub2(d2_, d1_), t1 = sg_sub2(d3_, d2_), t2 = sg_sub2(d4_, d3_);
+        const float2 s0 = sg_fma2(sg_f2(3.f), d2_, sg_neg2(d1_)), s1 = sg_add2(d2_, d3_);
+        const float2 s2 = sg_fma2(sg_f2(3.f), d3_, sg_neg2(d4_));
+        float2 E0 = sg_f2(1.f), E1 = sg_f2(1.f), E2 = sg_f2(1.f);  // 1 for Lagrange
+        if (!lagrange) {
+            const float2 c13 = sg_f2(13.f / 3.f), ep = sg_f2(eps4);
+            float2 e0 = sg_fma2(sg_mul2(c13, t0), t0, sg_fma2(s0, s0, ep));
+            float2 e1 = sg_fma2(sg_mul2(c13, t1), t1, sg_fma2(s1, s1, ep));
+            float2 e2 = sg_fma2(sg_mul2(c13, t2), t2, sg_fma2(s2, s2, ep));
+            weno_scale3(e0.x, e1.x, e2.x);
+            weno_scale3(e0.y, e1.y, e2.y);
+            const float2 q0 = sg_mul2(e0, e0), q1 = sg_mul2(e1, e1), q2 = sg_mul2(e2, e2);
+            E0 = sg_mul2(q1, q2);
+            E1 = sg_mul2(q0, q2);
+            E2 = sg_mul2(q0, q1);
+        }
+        // C_0 = 1/6 - s/4 + s^2/12, C_1 = 2/3 - s^2/6, C_2 = 1/6 + s/4 + s^2/12
+        const float2 A0 = sg_mul2(E0, s0), A1 = sg_mul2(E1, s1), A2 = sg_mul2(E2, s2);
+        const float2 B0 = sg_mul2(E0, t0), B1 = sg_mul2(E1, t1), B2 = sg_mul2(E2, t2);
+        const float2 Ap = sg_add2(A0, A2), Bp = sg_add2(B0, B2), Ep = sg_add2(E0, E2);
+        n0 = sg_fma2(Ap, sg_f2(1.f / 6.f), sg_mul2(sg_f2(2.f / 3.f), A1));
+        n1 = sg_fma2(Bp, sg_f2(1.f / 6.f), sg_fma2(sg_sub2(A2, A0), sg_f2(0.25f), sg_mul2(sg_f2(2.f / 3.f), B1)));
+        n2 = sg_fma2(sg_sub2(B2, B0), sg_f2(0.25f), sg_fma2(Ap, sg_f2(1.f / 12.f), sg_mul2(sg_f2(-1.f / 6.f), A1)));
+        n3 = sg_fma2(Bp, sg_f2(1.f / 12.f), sg_mul2(sg_f2(-1.f / 6.f), B1));
+        d0 = sg_fma2(Ep, sg_f2(1.f / 6.f), sg_mul2(sg_f2(2.f / 3.f), E1));
+        d1 = sg_mul2(sg_sub2(E2, E0), sg_f2(0.25f));
+        d2 = sg_fma2(Ep, sg_f2(1.f / 12.f), sg_mul2(sg_f2(-1.f / 6.f), E1));
+    }
+    // w2 + (s/2) N(s) / D(s); D >= 1/16 (see Weno<float>::interp), inside __fdividef's range
+    __device__ __forceinline__ float2 eval(float s) const {
+        if (s == 0.f) return w2;
+        const float2 S = sg_f2(s);
+        const float2 N = sg_fma2(sg_fma2(sg_fma2(n3, S, n2), S, n1), S, n0);
+        const float2 D = sg_fma2(sg_fma2(d2, S, d1), S, d0);
+        const float2 q = make_float2(__fdividef(N.x, D.x), __fdividef(N.y, D.y));
+        return sg_fma2(sg_f2(0.5f * s), q, w2);
+    }
+};
+
+// CombineAcc<float> for two columns: an unevaluated float pair per column (error-free sums
+// and products), lane by lane the same operations.
+struct CombineAcc2 {
+    float2 hi = make_float2(0.f, 0.f), lo = make_float2(0.f, 0.f);
+    template <bool EXACT>
+    __device__ __forceinline__ void add(float cf, float2 v) {
+        const float2 c = sg_f2(cf);
+        const float2 p = sg_mul2(c, v);
+        const float2 s = sg_add2(hi, p);  // two-sum of hi and p
+        const float2 bb = sg_sub2(s, hi);
+        const float2 e = sg_add2(sg_sub2(hi, sg_sub2(s, bb)), sg_sub2(p, bb));
+        hi = s;
+        if (EXACT) {
+            lo = sg_add2(lo, e);
+        } else {
+            const float2 pe = sg_fma2(c, v, sg_neg2(p));  // exact product error
+            lo = sg_add2(lo, sg_add2(e, pe));
+        }
+    }
+};
+
+template <int J, int CY, bool EXACT>
+__global__ void __launch_bounds__(32 * CY) sg_combine_last_axis_f32x2_kernel(const CombineGrid* __restrict__ tab, int G,
+                                                                         double* __restrict__ uhat, long long below,
+                                                                         int nf, double eps, int lagrange,
+                                                                         int zero_last) {
+    const float e4 = sg_eps4<float>(eps);
+    constexpr int JB = J * CY;  // fine nodes of the last axis per block
+    // centre and offset s of the block's JB fine nodes for every ratio r = 2^lr (lr <= 16)
+    __shared__ float s_tab[17 * JB];
+    __shared__ int c_tab[17 * JB];
+    const int ngroups = (nf + JB - 1) / JB;
+    const long long npairs = (below + 1) >> 1;
+    const bool even = (below & 1) == 0;
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int jb = grp * JB;
+        __syncthreads();  // the previous group's readers are done
+        for (int t = threadIdx.y * 32 + threadIdx.x; t < 17 * JB; t += 32 * CY) {
+            const int lr = t / JB, jf = jb + (t - lr * JB), r = 1 << lr;
+            const int i = jf >> lr, m = jf & (r - 1);  // jf = i r + m; centre i or i + 1
+            const float inv_r = pow2_neg<float>(lr);
+            if (2 * m < r) {
+                c_tab[t] = i;
+                s_tab[t] = (float)m * inv_r;
+            } else {
+                c_tab[t] = i + 1;
+                s_tab[t] = (float)(m - r) * inv_r;
+            }
+        }
+        __syncthreads();
+        const int j0 = jb + threadIdx.y * J;  // this warp's chunk
+        if (j0 >= nf) continue;
+        for (long long pr = blockIdx.y * 32LL + threadIdx.x; pr < npairs; pr += gridDim.y * 32LL) {
+            const long long lo = 2 * pr;
+            const bool two = lo + 1 < below;
+            CombineAcc2 acc[J];
+            for (int g = 0; g < G; ++g) {
+                const CombineGrid cg = tab[g];
+                const float* col = (const float*)cg.src + lo;
+                const int n = cg.n, r = cg.r;
+                const float cT = (float)cg.coeff;
+                // both columns with one 8-byte load where the rows keep them 8-byte aligned
+                const bool vec = even && ((reinterpret_cast<unsigned long long>(cg.src) & 7) == 0);
+                auto row = [&](int c) -> float2 {  // coarse row c of the last axis (c in [-2, n + 2])
+                    if (zero_last && (c < 0 || c >= n)) return make_float2(0.f, 0.f);
+                    const float* p = col + (long long)wrap_index(c, n) * below;
+                    if (vec) return *reinterpret_cast<const float2*>(p);
+                    return make_float2(p[0], two ? p[1] : 0.f);
+                };
+                if (r == 1) {  // last axis already fine: values at coincident nodes
+#pragma unroll
+                    for (int j = 0; j < J; ++j)
+                        if (j0 + j < nf) acc[j].template add<EXACT>(cT, row(j0 + j));
+                    continue;
+                }
+                const int lr = __ffs(r) - 1;  // r = 2^lr: this warp's centres and offsets
+                const int* ct = c_tab + lr * JB + threadIdx.y * J;
+                const float* sv = s_tab + lr * JB + threadIdx.y * J;
+                int cur = ct[0];
+                InterpWin2 W;
+                W.w0 = row(cur - 2);
+                W.w1 = row(cur - 1);
+                W.w2 = row(cur);
+                W.w3 = row(cur + 1);
+                W.w4 = row(cur + 2);
+                W.prepare(e4, lagrange);
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    if (j0 + j >= nf) break;
+                    const int ic = ct[j];
+                    if (ic != cur) {  // centres advance by one coarse node at a time (r >= 2)
+                        W.w0 = W.w1;
+                        W.w1 = W.w2;
+                        W.w2 = W.w3;
+                        W.w3 = W.w4;
+                        W.w4 = row(ic + 2);
+                        W.prepare(e4, lagrange);
+                        cur = ic;
+                    }
+                    acc[j].template add<EXACT>(cT, W.eval(sv[j]));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int jf = j0 + j;
+                if (jf >= nf) break;
+                const double v0 = (double)acc[j].hi.x + (double)acc[j].lo.x;
+                const double v1 = (double)acc[j].hi.y + (double)acc[j].lo.y;
+                double* o = uhat + lo + (long long)jf * below;
+                if (even) {
+                    *reinterpret_cast<double2*>(o) = make_double2(v0, v1);
+                } else {
+                    o[0] = v0;
+                    if (two) o[1] = v1;
+                }
+            }
+        }
+    }
+}

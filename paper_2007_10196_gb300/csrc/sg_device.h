@@ -119,6 +119,24 @@ struct CombineGrid {
     double coeff;     // combination coefficient
 };
 
+// One grid's share of a prolongation pass over many grids (Step 3, axes 0..d-2): the array
+// `in` of shape (below, n, above) (axis 0 fastest) is prolonged along its middle axis into
+// `out` of shape (below, nf, above).  Its units -- chunks of J consecutive fine nodes of one
+// line, numbered lo + below (chunk + nchunks hi) -- are the pass's global unit indices
+// [unit0, unit0 + below nchunks above).
+struct ProlongTask {
+    const void* in;
+    void* out;
+    long long unit0;
+    int below;        // < 2^31 (a pass's unit count is checked on the host)
+    int above;
+    int n;            // coarse points of the prolonged axis
+    int nf;           // fine points of the prolonged axis
+    int r;            // refinement ratio nf / n = 2^{N_L - l}
+    int zero_bc;      // 0 beyond the ends of the axis, else periodic
+    unsigned long long below_mag, nch_mag;  // sg_div_magic64 of below and of the chunks per line
+};
+
 // flags[0]: a non-finite value appeared; flags[1]: a time step came out non-positive or
 // non-finite (the instance is stopped)
 enum { SG_FLAG_NONFINITE = 0, SG_FLAG_BADDT = 1 };

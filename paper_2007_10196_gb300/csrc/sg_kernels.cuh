@@ -12,3 +12,4 @@
 #include "sg_stage.cuh"
 #include "sg_stage_line.cuh"
 #include "sg_aux.cuh"
+#include "sg_combine2.cuh"

@@ -69,6 +69,10 @@ struct Launch {
     // zero_bc as for prolong_axis.
     static cudaError_t prolong_axis_win(const T* in, T* out, long long below, int min_, int nf, long long above,
                                         int r, double eps, int lagrange, int zero_bc, cudaStream_t s);
+    // One prolongation pass over the ntasks tasks of a device table (their unit ranges cover
+    // [0, nunits)), J = 8 fine nodes per unit.
+    static cudaError_t prolong_multi(const ProlongTask* tasks, int ntasks, long long nunits, double eps, int lagrange,
+                                     cudaStream_t s);
     // uhat = sum_g c_g P_{d-1} I_g over the G entries of tab (device array), written once.
     // exact_coeffs: every |c_g| is a power of two (products c_g v are exact in the FP32 sum)
     static cudaError_t combine_last_axis(const CombineGrid* tab, int G, double* uhat, long long below, int nf,

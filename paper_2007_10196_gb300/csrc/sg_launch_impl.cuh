@@ -16,7 +16,7 @@ template <class T, int D, int PPT>
 struct StageKernel {
     static constexpr int threads = D == 3 ? SG_NT3 : SG_NT;
     static void* fn() {
-        if constexpr (D == 3) return (void*)sg_stage_sweep3_kernel<T>;
+        if constexpr (D == 3) return (void*)sg_stage_sweep3_kernel<T, false>;
         else if constexpr (D <= 2) return (void*)sg_stage_box_kernel<T, D, PPT>;
         else return (void*)sg_stage_line_kernel<T, D, PPT>;
     }
@@ -25,7 +25,10 @@ struct StageKernel {
 template <class T, int D, int PPT>
 cudaError_t stage_one(const StageArgs& a, int nblocks, size_t smem, cudaStream_t s) {
     // the dynamic shared-memory limit was raised by stage_prepare() when the handle was created
-    if constexpr (D == 3) sg_stage_sweep3_kernel<T><<<nblocks, SG_NT3, smem, s>>>(a);
+    if constexpr (D == 3) {
+        if (a.phys.zmask) sg_stage_sweep3_kernel<T, true><<<nblocks, SG_NT3, smem, s>>>(a);
+        else sg_stage_sweep3_kernel<T, false><<<nblocks, SG_NT3, smem, s>>>(a);
+    }
     else if constexpr (D <= 2) sg_stage_box_kernel<T, D, PPT><<<nblocks, SG_NT, smem, s>>>(a);
     else sg_stage_line_kernel<T, D, PPT><<<nblocks, SG_NT, smem, s>>>(a);
     return cudaGetLastError();
@@ -37,6 +40,13 @@ int prepare_one(size_t smem) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
+    }
+    if constexpr (D == 3) {  // the zero-boundary instantiation of the sweep kernel (same resources)
+        if (cudaFuncSetAttribute((const void*)sg_stage_sweep3_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
     }
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, StageKernel<T, D, PPT>::threads, smem) != cudaSuccess) {
@@ -269,10 +279,32 @@ cudaError_t Launch<T>::prolong_axis_win(const T* in, T* out, long long below, in
 }
 
 template <class T>
+cudaError_t Launch<T>::prolong_multi(const ProlongTask* tasks, int ntasks, long long nunits, double eps, int lagrange,
+                                     cudaStream_t s) {
+    if (ntasks < 1 || nunits < 1) return cudaSuccess;
+    const unsigned nb = (unsigned)std::min<long long>((nunits + 255) / 256, 1LL << 22);
+    sg_prolong_multi_kernel<T, 8><<<nb, 256, 0, s>>>(tasks, ntasks, nunits, eps, lagrange);
+    return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t Launch<T>::combine_last_axis(const CombineGrid* tab, int G, double* uhat, long long below, int nf,
                                          int exact_coeffs, int zero_last,
                                          double eps, int lagrange, cudaStream_t s) {
     constexpr int J = 8;
+    if constexpr (sizeof(T) == 4) {  // two columns per thread, packed f32x2 (sg_combine2.cuh)
+        constexpr int CY = 8;
+        const long long npairs = (below + 1) / 2;
+        const dim3 grid2((unsigned)std::min<long long>((nf + J * CY - 1) / (J * CY), 65535),
+                         (unsigned)std::min<long long>((npairs + 31) / 32, 65535));
+        if (exact_coeffs)
+            sg_combine_last_axis_f32x2_kernel<J, CY, true><<<grid2, dim3(32, CY), 0, s>>>(tab, G, uhat, below, nf, eps,
+                                                                                       lagrange, zero_last);
+        else
+            sg_combine_last_axis_f32x2_kernel<J, CY, false><<<grid2, dim3(32, CY), 0, s>>>(tab, G, uhat, below, nf, eps,
+                                                                                        lagrange, zero_last);
+        return cudaGetLastError();
+    }
     dim3 grid((unsigned)std::min<long long>((below + 255) / 256, 65535),
               (unsigned)std::min<long long>((nf + J - 1) / J, 65535));
     if (exact_coeffs)

@@ -567,7 +567,8 @@ __device__ __forceinline__ float sweep_flux(const SweepSide<float>& P, const Swe
 // lines a warp sweeps, and the points a warp updates, on distinct banks.
 #define SG_DK_AXIS 576
 
-template <class T>
+// ZB: some axis has a zero boundary (the periodic instantiation carries no boundary tests)
+template <class T, bool ZB>
 __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep3_kernel(const StageArgs A) {
     extern __shared__ __align__(16) unsigned char sg_smem_raw[];
     T* bp = reinterpret_cast<T*>(sg_smem_raw);   // f^+ (Burgers) or u (advection)
@@ -579,7 +580,7 @@ __global__ void __launch_bounds__(SG_NT3, sizeof(T) == 4 ? 6 : 1) sg_stage_sweep
     const bool burgers = ph.pde == 1;
     const T eps4 = sg_eps4<T>(ph.eps);
     const T adv[3] = {(T)ph.adv[0], (T)ph.adv[1], (T)ph.adv[2]};
-    const int zm = ph.zmask;  // zero boundary per axis (advection / Burgers)
+    const int zm = ZB ? ph.zmask : 0;  // zero boundary per axis (advection / Burgers)
 
     for (int it = A.item_begin + blockIdx.x; it < A.item_end; it += gridDim.x) {
         const WorkItem w = A.items[it];
