@@ -59,7 +59,7 @@ FP32_LANES_PER_SM = 128
 # Burgers shock time of u0 = 0.5 + a sin(pi (x+y+z)/2): characteristics in s = x+y+z move at
 # 3u, so they first cross at t = 1 / (3 a pi/2); members with a below this stay smooth to t_end.
 A_SMOOTH_AT_T_END = 2.0 / (3.0 * math.pi * 0.3)
-STAGE_SOURCES = ("sg_stage.cuh", "sg_weno.cuh", "sg_device.h")  # the d = 3 sweep kernel and what it includes
+STAGE_SOURCES = ("sg_stage.cuh", "sg_sweep2.cuh", "sg_weno.cuh", "sg_device.h")  # the d = 3 sweep kernels and what they include
 # Vlasov-Boltzmann (Example 5), FP32 line-buffer stage kernel, per point per RK stage: per axis
 # the split of the point (2: the line speed times the value, twice), two one-sided WENO5
 # reconstructions (2 x 54), their combination (7) and the flux difference (3); then the
@@ -234,6 +234,8 @@ def kernel_name(P, h):
     kern, tp, _ = P.sg_stage_config(h)
     if kern == P.SG_STAGE_SWEEP:
         return "sg_stage_sweep3_kernel<float, false>"
+    if kern == P.SG_STAGE_SWEEP2:
+        return "sg_stage_sweep3x2_kernel<false>"
     return "sg_stage_box_kernel<float,3,%d>" % (tp // 256)
 
 

@@ -96,8 +96,10 @@ enum { SG_DT_POW53 = 0, SG_DT_CFL = 1 };
  * SG_STAGE_TILED: the tiled kernel of the dimension (d <= 3 padded box, d >= 4 line buffer),
  *                 tiles of tile_points points (0 = 512);
  * SG_STAGE_SWEEP: d = 3 only -- one thread per grid line of an 8 x 8 x 8 tile, sweeping it
- *                 with a register window; tile_points is ignored. */
-enum { SG_STAGE_AUTO = 0, SG_STAGE_TILED = 1, SG_STAGE_SWEEP = 2 };
+ *                 with a register window; tile_points is ignored.
+ * SG_STAGE_SWEEP2: d = 3 and SG_F32 only -- the same sweep with two lines of one axis per
+ *                 thread, both in one packed two-lane FP32 instruction stream. */
+enum { SG_STAGE_AUTO = 0, SG_STAGE_TILED = 1, SG_STAGE_SWEEP = 2, SG_STAGE_SWEEP2 = 3 };
 /* Initial condition kinds for sg_init. SG_IC_SINE: u_0(x) = p0 + p1 sin(p2 (x_0+...+x_{d-1}) + p3).
  * SG_IC_LANDAU (SG_PDE_VLASOV only, 2 parameters a, k): f_0 = (1 + a cos(k x)) exp(-v^2/2)/sqrt(2 pi).
  * SG_IC_RELAX (SG_PDE_VLASOV_BOLTZMANN with dim 2 or 4, no parameters): the initial condition
@@ -258,12 +260,12 @@ sg_status sg_set_profiling(sg_handle h, int on);
 sg_status sg_profile(sg_handle h, int kind, double *ms, long *launches);
 
 /* The stage-kernel configuration the handle (or batch) steps with: *kernel receives
- * SG_STAGE_TILED or SG_STAGE_SWEEP, *tile_points the largest tile in points, *tune_ms the
+ * SG_STAGE_TILED, SG_STAGE_SWEEP or SG_STAGE_SWEEP2, *tile_points the largest tile in points, *tune_ms the
  * measured time of one RK-stage launch of the chosen configuration when the autotuner picked
  * it (0 otherwise).  Under SG_STAGE_AUTO with tile_points = 0 the autotuner runs at the first
  * sg_step: it times one stage-0 launch with dt = 0 (which leaves the solution untouched) of
  * each candidate -- the tiled kernel with 256-, 512- and 1024-point tiles and, for d = 3, the
- * sweep kernel -- keeps the fastest and remembers it, for the life of the process, per
+ * sweep kernels -- keeps the fastest and remembers it, for the life of the process, per
  * dimension, precision, PDE, scheme, execution mode and size class (total points rounded up
  * to a power of two).  Before that first step the query reports the starting configuration.
  * A batch puts all of its members on one configuration (the first member's at creation, the

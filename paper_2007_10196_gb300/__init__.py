@@ -28,7 +28,7 @@ SG_PLAIN, SG_BATCHED = 0, 1
 SG_WENO5, SG_LINEAR5 = 0, 1
 SG_PROLONG_WENO5, SG_PROLONG_LAGRANGE5 = 0, 1
 SG_DT_POW53, SG_DT_CFL = 0, 1
-SG_STAGE_AUTO, SG_STAGE_TILED, SG_STAGE_SWEEP = 0, 1, 2
+SG_STAGE_AUTO, SG_STAGE_TILED, SG_STAGE_SWEEP, SG_STAGE_SWEEP2 = 0, 1, 2, 3
 SG_IC_SINE, SG_IC_LANDAU, SG_IC_RELAX = 0, 1, 2
 SG_REDUCE_MASS, SG_REDUCE_ENERGY, SG_REDUCE_MIN, SG_REDUCE_MAX = 0, 1, 2, 3
 SG_REDUCE_L1_EXACT, SG_REDUCE_LINF_EXACT, SG_REDUCE_FIELD_ENERGY = 4, 5, 6

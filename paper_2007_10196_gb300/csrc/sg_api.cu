@@ -298,7 +298,7 @@ void stage_footprint(sg_ctx* h) {
     long long box = 1, flux = 1;
     for (const GridDesc& d : h->hgrids) {
         long long b, f;
-        if (h->dim == 3 && h->variant == 0) sg::sweep_footprint(d.te, &b, &f);
+        if (h->dim == 3 && (h->variant == 0 || h->variant == 3)) sg::sweep_footprint(d.te, &b, &f);
         else if (h->dim >= 4 || h->variant == 2) sg::line_footprint(h->dim, d.te, &b, &f);
         else sg::box_footprint(h->dim, d.te, &b, &f);
         box = std::max(box, b);
@@ -417,10 +417,13 @@ sg_status validate_params(const sg_params* p, int dim) {
     if (!(p->dt_coef > 0.0) || !(p->cfl > 0.0)) return fail(SG_ERR_ARG, "dt_coef and cfl must be > 0");
     if (p->tile_points != 0 && p->tile_points != 256 && p->tile_points != 512 && p->tile_points != 1024)
         return fail(SG_ERR_ARG, "tile_points must be 0, 256, 512 or 1024");
-    if (p->stage_kernel != SG_STAGE_AUTO && p->stage_kernel != SG_STAGE_TILED && p->stage_kernel != SG_STAGE_SWEEP)
+    if (p->stage_kernel != SG_STAGE_AUTO && p->stage_kernel != SG_STAGE_TILED && p->stage_kernel != SG_STAGE_SWEEP &&
+        p->stage_kernel != SG_STAGE_SWEEP2)
         return fail(SG_ERR_ARG, "stage_kernel");
-    if (p->stage_kernel == SG_STAGE_SWEEP && dim != 3)
-        return fail(SG_ERR_UNSUPPORTED, "the sweep stage kernel is implemented for d = 3 only");
+    if ((p->stage_kernel == SG_STAGE_SWEEP || p->stage_kernel == SG_STAGE_SWEEP2) && dim != 3)
+        return fail(SG_ERR_UNSUPPORTED, "the sweep stage kernels are implemented for d = 3 only");
+    if (p->stage_kernel == SG_STAGE_SWEEP2 && p->precision != SG_F32)
+        return fail(SG_ERR_UNSUPPORTED, "the two-line sweep kernel is FP32 only");
     if (!(p->theta > 0.0) || !std::isfinite(p->theta) || !(p->tau > 0.0) || std::isnan(p->tau))
         return fail(SG_ERR_ARG, "theta must be finite and > 0, tau > 0");
     return SG_OK;
@@ -450,7 +453,7 @@ sg_status build_tables(sg_ctx* h) {
         d.npts = h->npts[g];
         int n[SG_MAXD] = {1, 1, 1, 1, 1, 1};
         for (int k = 0; k < h->dim; ++k) n[k] = h->nr << h->levels[g][k];
-        if (h->dim == 3 && h->variant == 0) sg::sweep_tile(n, d.te);
+        if (h->dim == 3 && (h->variant == 0 || h->variant == 3)) sg::sweep_tile(n, d.te);
         else choose_tile(n, h->dim, pmax, d.te);
         int ntiles = 1;
         for (int k = 0; k < SG_MAXD; ++k) {
@@ -706,7 +709,7 @@ sg_status configure(sg_ctx* h, int variant, int ppt) {
 // times one RK-stage launch of each candidate configuration (stage 0 with dt = 0: it writes
 // only the first-stage buffer and an alpha slot, both of which the step itself rewrites) and
 // keeps the fastest.  Candidates: the tiled kernel with 256-, 512- and 1024-point tiles, and
-// for d = 3 the sweep kernel in place of the 256-point tile.  Choices are cached per
+// for d = 3 the sweep kernel in place of the 256-point tile (FP32: also the two-line sweep).  Choices are cached per
 // (dimension, precision, pde, scheme, batch or not, size class) for the life of the process.
 struct TuneKey {
     int dim, esize, pde, scheme, batched, size_class;
@@ -790,6 +793,7 @@ sg_status autotune(sg_ctx* h) {
     }
     std::vector<std::pair<int, int>> cand;
     if (h->pde == SG_PDE_VLASOV_BOLTZMANN) cand = {{2, 1}, {2, 2}, {2, 4}};
+    else if (h->dim == 3 && h->esize == 4) cand = {{3, 2}, {0, 2}, {1, 2}, {1, 4}};
     else if (h->dim == 3) cand = {{0, 2}, {1, 2}, {1, 4}};
     else cand = {{0, 1}, {0, 2}, {0, 4}};
     double best = INFINITY;
@@ -1232,8 +1236,9 @@ sg_status sg_create(int dim, int root_cells, int level, int pde, const sg_params
         // d = 3: variant 0 is the sweep kernel, 1 the padded box; other dimensions have one
         const bool autotuned = prm.stage_kernel == SG_STAGE_AUTO && prm.tile_points == 0;
         h->variant = dim == 3 && (autotuned || prm.stage_kernel == SG_STAGE_SWEEP) ? 0 : (dim == 3 ? 1 : 0);
+        if (dim == 3 && prm.stage_kernel == SG_STAGE_SWEEP2) h->variant = 3;
         if (pde == SG_PDE_VLASOV_BOLTZMANN) {  // the line-buffer kernel carries the kinetic terms
-            if (prm.stage_kernel == SG_STAGE_SWEEP) {
+            if (prm.stage_kernel == SG_STAGE_SWEEP || prm.stage_kernel == SG_STAGE_SWEEP2) {
                 delete h;
                 return fail(SG_ERR_UNSUPPORTED, "the Vlasov-Boltzmann model runs on the tiled kernel");
             }
@@ -1731,8 +1736,8 @@ const char* sg_last_error(void) { return g_err.c_str(); }
 
 sg_status sg_stage_config(sg_handle h, int* kernel, int* tile_points, double* tune_ms) {
     SG_TRY(check_handle(h));
-    const bool sweep = h->dim == 3 && h->variant == 0;
-    if (kernel) *kernel = sweep ? SG_STAGE_SWEEP : SG_STAGE_TILED;
+    const bool sweep = h->dim == 3 && (h->variant == 0 || h->variant == 3);
+    if (kernel) *kernel = !sweep ? SG_STAGE_TILED : (h->variant == 3 ? SG_STAGE_SWEEP2 : SG_STAGE_SWEEP);
     if (tile_points) *tile_points = sweep ? 512 : 256 * h->ppt;
     if (tune_ms) *tune_ms = h->tune_ms;
     return SG_OK;

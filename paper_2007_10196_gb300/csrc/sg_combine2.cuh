@@ -16,13 +16,6 @@
 #pragma once
 #include "sg_aux.cuh"
 
-__device__ __forceinline__ float2 sg_f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 sg_neg2(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 sg_add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sg_sub2(float2 a, float2 b) { return __fadd2_rn(a, sg_neg2(b)); }
-__device__ __forceinline__ float2 sg_mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 sg_fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
 // InterpWin<float> for two columns: the same formulas lane by lane (the rescaling of the
 // smoothness terms, weno_scale3, works per lane).
 struct InterpWin2 {

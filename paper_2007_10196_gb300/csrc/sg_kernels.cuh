@@ -11,5 +11,6 @@
 #include "sg_weno.cuh"
 #include "sg_stage.cuh"
 #include "sg_stage_line.cuh"
+#include "sg_sweep2.cuh"
 #include "sg_aux.cuh"
 #include "sg_combine2.cuh"

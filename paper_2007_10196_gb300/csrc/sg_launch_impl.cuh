@@ -94,7 +94,7 @@ size_t Launch<T>::stage_smem(int dim, int ppt, long long box, long long flux, in
 
 template <class T>
 int Launch<T>::stage_threads(int dim, int variant) {
-    return dim == 3 && variant == 0 ? SG_NT3 : SG_NT;
+    return dim == 3 && variant == 0 ? SG_NT3 : (dim == 3 && variant == 3 ? SG_NT3H : SG_NT);
 }
 
 namespace detail {
@@ -151,8 +151,33 @@ cudaError_t stage_box3(int ppt, const StageArgs& a, int nblocks, size_t smem, cu
 }
 }  // namespace detail
 
+namespace detail {
+// d = 3, FP32, two lines per thread (variant 3); both instantiations get the same limit
+template <class T>
+int prepare_sweep2(size_t smem) {
+    if constexpr (sizeof(T) != 4) {
+        return 0;
+    } else {
+        const void* k0 = (const void*)sg_stage_sweep3x2_kernel<false>;
+        const void* k1 = (const void*)sg_stage_sweep3x2_kernel<true>;
+        if (cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k0, SG_NT3H, smem) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return nb;
+    }
+}
+}  // namespace detail
+
 template <class T>
 int Launch<T>::stage_prepare(int dim, int ppt, size_t smem, int variant) {
+    if (dim == 3 && variant == 3) return detail::prepare_sweep2<T>(smem);
     if (dim == 3 && variant == 1) return detail::prepare_box3<T>(ppt, smem);
     if (dim == 2 && variant == 2) return detail::prepare_line2<T>(ppt, smem);
     switch (dim) {
@@ -170,6 +195,15 @@ template <class T>
 cudaError_t Launch<T>::stage(int dim, int ppt, const StageArgs& a, int nblocks, size_t smem, cudaStream_t s,
                              int variant) {
     if (nblocks < 1) return cudaSuccess;
+    if (dim == 3 && variant == 3) {
+        if constexpr (sizeof(T) != 4) {
+            return cudaErrorInvalidValue;
+        } else {
+            if (a.phys.zmask) sg_stage_sweep3x2_kernel<true><<<nblocks, SG_NT3H, smem, s>>>(a);
+            else sg_stage_sweep3x2_kernel<false><<<nblocks, SG_NT3H, smem, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
     if (dim == 3 && variant == 1) return detail::stage_box3<T>(ppt, a, nblocks, smem, s);
     if (dim == 2 && variant == 2) return detail::stage_line2<T>(ppt, a, nblocks, smem, s);
     switch (dim) {

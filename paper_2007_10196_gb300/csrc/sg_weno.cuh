@@ -146,6 +146,15 @@ __device__ __forceinline__ float block_max(float v, float* red) {
     return v;
 }
 
+// Packed two-lane FP32 arithmetic (one instruction for both lanes; sm_100 and later), used by
+// the kernels that carry two independent columns or lines per thread.
+__device__ __forceinline__ float2 sg_f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sg_neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sg_add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sg_sub2(float2 a, float2 b) { return __fadd2_rn(a, sg_neg2(b)); }
+__device__ __forceinline__ float2 sg_mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 sg_fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 template <class T>
 struct Weno;
 

@@ -82,7 +82,7 @@ def test_argument_errors_without_gpu(built):
         P.sg_create(2, 10, 3, P.SG_PDE_ADVECTION, P.sg_params_init(stage_kernel=P.SG_STAGE_SWEEP))
     assert e.value.status == P.SG_ERR_UNSUPPORTED
     with pytest.raises(P.SgError) as e:
-        P.sg_create(3, 10, 3, P.SG_PDE_ADVECTION, P.sg_params_init(stage_kernel=3))
+        P.sg_create(3, 10, 3, P.SG_PDE_ADVECTION, P.sg_params_init(stage_kernel=4))
     assert e.value.status == P.SG_ERR_ARG
     with pytest.raises(P.SgError) as e:
         P.sg_create(3, 10, 3, P.SG_PDE_ADVECTION, P.sg_params_init(tile_points=300))

@@ -20,12 +20,15 @@ from _helpers import make, oracle_problem, random_grids, read_grids
 pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
-SWEEP = -1
+SWEEP, SWEEP2 = -1, -2
 
-# (dim, nr, nl, pde, tile): tile SWEEP = the d = 3 line-sweep kernel, else the tiled kernel
-# with that tile (d <= 3 padded box, d = 4 line buffer)
+# (dim, nr, nl, pde, tile): tile SWEEP = the d = 3 line-sweep kernel, SWEEP2 its two-line form,
+# else the tiled kernel with that tile (d <= 3 padded box, d = 4 line buffer)
 KERNELS = [
     (3, 6, 2, 1, SWEEP),
+    (3, 6, 2, 1, SWEEP2),
+    (3, 8, 2, 0, SWEEP2),
+    (3, 13, 1, 1, SWEEP2),
     (3, 6, 2, 1, 512),
     (2, 6, 3, 1, 256),
     (2, 6, 3, 0, 1024),
@@ -40,7 +43,8 @@ def _levels(h, dim):
 
 
 def _run(orc, dim, nr, nl, pde, tile, kind, scale, eps, nsteps=3):
-    kern = dict(stage_kernel=P.SG_STAGE_SWEEP, tile_points=0) if tile == SWEEP else dict(tile_points=tile)
+    kern = (dict(stage_kernel=P.SG_STAGE_SWEEP, tile_points=0) if tile == SWEEP else
+            dict(stage_kernel=P.SG_STAGE_SWEEP2, tile_points=0) if tile == SWEEP2 else dict(tile_points=tile))
     adv = (1.0, -0.7, 0.5, 2.0)[:dim]
     h = make(dim, nr, nl, pde, precision=P.SG_F32, exec=P.SG_BATCHED, eps=eps, dt_rule=P.SG_DT_CFL,
              cfl=0.45, adv_speed=list(adv) + [1.0] * (6 - dim), **kern)
@@ -90,7 +94,7 @@ def test_fp32_mixed_data_any_scale(sg, orc, kernel, scale):
 
 
 @pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-8])
-@pytest.mark.parametrize("kernel", KERNELS[:3], ids=lambda k: "d%d_nr%d_nl%d_pde%d_tp%d" % k)
+@pytest.mark.parametrize("kernel", KERNELS[:4] + KERNELS[5:6], ids=lambda k: "d%d_nr%d_nl%d_pde%d_tp%d" % k)
 def test_fp32_smooth_small_differences_small_eps(sg, orc, kernel, eps):
     # smooth data of amplitude 1e-2: neighbouring differences ~1e-4, smoothness terms ~1e-8,
     # their squared products far below the float normal range unless rescaled
@@ -101,9 +105,10 @@ def test_fp32_smooth_small_differences_small_eps(sg, orc, kernel, eps):
 
 @pytest.mark.parametrize("eps", [1e-6, 1e-8])
 @pytest.mark.parametrize("scale", [1.0, 1e3])
-def test_fp32_mixed_data_small_eps(sg, orc, scale, eps):
+@pytest.mark.parametrize("tile", [SWEEP, SWEEP2])
+def test_fp32_mixed_data_small_eps(sg, orc, scale, eps, tile):
     # jumps with a tiny eps: the smoothness terms of one interface span many decades
-    out = _run(orc, 3, 6, 2, 1, SWEEP, "mixed", scale, eps)
+    out = _run(orc, 3, 6, 2, 1, tile, "mixed", scale, eps)
     _check(*out, 3)
 
 

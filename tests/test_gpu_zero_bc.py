@@ -17,7 +17,7 @@ from _helpers import make, oracle_problem, random_grids, read_grids
 pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
-SWEEP = -1
+SWEEP, SWEEP2 = -1, -2
 Z, PER = P.SG_BC_ZERO, P.SG_BC_PERIODIC
 
 # (dim, nr, nl, pde, bc, exec, tile, dt_rule, steps)
@@ -42,7 +42,8 @@ def _levels(h, dim):
 def _run(orc, case, prec):
     dim, nr, nl, pde, bc, exe, tile, rule, nsteps = case
     adv = (1.0, -0.7, 0.5, 2.0)[:dim]
-    kern = dict(stage_kernel=P.SG_STAGE_SWEEP, tile_points=0) if tile == SWEEP else dict(tile_points=tile)
+    kern = (dict(stage_kernel=P.SG_STAGE_SWEEP, tile_points=0) if tile == SWEEP else
+            dict(stage_kernel=P.SG_STAGE_SWEEP2, tile_points=0) if tile == SWEEP2 else dict(tile_points=tile))
     h = make(dim, nr, nl, pde, precision=prec, exec=exe, bc=list(bc) + [PER] * (6 - dim),
              adv_speed=list(adv) + [1.0] * (6 - dim), dt_rule=rule, dt_coef=0.7, cfl=0.45, **kern)
     try:
@@ -83,7 +84,13 @@ def test_zero_bc_fp64_bitwise(sg, orc, case):
     assert np.array_equal(uhat, refhat), np.max(np.abs(uhat - refhat))
 
 
-@pytest.mark.parametrize("case", [c for c in CASES if c[0] <= 3], ids=_id)
+FP32_CASES = [c for c in CASES if c[0] <= 3] + [
+    (3, 8, 2, 1, (Z, Z, Z), P.SG_BATCHED, SWEEP2, 1, 2),
+    (3, 13, 1, 1, (Z, PER, Z), P.SG_BATCHED, SWEEP2, 1, 2),
+]
+
+
+@pytest.mark.parametrize("case", FP32_CASES, ids=_id)
 def test_zero_bc_fp32_within_tolerance(sg, orc, case):
     got, ref, steps, osteps, uhat, refhat, co, g0 = _run(orc, case, P.SG_F32)
     assert steps == osteps
