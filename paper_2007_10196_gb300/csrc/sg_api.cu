@@ -1102,6 +1102,7 @@ sg_status prolong_combine_fused_t(sg_ctx* h, CombineBuffers& cb, cudaStream_t st
         tab[g].n = gd.n[d - 1];
         tab[g].r = 1 << (h->nl - gd.lev[d - 1]);
         tab[g].coeff = gd.coeff;
+        tab[g].coeff_f = (float)gd.coeff;
     }
     SG_CUDA(cudaMemcpyAsync(cb.tab.p, host.data(), all_bytes, cudaMemcpyHostToDevice, st));
     const ProlongTask* dptab = reinterpret_cast<const ProlongTask*>(cb.tab.as<unsigned char>() + ptab_off);

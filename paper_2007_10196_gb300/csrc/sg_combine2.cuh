@@ -52,8 +52,8 @@ struct InterpWin2 {
         d2 = sg_fma2(Ep, sg_f2(1.f / 12.f), sg_mul2(sg_f2(-1.f / 6.f), E1));
     }
     // w2 + (s/2) N(s) / D(s); D >= 1/16 (see Weno<float>::interp), inside __fdividef's range
+    // (at s = 0 the same value as the node itself: 0 x finite quotient added to w2)
     __device__ __forceinline__ float2 eval(float s) const {
-        if (s == 0.f) return w2;
         const float2 S = sg_f2(s);
         const float2 N = sg_fma2(sg_fma2(sg_fma2(n3, S, n2), S, n1), S, n0);
         const float2 D = sg_fma2(sg_fma2(d2, S, d1), S, d0);
@@ -84,7 +84,7 @@ struct CombineAcc2 {
 };
 
 template <int J, int CY, bool EXACT>
-__global__ void __launch_bounds__(32 * CY) sg_combine_last_axis_f32x2_kernel(const CombineGrid* __restrict__ tab, int G,
+__global__ void __launch_bounds__(32 * CY, 2) sg_combine_last_axis_f32x2_kernel(const CombineGrid* __restrict__ tab, int G,
                                                                          double* __restrict__ uhat, long long below,
                                                                          int nf, double eps, int lagrange,
                                                                          int zero_last) {
@@ -118,35 +118,65 @@ __global__ void __launch_bounds__(32 * CY) sg_combine_last_axis_f32x2_kernel(con
             const long long lo = 2 * pr;
             const bool two = lo + 1 < below;
             CombineAcc2 acc[J];
-            for (int g = 0; g < G; ++g) {
-                const CombineGrid cg = tab[g];
-                const float* col = (const float*)cg.src + lo;
-                const int n = cg.n, r = cg.r;
-                const float cT = (float)cg.coeff;
+            // one grid's last axis for this column pair
+            struct View {
+                const float* col;
+                int n, r;
+                float c;
+                bool vec;
+            };
+            auto view = [&](int g) -> View {
+                const CombineGrid& cg = tab[g];
+                View v;
+                v.col = (const float*)cg.src + lo;
+                v.n = cg.n;
+                v.r = cg.r;
+                v.c = cg.coeff_f;
                 // both columns with one 8-byte load where the rows keep them 8-byte aligned
-                const bool vec = even && ((reinterpret_cast<unsigned long long>(cg.src) & 7) == 0);
-                auto row = [&](int c) -> float2 {  // coarse row c of the last axis (c in [-2, n + 2])
-                    if (zero_last && (c < 0 || c >= n)) return make_float2(0.f, 0.f);
-                    const float* p = col + (long long)wrap_index(c, n) * below;
-                    if (vec) return *reinterpret_cast<const float2*>(p);
-                    return make_float2(p[0], two ? p[1] : 0.f);
-                };
-                if (r == 1) {  // last axis already fine: values at coincident nodes
+                v.vec = even && ((reinterpret_cast<unsigned long long>(cg.src) & 7) == 0);
+                return v;
+            };
+            auto row = [&](const View& v, int c) -> float2 {  // coarse row c (c in [-2, n + 2])
+                if (zero_last && (c < 0 || c >= v.n)) return make_float2(0.f, 0.f);
+                const float* p = v.col + (long long)wrap_index(c, v.n) * below;
+                if (v.vec) return *reinterpret_cast<const float2*>(p);
+                return make_float2(p[0], two ? p[1] : 0.f);
+            };
+            // the first five rows a grid needs: around the chunk's first centre (r >= 2) or the
+            // chunk's first five fine nodes (r = 1)
+            auto first = [&](const View& v, float2 (&w)[5]) {
+                const int c0 = v.r == 1 ? j0 + 2 : c_tab[(__ffs(v.r) - 1) * JB + threadIdx.y * J];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) w[k] = (v.r == 1 && j0 + k >= nf) ? make_float2(0.f, 0.f) : row(v, c0 - 2 + k);
+            };
+            View nv = view(0);
+            float2 nw[5];
+            first(nv, nw);
+            for (int g = 0; g < G; ++g) {
+                const View v = nv;
+                float2 w[5];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) w[k] = nw[k];
+                if (g + 1 < G) {  // the next grid's first rows are in flight during this grid's work
+                    nv = view(g + 1);
+                    first(nv, nw);
+                }
+                if (v.r == 1) {  // last axis already fine: values at coincident nodes
 #pragma unroll
                     for (int j = 0; j < J; ++j)
-                        if (j0 + j < nf) acc[j].template add<EXACT>(cT, row(j0 + j));
+                        if (j0 + j < nf) acc[j].template add<EXACT>(v.c, j < 5 ? w[j] : row(v, j0 + j));
                     continue;
                 }
-                const int lr = __ffs(r) - 1;  // r = 2^lr: this warp's centres and offsets
+                const int lr = __ffs(v.r) - 1;  // r = 2^lr: this warp's centres and offsets
                 const int* ct = c_tab + lr * JB + threadIdx.y * J;
                 const float* sv = s_tab + lr * JB + threadIdx.y * J;
                 int cur = ct[0];
                 InterpWin2 W;
-                W.w0 = row(cur - 2);
-                W.w1 = row(cur - 1);
-                W.w2 = row(cur);
-                W.w3 = row(cur + 1);
-                W.w4 = row(cur + 2);
+                W.w0 = w[0];
+                W.w1 = w[1];
+                W.w2 = w[2];
+                W.w3 = w[3];
+                W.w4 = w[4];
                 W.prepare(e4, lagrange);
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
@@ -157,11 +187,11 @@ __global__ void __launch_bounds__(32 * CY) sg_combine_last_axis_f32x2_kernel(con
                         W.w1 = W.w2;
                         W.w2 = W.w3;
                         W.w3 = W.w4;
-                        W.w4 = row(ic + 2);
+                        W.w4 = row(v, ic + 2);
                         W.prepare(e4, lagrange);
                         cur = ic;
                     }
-                    acc[j].template add<EXACT>(cT, W.eval(sv[j]));
+                    acc[j].template add<EXACT>(v.c, W.eval(sv[j]));
                 }
             }
 #pragma unroll

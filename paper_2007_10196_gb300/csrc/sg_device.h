@@ -117,6 +117,7 @@ struct CombineGrid {
     int n;            // coarse points of the last axis
     int r;            // refinement ratio 2^{N_L - l_{d-1}} of the last axis
     double coeff;     // combination coefficient
+    float coeff_f;    // the same as a float (exact: |c| = C(d-1, q) <= 10)
 };
 
 // One grid's share of a prolongation pass over many grids (Step 3, axes 0..d-2): the array

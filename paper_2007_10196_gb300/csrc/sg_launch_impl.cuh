@@ -160,8 +160,11 @@ int prepare_sweep2(size_t smem) {
     } else {
         const void* k0 = (const void*)sg_stage_sweep3x2_kernel<false>;
         const void* k1 = (const void*)sg_stage_sweep3x2_kernel<true>;
+        // the whole unified L1/shared array as shared memory: 7 blocks of ~30 KB per SM
         if (cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-            cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+            cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaFuncSetAttribute(k0, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess ||
+            cudaFuncSetAttribute(k1, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }

@@ -12,6 +12,19 @@
 
 #define SG_NT3H 96
 
+// weno_scale3 for two lanes: the scale per lane, the multiplications packed
+__device__ __forceinline__ void weno_scale3x2(float2& e0, float2& e1, float2& e2) {
+    const float mx = sg_min3(e0.x, e1.x, e2.x), my = sg_min3(e0.y, e1.y, e2.y);
+    const float2 sc = make_float2(__uint_as_float(0x7f000000u - (__float_as_uint(mx) & 0x7f800000u)),
+                                  __uint_as_float(0x7f000000u - (__float_as_uint(my) & 0x7f800000u)));
+    e0 = sg_mul2(e0, sc);
+    e1 = sg_mul2(e1, sc);
+    e2 = sg_mul2(e2, sc);
+    e0 = make_float2(fminf(e0.x, 0x1p20f), fminf(e0.y, 0x1p20f));
+    e1 = make_float2(fminf(e1.x, 0x1p20f), fminf(e1.y, 0x1p20f));
+    e2 = make_float2(fminf(e2.x, 0x1p20f), fminf(e2.y, 0x1p20f));
+}
+
 // SweepSide<float> for two lines: lane x is one line, lane y the other; the same operations
 // lane by lane (the rescaling of the smoothness terms per lane).
 struct SweepSide2 {
@@ -54,8 +67,7 @@ struct SweepSide2 {
             float2 e0 = sg_fma2(s0, s0, T0);
             float2 e1 = sg_fma2(s1, s1, T1);
             float2 e2 = sg_fma2(s2, s2, T2);
-            weno_scale3(e0.x, e1.x, e2.x);
-            weno_scale3(e0.y, e1.y, e2.y);
+            weno_scale3x2(e0, e1, e2);
             E0 = sg_mul2(e0, e0);
             E1 = sg_mul2(e1, e1);
             E2 = sg_mul2(e2, e2);
@@ -66,13 +78,14 @@ struct SweepSide2 {
     }
 };
 
-// fhat = fhat^+ + fhat^- of both lines (each den in [5/3, 2^81]: __fdividef's accurate range)
+// fhat = fhat^+ + fhat^- of both lines (each den in [5/3, 2^81], normal: the approximate
+// reciprocal is within about an ulp)
 __device__ __forceinline__ float2 sweep_flux2(const SweepSide2& P, const SweepSide2& M, int linear) {
     float2 np, dp, nm, dm;
     P.value(linear, np, dp);
     M.value(linear, nm, dm);
-    const float2 rp = make_float2(__fdividef(1.f, dp.x), __fdividef(1.f, dp.y));
-    const float2 rm = make_float2(__fdividef(1.f, dm.x), __fdividef(1.f, dm.y));
+    const float2 rp = make_float2(sg_rcp(dp.x), sg_rcp(dp.y));
+    const float2 rm = make_float2(sg_rcp(dm.x), sg_rcp(dm.y));
     return sg_add2(sg_add2(P.c, M.c), sg_fma2(np, rp, sg_mul2(nm, rm)));
 }
 
@@ -203,20 +216,21 @@ __global__ void __launch_bounds__(SG_NT3H, 6) sg_stage_sweep3x2_kernel(const Sta
                 put(b + 2, v.z);
                 if (!(code & (2 << 16))) put(b + 3, v.w);
             };
-            // up to five chunks per thread, three loads in flight, then two
-            for (int t0 = tid; t0 < ntask; t0 += 3 * SG_NT3H) {
-                int gg[3], cc[3];
-                float4 vv[3];
+            // up to five chunks per thread (448 for a full tile), three loads in flight at a time
+            constexpr int NU = 3;
+            for (int t0 = tid; t0 < ntask; t0 += NU * SG_NT3H) {
+                int gg[NU], cc[NU];
+                float4 vv[NU];
 #pragma unroll
-                for (int u = 0; u < 3; ++u) {
+                for (int u = 0; u < NU; ++u) {
                     const int t = t0 + u * SG_NT3H;
                     cc[u] = t < ntask ? chunk(t, gg[u]) : -1;
                 }
 #pragma unroll
-                for (int u = 0; u < 3; ++u)
+                for (int u = 0; u < NU; ++u)
                     if (cc[u] >= 0) vv[u] = fetch(cc[u], gg[u]);
 #pragma unroll
-                for (int u = 0; u < 3; ++u)
+                for (int u = 0; u < NU; ++u)
                     if (cc[u] >= 0) store(cc[u], vv[u]);
             }
         } else {

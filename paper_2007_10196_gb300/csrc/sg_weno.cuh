@@ -146,6 +146,13 @@ __device__ __forceinline__ float block_max(float v, float* red) {
     return v;
 }
 
+// 1/x to about one ulp (the hardware approximation; x normal)
+__device__ __forceinline__ float sg_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Packed two-lane FP32 arithmetic (one instruction for both lanes; sm_100 and later), used by
 // the kernels that carry two independent columns or lines per thread.
 __device__ __forceinline__ float2 sg_f2(float a) { return make_float2(a, a); }
@@ -266,8 +273,13 @@ __device__ __forceinline__ float sg_eps4<float>(double eps) { return fmaxf((floa
 
 // e_k <- min(e_k 2^-floor(log2 min_j e_j), 2^20); the scale is built from the exponent bits of
 // the smallest e (normal: e >= 4 eps >= 2^-100), so the division is exact.
+__device__ __forceinline__ float sg_min3(float a, float b, float c) {  // three-input min (sm_100+)
+    float m;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(m) : "f"(a), "f"(b), "f"(c));
+    return m;
+}
 __device__ __forceinline__ void weno_scale3(float& e0, float& e1, float& e2) {
-    const float m = fminf(e0, fminf(e1, e2));
+    const float m = sg_min3(e0, e1, e2);
     const float sc = __uint_as_float(0x7f000000u - (__float_as_uint(m) & 0x7f800000u));
     e0 = fminf(e0 * sc, 0x1p20f);
     e1 = fminf(e1 * sc, 0x1p20f);
