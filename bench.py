@@ -74,6 +74,8 @@ def _env_rank():
 
 
 N_MEMBERS = 256
+# --stage-kernel: sg_params.stage_kernel by name (0 = SG_STAGE_AUTO, 2 = SG_STAGE_SWEEP, ...)
+STAGE_KERNELS = {"auto": 0, "sweep": 2, "sweep2": 3}
 
 
 def _members(rank):
@@ -94,6 +96,41 @@ def _batch_points(members):
                     grids += 1
         out.append((grids, tot))
     return out
+
+
+# Algorithmic work of the prolongation + combination step (Step 3, Eqs. 8-15), FP32 arithmetic
+# (FMA = 2 FLOP): one interpolation at a fine node from a prepared window -- the cubic N(s) and
+# quadratic D(s) by Horner (10), their quotient (1), w2 + (s/2) q (3) -- is 14 FLOP; preparing
+# a window (the differences, the three smoothness indicators of Eq. 10, the weights' factors and
+# the coefficients of N and D) is 60 FLOP per coarse node and line; adding c_g v into the sum is
+# 2 FLOP per grid and finest node.  Bytes: Û is written once, 8 B per finest node.
+FLOP_INTERP, FLOP_PREPARE, FLOP_ACCUM = 14, 60, 2
+BYTES_PER_FINEST_POINT = 8
+
+
+def combine_work(members):
+    """(finest points, FLOPs) of Step 3 over the members: per grid, every prolonged axis k < d-1
+    interpolates each fine node of each line and prepares each coarse node once per line; the
+    last axis does so at every finest node (grids whose last axis is coarse) and adds c_g v."""
+    pts, flops = 0, 0
+    for m in members:
+        Nf = m.nr << m.nl
+        pts += Nf ** 3
+        for q in range(3):
+            s = m.nl - q
+            for l0 in range(s + 1):
+                for l1 in range(s - l0 + 1):
+                    n = [m.nr << l0, m.nr << l1, m.nr << (s - l0 - l1)]
+                    cur = list(n)
+                    for k in range(2):
+                        if n[k] < Nf:
+                            lines = (cur[0] * cur[1] * cur[2]) // cur[k]
+                            flops += lines * (Nf * FLOP_INTERP + n[k] * FLOP_PREPARE)
+                            cur[k] = Nf
+                    if n[2] < Nf:
+                        flops += Nf * Nf * (Nf * FLOP_INTERP + n[2] * FLOP_PREPARE)
+                    flops += Nf ** 3 * FLOP_ACCUM
+    return pts, flops
 
 
 # ------------------------------------------------------------------------------------------
@@ -403,7 +440,8 @@ def run_ours(args, rank, world, local_rank):
     with torch.cuda.stream(stream):
         for m in members:
             h = P.create(3, m.nr, m.nl, P.SG_PDE_BURGERS, precision=P.SG_F32, exec=P.SG_BATCHED,
-                         dt_rule=P.SG_DT_CFL, cfl=inputs.BATCH_CFL, cuda_stream=stream.cuda_stream)
+                         dt_rule=P.SG_DT_CFL, cfl=inputs.BATCH_CFL, cuda_stream=stream.cuda_stream,
+                         stage_kernel=STAGE_KERNELS[args.stage_kernel])
             hs.append(h)
         batch = P.sg_batch_create(hs)
     ics = [(0.5, m.a, math.pi / 2, 0.0) for m in members]
@@ -519,6 +557,16 @@ def run_ours(args, rank, world, local_rank):
     achieved = point_stages * FLOPS_PER_POINT_STAGE_3D / (stage_ms / 1e3) / 1e12
     hbm_gbs = upd_per_pass * args.steps * BYTES_PER_POINT_STEP / (stage_ms / 1e3) / 1e9
     traffic = _stage_traffic(kname, point_stages / max(stage_launches, 1))
+    # Step 3 (prolongation + signed combination of every member), timed by the events around it
+    fpts, fflops = combine_work(members)
+    comb_s = statistics.mean(comb_ms) / 1e3
+    comb_gbs = fpts * BYTES_PER_FINEST_POINT / comb_s / 1e9
+    comb_tf = fflops / comb_s / 1e12
+    roof_comb = {"finest_points": fpts, "bytes_per_finest_point": BYTES_PER_FINEST_POINT, "flops": fflops,
+                 "ms": comb_s * 1e3, "achieved_gbs": comb_gbs, "hbm_frac": comb_gbs / float(peaks.get("hbm_gbs", 6800.0)),
+                 "achieved_tflops": comb_tf, "alu_frac": comb_tf / alu_peak,
+                 "share_of_pass": statistics.mean(comb_ms) / mean_ms,
+                 "kernels": "sg_prolong_multi_kernel<float,8>, sg_combine_last_axis_f32x2_kernel"}
     clocks = clk.summary()
     cpu = None
     if pool is not None:
@@ -546,6 +594,7 @@ def run_ours(args, rank, world, local_rank):
         "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
                 "frac": hbm_gbs / float(peaks.get("hbm_gbs", 6800.0)), "peak_source": src,
                 "bytes_per_point_step": BYTES_PER_POINT_STEP},
+        "roofline_combine": roof_comb,
         "breakdown_ms": {"step_to_t_end": statistics.mean(step_ms), "stage_kernels": stage_ms / args.steps,
                          "stage_launches": stage_launches // args.steps,
                          "prolong_combine": statistics.mean(comb_ms)},
@@ -720,6 +769,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-plain comparison")
     ap.add_argument("--members", type=int, default=256,
                     help="first M members of the batch only (small cases for profiling)")
+    ap.add_argument("--stage-kernel", choices=sorted(STAGE_KERNELS), default="auto",
+                    help="the stage kernel of the batch (default: the autotuner's choice)")
     ap.add_argument("--workload", choices=["burgers3d_batch"] + sorted(RELAX), default="burgers3d_batch",
                     help="the benchmark batch (default), or Example 5 (Vlasov-Boltzmann) in 2-D or 4-D")
     args = ap.parse_args()
