@@ -15,6 +15,7 @@
 // the same columns, so the repeated window loads hit L1 or L2 instead of DRAM.
 #pragma once
 #include "sg_aux.cuh"
+#include "sg_sweep2.cuh"  // weno_scale3x2
 
 // InterpWin<float> for two columns: the same formulas lane by lane (the rescaling of the
 // smoothness terms, weno_scale3, works per lane).
@@ -32,8 +33,7 @@ struct InterpWin2 {
             float2 e0 = sg_fma2(sg_mul2(c13, t0), t0, sg_fma2(s0, s0, ep));
             float2 e1 = sg_fma2(sg_mul2(c13, t1), t1, sg_fma2(s1, s1, ep));
             float2 e2 = sg_fma2(sg_mul2(c13, t2), t2, sg_fma2(s2, s2, ep));
-            weno_scale3(e0.x, e1.x, e2.x);
-            weno_scale3(e0.y, e1.y, e2.y);
+            weno_scale3x2(e0, e1, e2);
             const float2 q0 = sg_mul2(e0, e0), q1 = sg_mul2(e1, e1), q2 = sg_mul2(e2, e2);
             E0 = sg_mul2(q1, q2);
             E1 = sg_mul2(q0, q2);
@@ -52,13 +52,14 @@ struct InterpWin2 {
         d2 = sg_fma2(Ep, sg_f2(1.f / 12.f), sg_mul2(sg_f2(-1.f / 6.f), E1));
     }
     // w2 + (s/2) N(s) / D(s); D >= 1/16 (see Weno<float>::interp), inside __fdividef's range
-    // (at s = 0 the same value as the node itself: 0 x finite quotient added to w2)
-    __device__ __forceinline__ float2 eval(float s) const {
-        const float2 S = sg_f2(s);
+    // sh = (s, s, s/2, s/2) (at s = 0 the value of the node itself: 0 x finite quotient added to
+    // w2); D >= 1/16 is normal, so the hardware reciprocal is within about an ulp
+    __device__ __forceinline__ float2 eval(const float4& sh) const {
+        const float2 S = make_float2(sh.x, sh.y);
         const float2 N = sg_fma2(sg_fma2(sg_fma2(n3, S, n2), S, n1), S, n0);
         const float2 D = sg_fma2(sg_fma2(d2, S, d1), S, d0);
-        const float2 q = make_float2(__fdividef(N.x, D.x), __fdividef(N.y, D.y));
-        return sg_fma2(sg_f2(0.5f * s), q, w2);
+        const float2 q = sg_mul2(N, make_float2(sg_rcp(D.x), sg_rcp(D.y)));
+        return sg_fma2(make_float2(sh.z, sh.w), q, w2);
     }
 };
 
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(32 * CY, 2) sg_combine_last_axis_f32x2_kernel(
     const float e4 = sg_eps4<float>(eps);
     constexpr int JB = J * CY;  // fine nodes of the last axis per block
     // centre and offset s of the block's JB fine nodes for every ratio r = 2^lr (lr <= 16)
-    __shared__ float s_tab[17 * JB];
+    __shared__ float4 s_tab[17 * JB];  // (s, s, s/2, s/2): both lanes of a packed operand
     __shared__ int c_tab[17 * JB];
     const int ngroups = (nf + JB - 1) / JB;
     const long long npairs = (below + 1) >> 1;
@@ -103,13 +104,15 @@ __global__ void __launch_bounds__(32 * CY, 2) sg_combine_last_axis_f32x2_kernel(
             const int lr = t / JB, jf = jb + (t - lr * JB), r = 1 << lr;
             const int i = jf >> lr, m = jf & (r - 1);  // jf = i r + m; centre i or i + 1
             const float inv_r = pow2_neg<float>(lr);
+            float sv;
             if (2 * m < r) {
                 c_tab[t] = i;
-                s_tab[t] = (float)m * inv_r;
+                sv = (float)m * inv_r;
             } else {
                 c_tab[t] = i + 1;
-                s_tab[t] = (float)(m - r) * inv_r;
+                sv = (float)(m - r) * inv_r;
             }
+            s_tab[t] = make_float4(sv, sv, 0.5f * sv, 0.5f * sv);
         }
         __syncthreads();
         const int j0 = jb + threadIdx.y * J;  // this warp's chunk
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(32 * CY, 2) sg_combine_last_axis_f32x2_kernel(
                 }
                 const int lr = __ffs(v.r) - 1;  // r = 2^lr: this warp's centres and offsets
                 const int* ct = c_tab + lr * JB + threadIdx.y * J;
-                const float* sv = s_tab + lr * JB + threadIdx.y * J;
+                const float4* sv = s_tab + lr * JB + threadIdx.y * J;
                 int cur = ct[0];
                 InterpWin2 W;
                 W.w0 = w[0];
