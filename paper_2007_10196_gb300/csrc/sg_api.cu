@@ -5,6 +5,7 @@
 #include <array>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -1071,30 +1072,39 @@ sg_status prolong_combine_fused_t(sg_ctx* h, CombineBuffers& cb, cudaStream_t st
         size_t first;
         int ntasks;
         long long units;
+        bool pairs;  // FP32 tasks whose adjacent columns pair up (sg_prolong_multi_x2_kernel)
     };
     std::vector<Launch1> launches;  // per group, per pass, in order
     size_t ti = 0;
     for (const auto& gp : passes)
         for (const auto& ps : gp) {  // passes in axis order: a grid's axes run 0, 1, ..., d-2
-            long long unit0 = 0;
-            const size_t first = ti;
-            for (const Plan& pl : ps) {
-                const GridDesc& gd = h->hgrids[pl.g];
-                ProlongTask& t = ptab[ti++];
-                t.in = pl.in_off < 0 ? (const void*)gd.u0 : (const void*)(intp + pl.in_off);
-                t.out = pl.out_pool ? (void*)(poolp + pl.out_off) : (void*)(intp + pl.out_off);
-                t.unit0 = unit0;
-                t.below = (int)pl.below;
-                t.above = (int)pl.above;
-                t.n = pl.n;
-                t.nf = (int)Nf;
-                t.r = pl.r;
-                t.zero_bc = pl.zero;
-                t.below_mag = sg_div_magic64((unsigned)pl.below);
-                t.nch_mag = sg_div_magic64((unsigned)nch);
-                unit0 += pl.below * nch * pl.above;
+            // the pass's tasks in two launches: those whose columns pair up, then the others
+            for (int kind = 0; kind < 2; ++kind) {
+                long long unit0 = 0;
+                const size_t first = ti;
+                for (const Plan& pl : ps) {
+                    const GridDesc& gd = h->hgrids[pl.g];
+                    const void* in = pl.in_off < 0 ? (const void*)gd.u0 : (const void*)(intp + pl.in_off);
+                    void* out = pl.out_pool ? (void*)(poolp + pl.out_off) : (void*)(intp + pl.out_off);
+                    const bool pairs = sizeof(T) == 4 && pl.below % 2 == 0 &&
+                                       ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 7) == 0;
+                    if (pairs != (kind == 0)) continue;
+                    ProlongTask& t = ptab[ti++];
+                    t.in = in;
+                    t.out = out;
+                    t.unit0 = unit0;
+                    t.below = (int)pl.below;
+                    t.above = (int)pl.above;
+                    t.n = pl.n;
+                    t.nf = (int)Nf;
+                    t.r = pl.r;
+                    t.zero_bc = pl.zero;
+                    t.below_mag = sg_div_magic64((unsigned)pl.below);
+                    t.nch_mag = sg_div_magic64((unsigned)nch);
+                    unit0 += pl.below * nch * pl.above;
+                }
+                if (ti > first) launches.push_back({first, (int)(ti - first), unit0, kind == 0});
             }
-            if (ti > first) launches.push_back({first, (int)(ti - first), unit0});
         }
     for (int g = 0; g < h->G; ++g) {
         const GridDesc& gd = h->hgrids[g];
@@ -1107,7 +1117,10 @@ sg_status prolong_combine_fused_t(sg_ctx* h, CombineBuffers& cb, cudaStream_t st
     SG_CUDA(cudaMemcpyAsync(cb.tab.p, host.data(), all_bytes, cudaMemcpyHostToDevice, st));
     const ProlongTask* dptab = reinterpret_cast<const ProlongTask*>(cb.tab.as<unsigned char>() + ptab_off);
     for (const Launch1& L : launches) {
-        SG_CUDA(sg::Launch<T>::prolong_multi(dptab + L.first, L.ntasks, L.units, h->prm.eps, h->prm.prolong, st));
+        if (L.pairs)
+            SG_CUDA(sg::Launch<T>::prolong_multi_pairs(dptab + L.first, L.ntasks, L.units, h->prm.eps, h->prm.prolong, st));
+        else
+            SG_CUDA(sg::Launch<T>::prolong_multi(dptab + L.first, L.ntasks, L.units, h->prm.eps, h->prm.prolong, st));
         h->launches += 1;
     }
     bool exact = true;  // |c| = C(d-1, q) a power of two for every grid (d <= 3)

@@ -214,3 +214,78 @@ __global__ void __launch_bounds__(32 * CY, 2) sg_combine_last_axis_f32x2_kernel(
         }
     }
 }
+
+// sg_prolong_multi_kernel for FP32 tasks whose lines come in adjacent pairs (below even, 8-byte
+// aligned arrays): thread p takes units 2p and 2p + 1 -- the same chunk of two adjacent columns
+// -- and runs the window arithmetic once for both in packed f32x2 form (InterpWin2), with
+// 8-byte loads and stores.  The tasks' unit ranges are even-sized, so a pair never straddles
+// two tasks.
+template <int J>
+__global__ void __launch_bounds__(256) sg_prolong_multi_x2_kernel(const ProlongTask* __restrict__ tasks, int ntasks,
+                                                                  long long nunits, double eps, int lagrange) {
+    const float e4 = sg_eps4<float>(eps);
+    const long long npairs = nunits >> 1;
+    for (long long pp = blockIdx.x * 256LL + threadIdx.x; pp < npairs; pp += gridDim.x * 256LL) {
+        const long long u = 2 * pp;
+        int a = 0, b = ntasks - 1;  // the last task with unit0 <= u
+        while (a < b) {
+            const int mid = (a + b + 1) >> 1;
+            if (tasks[mid].unit0 <= u) a = mid;
+            else b = mid - 1;
+        }
+        const ProlongTask& tk = tasks[a];
+        const unsigned v = (unsigned)(u - tk.unit0);
+        const unsigned below = (unsigned)tk.below;
+        const int nchunks = (tk.nf + J - 1) / J;
+        const unsigned q = div_mag(v, below, tk.below_mag);
+        const unsigned lo = v - q * below;  // even: below is even and v is even
+        const unsigned hi = div_mag(q, (unsigned)nchunks, tk.nch_mag);
+        const int j0 = (int)(q - hi * (unsigned)nchunks) * J;
+        const int n = tk.n, nf = tk.nf, r = tk.r, lr = __ffs(r) - 1;
+        const float inv_r = pow2_neg<float>(lr);
+        const float* col = (const float*)tk.in + (long long)hi * below * n + lo;
+        float* ocol = (float*)tk.out + (long long)hi * below * nf + lo;
+        auto centre = [&](int jf, int& ic, float& s) {  // as fine_to_coarse
+            const int i = jf >> lr, m = jf & (r - 1);
+            if (2 * m < r) {
+                ic = i;
+                s = (float)m * inv_r;
+            } else {
+                ic = i + 1;
+                s = (float)(m - r) * inv_r;
+            }
+        };
+        auto at = [&](int c) -> float2 {  // both columns' coarse value c, c in [-2, n + 2]
+            if (tk.zero_bc && (c < 0 || c >= n)) return make_float2(0.f, 0.f);
+            return *reinterpret_cast<const float2*>(col + (long long)wrap_index(c, n) * below);
+        };
+        int cur;
+        float s0;
+        centre(j0, cur, s0);
+        InterpWin2 W;
+        W.w0 = at(cur - 2);
+        W.w1 = at(cur - 1);
+        W.w2 = at(cur);
+        W.w3 = at(cur + 1);
+        W.w4 = at(cur + 2);
+        W.prepare(e4, lagrange);
+#pragma unroll 1
+        for (int j = 0; j < J; ++j) {
+            const int jf = j0 + j;
+            if (jf >= nf) break;
+            int ic;
+            float s;
+            centre(jf, ic, s);
+            if (ic != cur) {  // centres advance by one coarse node at a time (r >= 2)
+                W.w0 = W.w1;
+                W.w1 = W.w2;
+                W.w2 = W.w3;
+                W.w3 = W.w4;
+                W.w4 = at(ic + 2);
+                W.prepare(e4, lagrange);
+                cur = ic;
+            }
+            *reinterpret_cast<float2*>(ocol + (long long)jf * below) = W.eval(make_float4(s, s, 0.5f * s, 0.5f * s));
+        }
+    }
+}

@@ -73,6 +73,10 @@ struct Launch {
     // [0, nunits)), J = 8 fine nodes per unit.
     static cudaError_t prolong_multi(const ProlongTask* tasks, int ntasks, long long nunits, double eps, int lagrange,
                                      cudaStream_t s);
+    // The same for tasks whose lines pair up (below even, 8-byte aligned arrays; FP32): two
+    // adjacent columns per thread in packed arithmetic.  FP64: the same as prolong_multi.
+    static cudaError_t prolong_multi_pairs(const ProlongTask* tasks, int ntasks, long long nunits, double eps,
+                                           int lagrange, cudaStream_t s);
     // uhat = sum_g c_g P_{d-1} I_g over the G entries of tab (device array), written once.
     // exact_coeffs: every |c_g| is a power of two (products c_g v are exact in the FP32 sum)
     static cudaError_t combine_last_axis(const CombineGrid* tab, int G, double* uhat, long long below, int nf,

@@ -325,6 +325,19 @@ cudaError_t Launch<T>::prolong_multi(const ProlongTask* tasks, int ntasks, long 
 }
 
 template <class T>
+cudaError_t Launch<T>::prolong_multi_pairs(const ProlongTask* tasks, int ntasks, long long nunits, double eps,
+                                           int lagrange, cudaStream_t s) {
+    if constexpr (sizeof(T) != 4) {
+        return prolong_multi(tasks, ntasks, nunits, eps, lagrange, s);
+    } else {
+        if (ntasks < 1 || nunits < 2) return cudaSuccess;
+        const unsigned nb = (unsigned)std::min<long long>((nunits / 2 + 255) / 256, 1LL << 22);
+        sg_prolong_multi_x2_kernel<8><<<nb, 256, 0, s>>>(tasks, ntasks, nunits, eps, lagrange);
+        return cudaGetLastError();
+    }
+}
+
+template <class T>
 cudaError_t Launch<T>::combine_last_axis(const CombineGrid* tab, int G, double* uhat, long long below, int nf,
                                          int exact_coeffs, int zero_last,
                                          double eps, int lagrange, cudaStream_t s) {
