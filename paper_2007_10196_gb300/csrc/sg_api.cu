@@ -1128,9 +1128,11 @@ sg_status prolong_combine_fused_t(sg_ctx* h, CombineBuffers& cb, cudaStream_t st
         const double a = std::fabs(h->coeff[g]);
         exact = exact && a >= 1.0 && std::ldexp(1.0, std::ilogb(a)) == a;
     }
+    bool aligned = (below & 1) == 0;  // both columns of every pair with one 8-byte load
+    for (int g = 0; g < h->G; ++g) aligned = aligned && (reinterpret_cast<uintptr_t>(tab[g].src) & 7) == 0;
     SG_CUDA(sg::Launch<T>::combine_last_axis(cb.tab.as<CombineGrid>(), h->G, h->uhat.as<double>(), below, (int)Nf,
-                                             exact ? 1 : 0, zero_axis(h, d - 1) ? 1 : 0, h->prm.eps,
-                                             h->prm.prolong, st));
+                                             exact ? 1 : 0, zero_axis(h, d - 1) ? 1 : 0, aligned ? 1 : 0,
+                                             h->prm.eps, h->prm.prolong, st));
     h->launches += 1;
     if (sync) SG_CUDA(cudaStreamSynchronize(st));
     h->combined = true;

@@ -18,7 +18,8 @@
 #include "sg_sweep2.cuh"  // weno_scale3x2
 
 // InterpWin<float> for two columns: the same formulas lane by lane (the rescaling of the
-// smoothness terms, weno_scale3, works per lane).
+// smoothness terms, weno_scale3, works per lane).  The denominator coefficients are kept
+// doubled (d = 2 D, exact), so that eval needs the offset s only once per lane.
 struct InterpWin2 {
     float2 w0, w1, w2, w3, w4;
     float2 n0, n1, n2, n3, d0, d1, d2;
@@ -47,76 +48,121 @@ struct InterpWin2 {
         n1 = sg_fma2(Bp, sg_f2(1.f / 6.f), sg_fma2(sg_sub2(A2, A0), sg_f2(0.25f), sg_mul2(sg_f2(2.f / 3.f), B1)));
         n2 = sg_fma2(sg_sub2(B2, B0), sg_f2(0.25f), sg_fma2(Ap, sg_f2(1.f / 12.f), sg_mul2(sg_f2(-1.f / 6.f), A1)));
         n3 = sg_fma2(Bp, sg_f2(1.f / 12.f), sg_mul2(sg_f2(-1.f / 6.f), B1));
-        d0 = sg_fma2(Ep, sg_f2(1.f / 6.f), sg_mul2(sg_f2(2.f / 3.f), E1));
-        d1 = sg_mul2(sg_sub2(E2, E0), sg_f2(0.25f));
-        d2 = sg_fma2(Ep, sg_f2(1.f / 12.f), sg_mul2(sg_f2(-1.f / 6.f), E1));
+        d0 = sg_fma2(Ep, sg_f2(1.f / 3.f), sg_mul2(sg_f2(4.f / 3.f), E1));
+        d1 = sg_mul2(sg_sub2(E2, E0), sg_f2(0.5f));
+        d2 = sg_fma2(Ep, sg_f2(1.f / 6.f), sg_mul2(sg_f2(-1.f / 3.f), E1));
     }
-    // w2 + (s/2) N(s) / D(s); D >= 1/16 (see Weno<float>::interp), inside __fdividef's range
-    // sh = (s, s, s/2, s/2) (at s = 0 the value of the node itself: 0 x finite quotient added to
-    // w2); D >= 1/16 is normal, so the hardware reciprocal is within about an ulp
-    __device__ __forceinline__ float2 eval(const float4& sh) const {
-        const float2 S = make_float2(sh.x, sh.y);
+    // w2 + s N(s) / d(s) = w2 + (s/2) N(s) / D(s); D >= 1/16 (see Weno<float>::interp), so
+    // d >= 1/8 is normal and the hardware reciprocal is within about an ulp.  S = (s, s); at
+    // s = 0 the value of the node itself (0 x a finite quotient added to w2).
+    __device__ __forceinline__ float2 eval(float2 S) const {
         const float2 N = sg_fma2(sg_fma2(sg_fma2(n3, S, n2), S, n1), S, n0);
         const float2 D = sg_fma2(sg_fma2(d2, S, d1), S, d0);
         const float2 q = sg_mul2(N, make_float2(sg_rcp(D.x), sg_rcp(D.y)));
-        return sg_fma2(make_float2(sh.z, sh.w), q, w2);
+        return sg_fma2(S, q, w2);
+    }
+    // the window moved by one coarse node: v is the new last value
+    __device__ __forceinline__ void shift(float2 v) {
+        w0 = w1;
+        w1 = w2;
+        w2 = w3;
+        w3 = w4;
+        w4 = v;
     }
 };
 
 // CombineAcc<float> for two columns: an unevaluated float pair per column (error-free sums
-// and products), lane by lane the same operations.
+// and products), lane by lane the same operations.  c = (c_g, c_g).
 struct CombineAcc2 {
     float2 hi = make_float2(0.f, 0.f), lo = make_float2(0.f, 0.f);
     template <bool EXACT>
-    __device__ __forceinline__ void add(float cf, float2 v) {
-        const float2 c = sg_f2(cf);
-        const float2 p = sg_mul2(c, v);
-        const float2 s = sg_add2(hi, p);  // two-sum of hi and p
-        const float2 bb = sg_sub2(s, hi);
-        const float2 e = sg_add2(sg_sub2(hi, sg_sub2(s, bb)), sg_sub2(p, bb));
-        hi = s;
+    __device__ __forceinline__ void add(float2 c, float2 v) {
         if (EXACT) {
+            // c v is exact: the two-sum of hi and p = c v with p formed inside the fused
+            // operations (s = hi + p and p - bb each rounded once, as with p stored)
+            const float2 s = sg_fma2(c, v, hi);
+            const float2 bb = sg_sub2(s, hi);
+            const float2 e = sg_add2(sg_sub2(hi, sg_sub2(s, bb)), sg_fma2(c, v, sg_neg2(bb)));
+            hi = s;
             lo = sg_add2(lo, e);
         } else {
+            const float2 p = sg_mul2(c, v);
+            const float2 s = sg_add2(hi, p);  // two-sum of hi and p
+            const float2 bb = sg_sub2(s, hi);
+            const float2 e = sg_add2(sg_sub2(hi, sg_sub2(s, bb)), sg_sub2(p, bb));
             const float2 pe = sg_fma2(c, v, sg_neg2(p));  // exact product error
+            hi = s;
             lo = sg_add2(lo, sg_add2(e, pe));
         }
     }
 };
 
-template <int J, int CY, bool EXACT>
+// One grid's contribution to the 8 fine nodes j0..j0+7 of a column pair for a last-axis ratio
+// r = 2^LR <= 8, where j0 is a multiple of 8 (so j0 is a multiple of r): node j0 + j has the
+// centre c0 + (j >> LR) (+1 in the upper half of its cell) and the offset s = m / r or
+// (m - r) / r, m = j mod r -- all fixed at compile time.  W holds the rows c0 - 2 .. c0 + 2;
+// the further rows the chunk needs are loaded first.  Nodes with s = 0 coincide with coarse
+// node c0 + (j >> LR) and take its value.
+template <int LR, bool EXACT, class Row>
+__device__ __forceinline__ void combine_chunk_pow2(CombineAcc2 (&acc)[8], InterpWin2& W, int c0, float2 cf,
+                                                   float e4, int lagrange, const Row& row) {
+    constexpr int R = 1 << LR;
+    constexpr int NX = (7 >> LR) + (2 * (7 & (R - 1)) < R ? 0 : 1);  // centre offset of node 7
+    float2 ex[NX];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) ex[k] = row(c0 + k + 3);
+    W.prepare(e4, lagrange);
+    int at = 0;  // centre offset of the prepared window
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int m = j & (R - 1);
+        const int cj = (j >> LR) + (2 * m < R ? 0 : 1);
+        if (cj != at) {  // one coarse node further (r >= 2: the centres advance by one)
+            W.shift(ex[cj - 1]);
+            W.prepare(e4, lagrange);
+            at = cj;
+        }
+        if (m == 0) acc[j].template add<EXACT>(cf, W.w2);
+        else acc[j].template add<EXACT>(cf, W.eval(sg_f2((float)(2 * m < R ? m : m - R) / (float)R)));
+    }
+}
+
+// The grid table as the last-axis kernel keeps it in shared memory: one 16-byte entry per grid
+// (the phase-1 array, n | lr << 26 with r = 2^lr, the float coefficient).
+struct CombineEntry {
+    const float* src;
+    int nlr;
+    float c;
+};
+#define SG_COMBINE_NLR_SHIFT 26
+
+// Template flags: VEC -- below is even and every source array is 8-byte aligned (both columns
+// of a pair with one 8-byte load); ZL -- zeros beyond the ends of the last axis (else periodic).
+// Dynamic shared memory: G CombineEntry.
+template <int J, int CY, bool EXACT, bool VEC, bool ZL>
 __global__ void __launch_bounds__(32 * CY, 2) sg_combine_last_axis_f32x2_kernel(const CombineGrid* __restrict__ tab, int G,
                                                                          double* __restrict__ uhat, long long below,
-                                                                         int nf, double eps, int lagrange,
-                                                                         int zero_last) {
+                                                                         int nf, double eps, int lagrange) {
+    static_assert(J == 8, "the chunk schedules assume 8 fine nodes per chunk");
+    extern __shared__ __align__(16) unsigned char sg_smem_raw[];
+    CombineEntry* s_grid = reinterpret_cast<CombineEntry*>(sg_smem_raw);
+    for (int t = threadIdx.y * 32 + threadIdx.x; t < G; t += 32 * CY) {
+        const CombineGrid& cg = tab[t];
+        CombineEntry e;
+        e.src = (const float*)cg.src;
+        e.nlr = cg.n | ((__ffs(cg.r) - 1) << SG_COMBINE_NLR_SHIFT);
+        e.c = cg.coeff_f;
+        s_grid[t] = e;
+    }
+    __syncthreads();
     const float e4 = sg_eps4<float>(eps);
     constexpr int JB = J * CY;  // fine nodes of the last axis per block
-    // centre and offset s of the block's JB fine nodes for every ratio r = 2^lr (lr <= 16)
-    __shared__ float4 s_tab[17 * JB];  // (s, s, s/2, s/2): both lanes of a packed operand
-    __shared__ int c_tab[17 * JB];
     const int ngroups = (nf + JB - 1) / JB;
     const long long npairs = (below + 1) >> 1;
-    const bool even = (below & 1) == 0;
     for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-        const int jb = grp * JB;
-        __syncthreads();  // the previous group's readers are done
-        for (int t = threadIdx.y * 32 + threadIdx.x; t < 17 * JB; t += 32 * CY) {
-            const int lr = t / JB, jf = jb + (t - lr * JB), r = 1 << lr;
-            const int i = jf >> lr, m = jf & (r - 1);  // jf = i r + m; centre i or i + 1
-            const float inv_r = pow2_neg<float>(lr);
-            float sv;
-            if (2 * m < r) {
-                c_tab[t] = i;
-                sv = (float)m * inv_r;
-            } else {
-                c_tab[t] = i + 1;
-                sv = (float)(m - r) * inv_r;
-            }
-            s_tab[t] = make_float4(sv, sv, 0.5f * sv, 0.5f * sv);
-        }
-        __syncthreads();
-        const int j0 = jb + threadIdx.y * J;  // this warp's chunk
+        const int j0 = grp * JB + threadIdx.y * J;  // this warp's chunk: a multiple of 8
         if (j0 >= nf) continue;
+        const bool full = j0 + J <= nf;
         for (long long pr = blockIdx.y * 32LL + threadIdx.x; pr < npairs; pr += gridDim.y * 32LL) {
             const long long lo = 2 * pr;
             const bool two = lo + 1 < below;
@@ -124,77 +170,110 @@ __global__ void __launch_bounds__(32 * CY, 2) sg_combine_last_axis_f32x2_kernel(
             // one grid's last axis for this column pair
             struct View {
                 const float* col;
-                int n, r;
-                float c;
-                bool vec;
+                int n, lr;
+                float2 c;
             };
             auto view = [&](int g) -> View {
-                const CombineGrid& cg = tab[g];
+                const int4 e = *reinterpret_cast<const int4*>(s_grid + g);
                 View v;
-                v.col = (const float*)cg.src + lo;
-                v.n = cg.n;
-                v.r = cg.r;
-                v.c = cg.coeff_f;
-                // both columns with one 8-byte load where the rows keep them 8-byte aligned
-                v.vec = even && ((reinterpret_cast<unsigned long long>(cg.src) & 7) == 0);
+                v.col = reinterpret_cast<const float*>(((unsigned long long)(unsigned)e.y << 32) | (unsigned)e.x) + lo;
+                v.n = e.z & ((1 << SG_COMBINE_NLR_SHIFT) - 1);
+                v.lr = e.z >> SG_COMBINE_NLR_SHIFT;
+                v.c = sg_f2(__int_as_float(e.w));
                 return v;
             };
-            auto row = [&](const View& v, int c) -> float2 {  // coarse row c (c in [-2, n + 2])
-                if (zero_last && (c < 0 || c >= v.n)) return make_float2(0.f, 0.f);
+            auto row = [&](const View& v, int c) -> float2 {  // coarse row c (c in [-n, 2n))
                 const float* p = v.col + (long long)wrap_index(c, v.n) * below;
-                if (v.vec) return *reinterpret_cast<const float2*>(p);
-                return make_float2(p[0], two ? p[1] : 0.f);
+                float2 x;
+                if (VEC) x = __ldg(reinterpret_cast<const float2*>(p));
+                else x = make_float2(__ldg(p), two ? __ldg(p + 1) : 0.f);
+                if (ZL && (c < 0 || c >= v.n)) x = make_float2(0.f, 0.f);
+                return x;
             };
-            // the first five rows a grid needs: around the chunk's first centre (r >= 2) or the
-            // chunk's first five fine nodes (r = 1)
+            // centre of node j0: the rows c0 - 2 .. c0 + 2 of the first window (r >= 2), or the
+            // first five fine rows j0 .. j0 + 4 (r = 1: c0 = j0 + 2)
+            auto centre0 = [&](const View& v) -> int {
+                if (v.lr == 0) return j0 + 2;
+                const int i0 = j0 >> v.lr, m0 = j0 & ((1 << v.lr) - 1);
+                return 2 * m0 < (1 << v.lr) ? i0 : i0 + 1;
+            };
             auto first = [&](const View& v, float2 (&w)[5]) {
-                const int c0 = v.r == 1 ? j0 + 2 : c_tab[(__ffs(v.r) - 1) * JB + threadIdx.y * J];
+                const int c0 = centre0(v);
 #pragma unroll
-                for (int k = 0; k < 5; ++k) w[k] = (v.r == 1 && j0 + k >= nf) ? make_float2(0.f, 0.f) : row(v, c0 - 2 + k);
+                for (int k = 0; k < 5; ++k) w[k] = row(v, c0 - 2 + k);
             };
             View nv = view(0);
             float2 nw[5];
             first(nv, nw);
             for (int g = 0; g < G; ++g) {
                 const View v = nv;
-                float2 w[5];
-#pragma unroll
-                for (int k = 0; k < 5; ++k) w[k] = nw[k];
+                InterpWin2 W;
+                W.w0 = nw[0];
+                W.w1 = nw[1];
+                W.w2 = nw[2];
+                W.w3 = nw[3];
+                W.w4 = nw[4];
+                const int c0 = centre0(v);
                 if (g + 1 < G) {  // the next grid's first rows are in flight during this grid's work
                     nv = view(g + 1);
                     first(nv, nw);
                 }
-                if (v.r == 1) {  // last axis already fine: values at coincident nodes
+                auto rowv = [&](int c) { return row(v, c); };
+                if (v.lr == 0) {  // last axis already fine: values at coincident nodes (rows
+                                  // j0 + j < 2 nf, read also for j0 + j >= nf and not used)
+                    const float2 w8[8] = {W.w0, W.w1, W.w2, W.w3, W.w4, row(v, j0 + 5), row(v, j0 + 6), row(v, j0 + 7)};
 #pragma unroll
                     for (int j = 0; j < J; ++j)
-                        if (j0 + j < nf) acc[j].template add<EXACT>(v.c, j < 5 ? w[j] : row(v, j0 + j));
+                        if (j0 + j < nf) acc[j].template add<EXACT>(v.c, w8[j]);
                     continue;
                 }
-                const int lr = __ffs(v.r) - 1;  // r = 2^lr: this warp's centres and offsets
-                const int* ct = c_tab + lr * JB + threadIdx.y * J;
-                const float4* sv = s_tab + lr * JB + threadIdx.y * J;
-                int cur = ct[0];
-                InterpWin2 W;
-                W.w0 = w[0];
-                W.w1 = w[1];
-                W.w2 = w[2];
-                W.w3 = w[3];
-                W.w4 = w[4];
+                if (full) {
+                    if (v.lr == 1) {
+                        combine_chunk_pow2<1, EXACT>(acc, W, c0, v.c, e4, lagrange, rowv);
+                        continue;
+                    }
+                    if (v.lr == 2) {
+                        combine_chunk_pow2<2, EXACT>(acc, W, c0, v.c, e4, lagrange, rowv);
+                        continue;
+                    }
+                    if (v.lr == 3) {
+                        combine_chunk_pow2<3, EXACT>(acc, W, c0, v.c, e4, lagrange, rowv);
+                        continue;
+                    }
+                    // r >= 16: the chunk lies in one half of one coarse cell (j0 and r / 2 are
+                    // multiples of 8), so one window serves all 8 nodes, at the offsets
+                    // s_j = s_0 + j / r (exact steps)
+                    W.prepare(e4, lagrange);
+                    const int m0 = j0 & ((1 << v.lr) - 1);
+                    const float inv_r = pow2_neg<float>(v.lr);
+                    float2 S = sg_f2((float)(2 * m0 < (1 << v.lr) ? m0 : m0 - (1 << v.lr)) * inv_r);
+                    const float2 dS = sg_f2(inv_r);
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        acc[j].template add<EXACT>(v.c, W.eval(S));
+                        S = sg_add2(S, dS);
+                    }
+                    continue;
+                }
+                // the last, ragged chunk (r <= 4 only: N_f is a multiple of 8 when N_L >= 3):
+                // centres and offsets node by node
+                const int r = 1 << v.lr;
+                const float inv_r = pow2_neg<float>(v.lr);
+                int cur = c0;
                 W.prepare(e4, lagrange);
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
-                    if (j0 + j >= nf) break;
-                    const int ic = ct[j];
+                    const int jf = j0 + j;
+                    if (jf >= nf) break;
+                    const int i = jf >> v.lr, m = jf & (r - 1);
+                    const int ic = 2 * m < r ? i : i + 1;
+                    const float s = (float)(2 * m < r ? m : m - r) * inv_r;
                     if (ic != cur) {  // centres advance by one coarse node at a time (r >= 2)
-                        W.w0 = W.w1;
-                        W.w1 = W.w2;
-                        W.w2 = W.w3;
-                        W.w3 = W.w4;
-                        W.w4 = row(v, ic + 2);
+                        W.shift(row(v, ic + 2));
                         W.prepare(e4, lagrange);
                         cur = ic;
                     }
-                    acc[j].template add<EXACT>(v.c, W.eval(sv[j]));
+                    acc[j].template add<EXACT>(v.c, W.eval(sg_f2(s)));
                 }
             }
 #pragma unroll
@@ -204,7 +283,7 @@ __global__ void __launch_bounds__(32 * CY, 2) sg_combine_last_axis_f32x2_kernel(
                 const double v0 = (double)acc[j].hi.x + (double)acc[j].lo.x;
                 const double v1 = (double)acc[j].hi.y + (double)acc[j].lo.y;
                 double* o = uhat + lo + (long long)jf * below;
-                if (even) {
+                if (VEC) {
                     *reinterpret_cast<double2*>(o) = make_double2(v0, v1);
                 } else {
                     o[0] = v0;
@@ -277,15 +356,11 @@ __global__ void __launch_bounds__(256) sg_prolong_multi_x2_kernel(const ProlongT
             float s;
             centre(jf, ic, s);
             if (ic != cur) {  // centres advance by one coarse node at a time (r >= 2)
-                W.w0 = W.w1;
-                W.w1 = W.w2;
-                W.w2 = W.w3;
-                W.w3 = W.w4;
-                W.w4 = at(ic + 2);
+                W.shift(at(ic + 2));
                 W.prepare(e4, lagrange);
                 cur = ic;
             }
-            *reinterpret_cast<float2*>(ocol + (long long)jf * below) = W.eval(make_float4(s, s, 0.5f * s, 0.5f * s));
+            *reinterpret_cast<float2*>(ocol + (long long)jf * below) = W.eval(sg_f2(s));
         }
     }
 }

@@ -78,9 +78,11 @@ struct Launch {
     static cudaError_t prolong_multi_pairs(const ProlongTask* tasks, int ntasks, long long nunits, double eps,
                                            int lagrange, cudaStream_t s);
     // uhat = sum_g c_g P_{d-1} I_g over the G entries of tab (device array), written once.
-    // exact_coeffs: every |c_g| is a power of two (products c_g v are exact in the FP32 sum)
+    // exact_coeffs: every |c_g| is a power of two (products c_g v are exact in the FP32 sum);
+    // pairs_aligned: below is even and every tab[g].src is 8-byte aligned (FP32: both columns
+    // of a pair with one 8-byte load)
     static cudaError_t combine_last_axis(const CombineGrid* tab, int G, double* uhat, long long below, int nf,
-                                         int exact_coeffs, int zero_last,
+                                         int exact_coeffs, int zero_last, int pairs_aligned,
                                          double eps, int lagrange, cudaStream_t s);
     // FP64 reduction of n values u (+ comp if non-null); partial holds >= 1024 doubles.
     static cudaError_t reduce(const T* u, const T* comp, long long n, int kind, const ExactSpec& X,

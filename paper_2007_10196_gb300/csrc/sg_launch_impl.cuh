@@ -339,21 +339,38 @@ cudaError_t Launch<T>::prolong_multi_pairs(const ProlongTask* tasks, int ntasks,
 
 template <class T>
 cudaError_t Launch<T>::combine_last_axis(const CombineGrid* tab, int G, double* uhat, long long below, int nf,
-                                         int exact_coeffs, int zero_last,
+                                         int exact_coeffs, int zero_last, int pairs_aligned,
                                          double eps, int lagrange, cudaStream_t s) {
     constexpr int J = 8;
-    if constexpr (sizeof(T) == 4) {  // two columns per thread, packed f32x2 (sg_combine2.cuh)
-        constexpr int CY = 8;
-        const long long npairs = (below + 1) / 2;
-        const dim3 grid2((unsigned)std::min<long long>((nf + J * CY - 1) / (J * CY), 65535),
-                         (unsigned)std::min<long long>((npairs + 31) / 32, 65535));
-        if (exact_coeffs)
-            sg_combine_last_axis_f32x2_kernel<J, CY, true><<<grid2, dim3(32, CY), 0, s>>>(tab, G, uhat, below, nf, eps,
-                                                                                       lagrange, zero_last);
-        else
-            sg_combine_last_axis_f32x2_kernel<J, CY, false><<<grid2, dim3(32, CY), 0, s>>>(tab, G, uhat, below, nf, eps,
-                                                                                        lagrange, zero_last);
-        return cudaGetLastError();
+    // FP32: two columns per thread, packed f32x2 (sg_combine2.cuh), the grid table in shared
+    // memory (16 bytes a grid, at most 48 KB; n below 2^26)
+    if constexpr (sizeof(T) == 4) {
+        if ((size_t)G * sizeof(CombineEntry) <= 48 * 1024 && nf < (1 << SG_COMBINE_NLR_SHIFT)) {
+            constexpr int CY = 8;
+            const long long npairs = (below + 1) / 2;
+            const dim3 grid2((unsigned)std::min<long long>((nf + J * CY - 1) / (J * CY), 65535),
+                             (unsigned)std::min<long long>((npairs + 31) / 32, 65535));
+            const dim3 blk(32, CY);
+            const size_t sm = (size_t)G * sizeof(CombineEntry);
+            const int key = (exact_coeffs ? 4 : 0) | (pairs_aligned ? 2 : 0) | (zero_last ? 1 : 0);
+            switch (key) {
+#define SG_COMB2(K, E, V, Z)                                                                                   \
+    case K:                                                                                                    \
+        sg_combine_last_axis_f32x2_kernel<J, CY, E, V, Z><<<grid2, blk, sm, s>>>(tab, G, uhat, below, nf, eps, \
+                                                                                 lagrange);                    \
+        break;
+                SG_COMB2(0, false, false, false)
+                SG_COMB2(1, false, false, true)
+                SG_COMB2(2, false, true, false)
+                SG_COMB2(3, false, true, true)
+                SG_COMB2(4, true, false, false)
+                SG_COMB2(5, true, false, true)
+                SG_COMB2(6, true, true, false)
+                SG_COMB2(7, true, true, true)
+#undef SG_COMB2
+            }
+            return cudaGetLastError();
+        }
     }
     dim3 grid((unsigned)std::min<long long>((below + 255) / 256, 65535),
               (unsigned)std::min<long long>((nf + J - 1) / J, 65535));

@@ -207,7 +207,12 @@ def test_prolong_combine_fp64_bitwise(sg, orc, dim, nr, nl, prolong, kind, budge
     assert np.array_equal(got, ref), np.max(np.abs(got - ref))
 
 
-@pytest.mark.parametrize("dim,nr,nl,prolong", [(2, 6, 3, 0), (3, 5, 2, 0), (3, 5, 2, 1)])
+# last-axis ratios r = 2^(N_L - l_{d-1}) up to 4 with ragged 8-node chunks (N_f = 20), and up
+# to 16 (d = 3, N_L = 4) and 64 (d = 2, N_L = 6) on whole chunks: every chunk schedule of the
+# FP32 last-axis kernel (r = 1, 2, 4, 8, >= 16, ragged); N_L = 0 with odd N_r: an odd number of
+# columns (no 8-byte column pairs)
+@pytest.mark.parametrize("dim,nr,nl,prolong", [(2, 6, 3, 0), (3, 5, 2, 0), (3, 5, 2, 1), (3, 5, 4, 0), (3, 5, 4, 1),
+                                               (2, 5, 6, 0), (2, 5, 0, 0), (3, 7, 0, 1)])
 @pytest.mark.parametrize("budget", [0.0, -1.0], ids=["one_pass", "grid_by_grid"])
 def test_prolong_combine_fp32_within_tolerance(sg, orc, dim, nr, nl, prolong, budget):
     h = make(dim, nr, nl, P.SG_PDE_ADVECTION, prolong=prolong, precision=P.SG_F32, combine_budget_gb=budget)

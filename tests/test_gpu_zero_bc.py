@@ -120,6 +120,28 @@ def test_zero_bc_combination_fp64_bitwise(sg, orc, dim, nr, nl, prolong, bc, bud
     assert np.array_equal(got, orc.combine(p, lev, co, g0))
 
 
+# FP32 last-axis kernel with zeros beyond the ends of the last axis: ratios r up to 16 (d = 3,
+# N_L = 4) and 64 (d = 2, N_L = 6), so the window rows of every chunk schedule reach past
+# both ends; within the FP32 combination bound (d interpolation passes, summed with |c_g|)
+@pytest.mark.parametrize("dim,nr,nl,prolong,bc", [(3, 5, 4, 0, (PER, Z, Z)), (3, 5, 4, 1, (Z, PER, Z)),
+                                                  (2, 5, 6, 0, (Z, Z)), (2, 6, 3, 0, (PER, Z))])
+def test_zero_bc_combination_fp32_large_ratios(sg, orc, dim, nr, nl, prolong, bc):
+    h = make(dim, nr, nl, P.SG_PDE_BURGERS, prolong=prolong, precision=P.SG_F32, bc=list(bc) + [PER] * (6 - dim))
+    try:
+        lev, shp, co = _levels(h, dim)
+        g0 = [g.astype(np.float32).astype(np.float64) for g in random_grids(9, nr, lev, "mixed")]
+        P.sg_init_grids(h, np.concatenate(g0))
+        P.sg_prolong_combine(h)
+        got = P.sg_read(h, P.SG_WHICH_COMBINED, count=(nr << nl) ** dim)
+    finally:
+        P.sg_destroy(h)
+    p = orc.problem(dim, nr, nl, pde=1, prolong=prolong, eps=1e-3, bc=bc)
+    ref = orc.combine(p, lev, co, g0)
+    umax = max(np.abs(g).max() for g in g0)
+    tol = 32 * U32 * dim * umax * sum(abs(c) for c in co)
+    assert np.max(np.abs(got - ref)) <= tol
+
+
 def test_zero_bc_batch_matches_members(sg, orc):
     case = (3, 8, 2, 1, (Z, Z, PER), P.SG_BATCHED, SWEEP, 1, 2)
     single = _run(orc, case, P.SG_F64)
