@@ -55,15 +55,18 @@ struct SweepSide2 {
         T2 = T1; T1 = T0;
         T0 = tterm(sg_sub2(d2, d1), ep);
     }
-    // numerator and denominator of fhat - c, as SweepSide<float>::value
+    // numerator and denominator of 6 (fhat - c): with s_r as in SweepSide<float>, the candidate
+    // differences times 6 are P_0 = 2 s_0 - d_2, P_1 = s_1 + d_3, P_2 = s_2 + d_3, and the linear
+    // weights times 10 are (1, 6, 3): num = E_1 (E_2 P_0 + 3 E_0 P_2) + 6 E_0 E_2 P_1,
+    // den = E_1 (E_2 + 3 E_0) + 6 E_0 E_2
     __device__ __forceinline__ void value(int linear, float2& num, float2& den) const {
-        const float2 p0s = sg_fma2(sg_f2(5.f / 36.f), d2, sg_mul2(sg_f2(-1.f / 18.f), d1));  // p_0 / 6
-        const float2 p1 = sg_fma2(sg_f2(1.f / 6.f), d2, sg_mul2(sg_f2(1.f / 3.f), d3));
-        const float2 p2h = sg_fma2(sg_f2(1.f / 3.f), d3, sg_mul2(sg_f2(-1.f / 12.f), d4));  // p_2 / 2
+        const float2 k3 = sg_f2(3.f);
+        const float2 s0 = sg_fma2(k3, d2, sg_neg2(d1)), s1 = sg_add2(d2, d3);
+        const float2 s2 = sg_fma2(k3, d3, sg_neg2(d4));
+        const float2 P0 = sg_fma2(sg_f2(2.f), s0, sg_neg2(d2));
+        const float2 P1 = sg_add2(s1, d3), P2 = sg_add2(s2, d3);
         float2 E0 = sg_f2(1.f), E1 = sg_f2(1.f), E2 = sg_f2(1.f);
         if (!linear) {
-            const float2 s0 = sg_fma2(sg_f2(3.f), d2, sg_neg2(d1)), s1 = sg_add2(d2, d3);
-            const float2 s2 = sg_fma2(sg_f2(3.f), d3, sg_neg2(d4));
             float2 e0 = sg_fma2(s0, s0, T0);
             float2 e1 = sg_fma2(s1, s1, T1);
             float2 e2 = sg_fma2(s2, s2, T2);
@@ -72,21 +75,21 @@ struct SweepSide2 {
             E1 = sg_mul2(e1, e1);
             E2 = sg_mul2(e2, e2);
         }
-        const float2 X = sg_mul2(E0, E2);
-        num = sg_fma2(E1, sg_fma2(E2, p0s, sg_mul2(E0, p2h)), sg_mul2(X, p1));
-        den = sg_fma2(E1, sg_fma2(E2, sg_f2(1.f / 6.f), sg_mul2(sg_f2(0.5f), E0)), X);
+        const float2 X6 = sg_mul2(sg_f2(6.f), sg_mul2(E0, E2));
+        num = sg_fma2(E1, sg_fma2(E2, P0, sg_mul2(k3, sg_mul2(E0, P2))), sg_mul2(X6, P1));
+        den = sg_fma2(E1, sg_fma2(k3, E0, E2), X6);
     }
 };
 
-// fhat = fhat^+ + fhat^- of both lines (each den in [5/3, 2^81], normal: the approximate
-// reciprocal is within about an ulp)
+// fhat = fhat^+ + fhat^- of both lines: c^+ + c^- + (1/6) (num^+ / den^+ + num^- / den^-) (each
+// den in [10, 10 2^80], normal: the approximate reciprocal is within about an ulp)
 __device__ __forceinline__ float2 sweep_flux2(const SweepSide2& P, const SweepSide2& M, int linear) {
     float2 np, dp, nm, dm;
     P.value(linear, np, dp);
     M.value(linear, nm, dm);
     const float2 rp = make_float2(sg_rcp(dp.x), sg_rcp(dp.y));
     const float2 rm = make_float2(sg_rcp(dm.x), sg_rcp(dm.y));
-    return sg_add2(sg_add2(P.c, M.c), sg_fma2(np, rp, sg_mul2(nm, rm)));
+    return sg_fma2(sg_f2(1.f / 6.f), sg_fma2(np, rp, sg_mul2(nm, rm)), sg_add2(P.c, M.c));
 }
 
 template <bool ZB>
@@ -103,8 +106,12 @@ __global__ void __launch_bounds__(SG_NT3H, 6) sg_stage_sweep3x2_kernel(const Sta
     const float adv[3] = {(float)ph.adv[0], (float)ph.adv[1], (float)ph.adv[2]};
     const int zm = ZB ? ph.zmask : 0;  // zero boundary per axis (advection / Burgers)
 
+    // the next work item is read one item early (its load is in flight during this item)
+    WorkItem wn;
+    if (A.item_begin + blockIdx.x < A.item_end) wn = A.items[A.item_begin + blockIdx.x];
     for (int it = A.item_begin + blockIdx.x; it < A.item_end; it += gridDim.x) {
-        const WorkItem w = A.items[it];
+        const WorkItem w = wn;
+        if (it + (int)gridDim.x < A.item_end) wn = A.items[it + gridDim.x];
         const GridDesc* G = A.grids + w.grid;
         const InstState* S = A.inst + G->inst;
         if (!S->active) continue;  // uniform: the state is not written during this kernel
