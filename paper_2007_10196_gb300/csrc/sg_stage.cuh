@@ -159,59 +159,6 @@ struct StageIO<float> {
         }
         return make_float4(o[0], o[1], o[2], o[3]);
     }
-    // update4 in two halves: load4 reads the operands, finish4 forms the results (the same
-    // arithmetic per point) and stores them, so that several groups' loads can be in flight at
-    // once
-    struct Ops4 {
-        float4 u, a, b;  // U; D1 (stage 1) or D2 and C (stage 2)
-    };
-    __device__ __forceinline__ void load4(long long g, Ops4& x) const {
-        x.u = *reinterpret_cast<const float4*>(U + g);
-        if (stage == 1) {
-            x.a = *reinterpret_cast<const float4*>(Ub + g);
-        } else if (stage == 2) {
-            x.a = *reinterpret_cast<const float4*>(D2 + g);
-            x.b = *reinterpret_cast<const float4*>(Cc + g);
-        }
-    }
-    __device__ __forceinline__ float4 finish4(long long g, const Ops4& x, const float (&L)[4], float dt) const {
-        const float uu[4] = {x.u.x, x.u.y, x.u.z, x.u.w};
-        float o[4];
-        if (stage == 0) {
-            float dd[4];
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                dd[l] = dt * L[l];
-                o[l] = uu[l] + dd[l];
-            }
-            *reinterpret_cast<float4*>(Ub + g) = make_float4(dd[0], dd[1], dd[2], dd[3]);
-        } else if (stage == 1) {
-            const float bb[4] = {x.a.x, x.a.y, x.a.z, x.a.w};
-            float nd[4];
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const float d = dt * L[l];
-                nd[l] = 0.25f * (bb[l] + d);
-                o[l] = uu[l] + nd[l];
-            }
-            *reinterpret_cast<float4*>(D2 + g) = make_float4(nd[0], nd[1], nd[2], nd[3]);
-        } else {
-            const float dd2[4] = {x.a.x, x.a.y, x.a.z, x.a.w}, cc[4] = {x.b.x, x.b.y, x.b.z, x.b.w};
-            float er[4];
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const float d = dt * L[l];
-                const float y = fmaf(2.f / 3.f, dd2[l] + d, cc[l]);
-                const float sm = uu[l] + y;
-                const float bb = sm - uu[l];
-                er[l] = (uu[l] - (sm - bb)) + (y - bb);
-                o[l] = sm;
-            }
-            *reinterpret_cast<float4*>(Ub + g) = make_float4(o[0], o[1], o[2], o[3]);
-            *reinterpret_cast<float4*>(Cc + g) = make_float4(er[0], er[1], er[2], er[3]);
-        }
-        return make_float4(o[0], o[1], o[2], o[3]);
-    }
 };
 
 template <class T>
