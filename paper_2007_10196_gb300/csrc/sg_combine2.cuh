@@ -97,15 +97,14 @@ struct CombineAcc2 {
     }
 };
 
-// One grid's contribution to the 8 fine nodes j0..j0+7 of a column pair for a last-axis ratio
-// r = 2^LR <= 8, where j0 is a multiple of 8 (so j0 is a multiple of r): node j0 + j has the
-// centre c0 + (j >> LR) (+1 in the upper half of its cell) and the offset s = m / r or
-// (m - r) / r, m = j mod r -- all fixed at compile time.  W holds the rows c0 - 2 .. c0 + 2;
-// the further rows the chunk needs are loaded first.  Nodes with s = 0 coincide with coarse
-// node c0 + (j >> LR) and take its value.
-template <int LR, bool EXACT, class Row>
-__device__ __forceinline__ void combine_chunk_pow2(CombineAcc2 (&acc)[8], InterpWin2& W, int c0, float2 cf,
-                                                   float e4, int lagrange, const Row& row) {
+// The values of a column pair at the 8 fine nodes j0..j0+7 of one axis for a ratio r = 2^LR <= 8,
+// where j0 is a multiple of 8 (so j0 is a multiple of r): node j0 + j has the centre
+// c0 + (j >> LR) (+1 in the upper half of its cell) and the offset s = m / r or (m - r) / r,
+// m = j mod r -- all fixed at compile time.  W holds the rows c0 - 2 .. c0 + 2; the further rows
+// the chunk needs are loaded first.  Nodes with s = 0 coincide with coarse node c0 + (j >> LR) and
+// take its value.  sink(j, value) receives node j0 + j.
+template <int LR, class Row, class Sink>
+__device__ __forceinline__ void chunk_pow2(InterpWin2& W, int c0, float e4, int lagrange, const Row& row, Sink sink) {
     constexpr int R = 1 << LR;
     constexpr int NX = (7 >> LR) + (2 * (7 & (R - 1)) < R ? 0 : 1);  // centre offset of node 7
     float2 ex[NX];
@@ -122,9 +121,32 @@ __device__ __forceinline__ void combine_chunk_pow2(CombineAcc2 (&acc)[8], Interp
             W.prepare(e4, lagrange);
             at = cj;
         }
-        if (m == 0) acc[j].template add<EXACT>(cf, W.w2);
-        else acc[j].template add<EXACT>(cf, W.eval(sg_f2((float)(2 * m < R ? m : m - R) / (float)R)));
+        if (m == 0) sink(j, W.w2);
+        else sink(j, W.eval(sg_f2((float)(2 * m < R ? m : m - R) / (float)R)));
     }
+}
+
+// The same for r = 2^lr >= 16: the chunk lies in one half of one coarse cell (j0 and r / 2 are
+// multiples of 8), so one window (rows c0 - 2 .. c0 + 2 in W) serves all 8 nodes, at the
+// offsets s_j = s_0 + j / r (exact steps).
+template <class Sink>
+__device__ __forceinline__ void chunk_one_window(InterpWin2& W, int j0, int lr, float e4, int lagrange, Sink sink) {
+    W.prepare(e4, lagrange);
+    const int m0 = j0 & ((1 << lr) - 1);
+    const float inv_r = pow2_neg<float>(lr);
+    float2 S = sg_f2((float)(2 * m0 < (1 << lr) ? m0 : m0 - (1 << lr)) * inv_r);
+    const float2 dS = sg_f2(inv_r);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        sink(j, W.eval(S));
+        S = sg_add2(S, dS);
+    }
+}
+
+// centre of fine node j0 for r = 2^lr >= 2: the centre of the window of its first node
+__device__ __forceinline__ int chunk_centre0(int j0, int lr) {
+    const int i0 = j0 >> lr, m0 = j0 & ((1 << lr) - 1);
+    return 2 * m0 < (1 << lr) ? i0 : i0 + 1;
 }
 
 // The grid table as the last-axis kernel keeps it in shared memory: one 16-byte entry per grid
@@ -192,11 +214,7 @@ __global__ void __launch_bounds__(32 * CY, 2) sg_combine_last_axis_f32x2_kernel(
             };
             // centre of node j0: the rows c0 - 2 .. c0 + 2 of the first window (r >= 2), or the
             // first five fine rows j0 .. j0 + 4 (r = 1: c0 = j0 + 2)
-            auto centre0 = [&](const View& v) -> int {
-                if (v.lr == 0) return j0 + 2;
-                const int i0 = j0 >> v.lr, m0 = j0 & ((1 << v.lr) - 1);
-                return 2 * m0 < (1 << v.lr) ? i0 : i0 + 1;
-            };
+            auto centre0 = [&](const View& v) -> int { return v.lr == 0 ? j0 + 2 : chunk_centre0(j0, v.lr); };
             auto first = [&](const View& v, float2 (&w)[5]) {
                 const int c0 = centre0(v);
 #pragma unroll
@@ -219,6 +237,7 @@ __global__ void __launch_bounds__(32 * CY, 2) sg_combine_last_axis_f32x2_kernel(
                     first(nv, nw);
                 }
                 auto rowv = [&](int c) { return row(v, c); };
+                auto accv = [&](int j, float2 x) { acc[j].template add<EXACT>(v.c, x); };
                 if (v.lr == 0) {  // last axis already fine: values at coincident nodes (rows
                                   // j0 + j < 2 nf, read also for j0 + j >= nf and not used)
                     const float2 w8[8] = {W.w0, W.w1, W.w2, W.w3, W.w4, row(v, j0 + 5), row(v, j0 + 6), row(v, j0 + 7)};
@@ -229,30 +248,18 @@ __global__ void __launch_bounds__(32 * CY, 2) sg_combine_last_axis_f32x2_kernel(
                 }
                 if (full) {
                     if (v.lr == 1) {
-                        combine_chunk_pow2<1, EXACT>(acc, W, c0, v.c, e4, lagrange, rowv);
+                        chunk_pow2<1>(W, c0, e4, lagrange, rowv, accv);
                         continue;
                     }
                     if (v.lr == 2) {
-                        combine_chunk_pow2<2, EXACT>(acc, W, c0, v.c, e4, lagrange, rowv);
+                        chunk_pow2<2>(W, c0, e4, lagrange, rowv, accv);
                         continue;
                     }
                     if (v.lr == 3) {
-                        combine_chunk_pow2<3, EXACT>(acc, W, c0, v.c, e4, lagrange, rowv);
+                        chunk_pow2<3>(W, c0, e4, lagrange, rowv, accv);
                         continue;
                     }
-                    // r >= 16: the chunk lies in one half of one coarse cell (j0 and r / 2 are
-                    // multiples of 8), so one window serves all 8 nodes, at the offsets
-                    // s_j = s_0 + j / r (exact steps)
-                    W.prepare(e4, lagrange);
-                    const int m0 = j0 & ((1 << v.lr) - 1);
-                    const float inv_r = pow2_neg<float>(v.lr);
-                    float2 S = sg_f2((float)(2 * m0 < (1 << v.lr) ? m0 : m0 - (1 << v.lr)) * inv_r);
-                    const float2 dS = sg_f2(inv_r);
-#pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        acc[j].template add<EXACT>(v.c, W.eval(S));
-                        S = sg_add2(S, dS);
-                    }
+                    chunk_one_window(W, j0, v.lr, e4, lagrange, accv);  // r >= 16
                     continue;
                 }
                 // the last, ragged chunk (r <= 4 only: N_f is a multiple of 8 when N_L >= 3):
@@ -298,10 +305,13 @@ __global__ void __launch_bounds__(32 * CY, 2) sg_combine_last_axis_f32x2_kernel(
 // aligned arrays): thread p takes units 2p and 2p + 1 -- the same chunk of two adjacent columns
 // -- and runs the window arithmetic once for both in packed f32x2 form (InterpWin2), with
 // 8-byte loads and stores.  The tasks' unit ranges are even-sized, so a pair never straddles
-// two tasks.
+// two tasks.  A chunk starts at a multiple of 8, so whole chunks follow the compile-time
+// schedules of chunk_pow2 (r <= 8) or one window (r >= 16); only a last, ragged chunk takes its
+// centres node by node.  Every task has r >= 2 (axes already at the finest level are skipped).
 template <int J>
 __global__ void __launch_bounds__(256) sg_prolong_multi_x2_kernel(const ProlongTask* __restrict__ tasks, int ntasks,
                                                                   long long nunits, double eps, int lagrange) {
+    static_assert(J == 8, "the chunk schedules assume 8 fine nodes per chunk");
     const float e4 = sg_eps4<float>(eps);
     const long long npairs = nunits >> 1;
     for (long long pp = blockIdx.x * 256LL + threadIdx.x; pp < npairs; pp += gridDim.x * 256LL) {
@@ -320,47 +330,47 @@ __global__ void __launch_bounds__(256) sg_prolong_multi_x2_kernel(const ProlongT
         const unsigned lo = v - q * below;  // even: below is even and v is even
         const unsigned hi = div_mag(q, (unsigned)nchunks, tk.nch_mag);
         const int j0 = (int)(q - hi * (unsigned)nchunks) * J;
-        const int n = tk.n, nf = tk.nf, r = tk.r, lr = __ffs(r) - 1;
-        const float inv_r = pow2_neg<float>(lr);
+        const int n = tk.n, nf = tk.nf, lr = __ffs(tk.r) - 1;
+        const bool zero_bc = tk.zero_bc != 0;
         const float* col = (const float*)tk.in + (long long)hi * below * n + lo;
         float* ocol = (float*)tk.out + (long long)hi * below * nf + lo;
-        auto centre = [&](int jf, int& ic, float& s) {  // as fine_to_coarse
-            const int i = jf >> lr, m = jf & (r - 1);
-            if (2 * m < r) {
-                ic = i;
-                s = (float)m * inv_r;
-            } else {
-                ic = i + 1;
-                s = (float)(m - r) * inv_r;
-            }
+        auto at = [&](int c) -> float2 {  // both columns' coarse value c, c in [-n, 2n)
+            float2 x = __ldg(reinterpret_cast<const float2*>(col + (long long)wrap_index(c, n) * below));
+            if (zero_bc && (c < 0 || c >= n)) x = make_float2(0.f, 0.f);
+            return x;
         };
-        auto at = [&](int c) -> float2 {  // both columns' coarse value c, c in [-2, n + 2]
-            if (tk.zero_bc && (c < 0 || c >= n)) return make_float2(0.f, 0.f);
-            return *reinterpret_cast<const float2*>(col + (long long)wrap_index(c, n) * below);
-        };
-        int cur;
-        float s0;
-        centre(j0, cur, s0);
+        auto put = [&](int j, float2 x) { *reinterpret_cast<float2*>(ocol + (long long)(j0 + j) * below) = x; };
+        const int c0 = chunk_centre0(j0, lr);
         InterpWin2 W;
-        W.w0 = at(cur - 2);
-        W.w1 = at(cur - 1);
-        W.w2 = at(cur);
-        W.w3 = at(cur + 1);
-        W.w4 = at(cur + 2);
+        W.w0 = at(c0 - 2);
+        W.w1 = at(c0 - 1);
+        W.w2 = at(c0);
+        W.w3 = at(c0 + 1);
+        W.w4 = at(c0 + 2);
+        if (j0 + J <= nf) {
+            if (lr == 1) chunk_pow2<1>(W, c0, e4, lagrange, at, put);
+            else if (lr == 2) chunk_pow2<2>(W, c0, e4, lagrange, at, put);
+            else if (lr == 3) chunk_pow2<3>(W, c0, e4, lagrange, at, put);
+            else chunk_one_window(W, j0, lr, e4, lagrange, put);
+            continue;
+        }
+        const int r = 1 << lr;
+        const float inv_r = pow2_neg<float>(lr);
+        int cur = c0;
         W.prepare(e4, lagrange);
 #pragma unroll 1
         for (int j = 0; j < J; ++j) {
             const int jf = j0 + j;
             if (jf >= nf) break;
-            int ic;
-            float s;
-            centre(jf, ic, s);
+            const int i = jf >> lr, m = jf & (r - 1);
+            const int ic = 2 * m < r ? i : i + 1;
+            const float sv = (float)(2 * m < r ? m : m - r) * inv_r;
             if (ic != cur) {  // centres advance by one coarse node at a time (r >= 2)
                 W.shift(at(ic + 2));
                 W.prepare(e4, lagrange);
                 cur = ic;
             }
-            *reinterpret_cast<float2*>(ocol + (long long)jf * below) = W.eval(sg_f2(s));
+            put(j, W.eval(sg_f2(sv)));
         }
     }
 }
