@@ -271,8 +271,8 @@ def kernel_name(P, h):
     kern, tp, _ = P.sg_stage_config(h)
     if kern == P.SG_STAGE_SWEEP:
         return "sg_stage_sweep3_kernel<float, false>"
-    if kern == P.SG_STAGE_SWEEP2:
-        return "sg_stage_sweep3x2_kernel<false>"
+    if kern == P.SG_STAGE_SWEEP2:  # pairs of work items per block at the batch's sizes
+        return "sg_stage_sweep3x2_kernel<false, 2>"
     return "sg_stage_box_kernel<float,3,%d>" % (tp // 256)
 
 

@@ -152,24 +152,27 @@ cudaError_t stage_box3(int ppt, const StageArgs& a, int nblocks, size_t smem, cu
 }  // namespace detail
 
 namespace detail {
-// d = 3, FP32, two lines per thread (variant 3); both instantiations get the same limit
+// d = 3, FP32, two lines per thread (variant 3); all four instantiations get the same limits
 template <class T>
 int prepare_sweep2(size_t smem) {
     if constexpr (sizeof(T) != 4) {
         return 0;
     } else {
-        const void* k0 = (const void*)sg_stage_sweep3x2_kernel<false>;
-        const void* k1 = (const void*)sg_stage_sweep3x2_kernel<true>;
-        // the whole unified L1/shared array as shared memory: 7 blocks of ~30 KB per SM
-        if (cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-            cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-            cudaFuncSetAttribute(k0, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess ||
-            cudaFuncSetAttribute(k1, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess) {
-            cudaGetLastError();
-            return 0;
+        const void* kk[4] = {(const void*)sg_stage_sweep3x2_kernel<false, 1>, (const void*)sg_stage_sweep3x2_kernel<true, 1>,
+                             (const void*)sg_stage_sweep3x2_kernel<false, 2>, (const void*)sg_stage_sweep3x2_kernel<true, 2>};
+        // 72% of the unified L1/shared array as shared memory (164 KB: 5 blocks of ~31 KB per SM)
+        // and the rest as L1 (~92 KB): the update's loads of U and D then mostly hit the lines
+        // the same tile's gather brought in.  Measured faster than 6 blocks with a 28 KB L1
+        // (the register limit) or 4 blocks with a 124 KB L1.
+        for (const void* k : kk) {
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+                cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 72) != cudaSuccess) {
+                cudaGetLastError();
+                return 0;
+            }
         }
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k0, SG_NT3H, smem) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kk[0], SG_NT3H, smem) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
@@ -202,8 +205,15 @@ cudaError_t Launch<T>::stage(int dim, int ppt, const StageArgs& a, int nblocks, 
         if constexpr (sizeof(T) != 4) {
             return cudaErrorInvalidValue;
         } else {
-            if (a.phys.zmask) sg_stage_sweep3x2_kernel<true><<<nblocks, SG_NT3H, smem, s>>>(a);
-            else sg_stage_sweep3x2_kernel<false><<<nblocks, SG_NT3H, smem, s>>>(a);
+            // pairs of consecutive items per block when there are at least two per block
+            const bool pairs = a.item_end - a.item_begin >= 2 * nblocks;
+            if (a.phys.zmask) {
+                if (pairs) sg_stage_sweep3x2_kernel<true, 2><<<nblocks, SG_NT3H, smem, s>>>(a);
+                else sg_stage_sweep3x2_kernel<true, 1><<<nblocks, SG_NT3H, smem, s>>>(a);
+            } else {
+                if (pairs) sg_stage_sweep3x2_kernel<false, 2><<<nblocks, SG_NT3H, smem, s>>>(a);
+                else sg_stage_sweep3x2_kernel<false, 1><<<nblocks, SG_NT3H, smem, s>>>(a);
+            }
             return cudaGetLastError();
         }
     }

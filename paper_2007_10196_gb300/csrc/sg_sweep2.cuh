@@ -92,7 +92,7 @@ __device__ __forceinline__ float2 sweep_flux2(const SweepSide2& P, const SweepSi
     return sg_fma2(sg_f2(1.f / 6.f), sg_fma2(np, rp, sg_mul2(nm, rm)), sg_add2(P.c, M.c));
 }
 
-template <bool ZB>
+template <bool ZB, int RUN>
 __global__ void __launch_bounds__(SG_NT3H, 6) sg_stage_sweep3x2_kernel(const StageArgs A) {
     extern __shared__ __align__(16) unsigned char sg_smem_raw[];
     float* bp = reinterpret_cast<float*>(sg_smem_raw);  // f^+ (Burgers) or u (advection)
@@ -106,12 +106,19 @@ __global__ void __launch_bounds__(SG_NT3H, 6) sg_stage_sweep3x2_kernel(const Sta
     const float adv[3] = {(float)ph.adv[0], (float)ph.adv[1], (float)ph.adv[2]};
     const int zm = ZB ? ph.zmask : 0;  // zero boundary per axis (advection / Burgers)
 
-    // the next work item is read one item early (its load is in flight during this item)
+    // Runs of RUN consecutive work items per block (run c = blockIdx.x, + gridDim.x, ...); the
+    // host takes RUN = 2 when the launch has at least two items per block: consecutive tiles of
+    // a grid row share half of their x-row chunks, which the second finds in L1.  The next work
+    // item is read one item early (its load is in flight during this item).
+    auto next_item = [&](int i) {
+        return ((i - A.item_begin + 1) % RUN) != 0 ? i + 1 : i + 1 + ((int)gridDim.x - 1) * RUN;
+    };
+    const int it0 = A.item_begin + (int)blockIdx.x * RUN;
     WorkItem wn;
-    if (A.item_begin + blockIdx.x < A.item_end) wn = A.items[A.item_begin + blockIdx.x];
-    for (int it = A.item_begin + blockIdx.x; it < A.item_end; it += gridDim.x) {
+    if (it0 < A.item_end) wn = A.items[it0];
+    for (int it = it0; it < A.item_end; it = next_item(it)) {
         const WorkItem w = wn;
-        if (it + (int)gridDim.x < A.item_end) wn = A.items[it + gridDim.x];
+        if (next_item(it) < A.item_end) wn = A.items[next_item(it)];
         const GridDesc* G = A.grids + w.grid;
         const InstState* S = A.inst + G->inst;
         if (!S->active) continue;  // uniform: the state is not written during this kernel
