@@ -1368,9 +1368,11 @@ sg_status sg_init(sg_handle h, int ic_kind, const double* p, int n_params) {
     if (ic_kind != SG_IC_SINE || n_params != 4 || !p) return fail(SG_ERR_ARG, "SG_IC_SINE takes 4 parameters");
     for (int i = 0; i < 4; ++i)
         if (!std::isfinite(p[i])) return fail(SG_ERR_ARG, "initial-condition parameter %d not finite", i);
-    for (int g = 0; g < h->G; ++g) {
-        if (h->esize == 8) SG_CUDA(sg::Launch<double>::restrict_sine(h->hgrids[g], h->dim, p, h->stream));
-        else SG_CUDA(sg::Launch<float>::restrict_sine(h->hgrids[g], h->dim, p, h->stream));
+    {
+        long long maxp = 1;
+        for (int g = 0; g < h->G; ++g) maxp = std::max(maxp, h->hgrids[g].npts);
+        if (h->esize == 8) SG_CUDA(sg::Launch<double>::restrict_sine(h->dgrids.as<GridDesc>(), h->G, maxp, h->dim, p, h->stream));
+        else SG_CUDA(sg::Launch<float>::restrict_sine(h->dgrids.as<GridDesc>(), h->G, maxp, h->dim, p, h->stream));
         h->launches += 1;
     }
     SG_CUDA(cudaStreamSynchronize(h->stream));

@@ -92,18 +92,34 @@ static __global__ void sg_dt_kernel(InstState* inst, int ninst, const GridDesc* 
 
 // ------------------------------------------------------------------------------------
 // Step 1: restriction of u0 = p0 + p1 sin(p2 sum_k x_k + p3), x_k = lo_k + j_k h_k.
+// One launch for all grids of a problem: blockIdx.y = grid, the blocks along x stride over its
+// points.  The node indices j_k come from 32-bit division when the grid has fewer than 2^31
+// points (64-bit otherwise); the sum, sine and split are the same operations in the same order
+// either way.
 // ------------------------------------------------------------------------------------
 template <class T>
-__global__ void sg_restrict_sine_kernel(GridDesc G, int dim, double p0, double p1, double p2,
+__global__ void sg_restrict_sine_kernel(const GridDesc* __restrict__ grids, int dim, double p0, double p1, double p2,
                                         double p3) {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < G.npts;
+    const GridDesc& G = grids[blockIdx.y];
+    const long long npts = G.npts;
+    const bool narrow = npts < (1LL << 31);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npts;
          p += (long long)gridDim.x * blockDim.x) {
-        long long r = p;
         double S = 0.0;
-        for (int k = 0; k < dim; ++k) {
-            const long long j = r % G.n[k];
-            r /= G.n[k];
-            S = S + (G.lo[k] + (double)j * G.h[k]);
+        if (narrow) {
+            unsigned r = (unsigned)p;
+            for (int k = 0; k < dim; ++k) {
+                const unsigned n = (unsigned)G.n[k], q = r / n;
+                S = S + (G.lo[k] + (double)(r - q * n) * G.h[k]);
+                r = q;
+            }
+        } else {
+            long long r = p;
+            for (int k = 0; k < dim; ++k) {
+                const long long j = r % G.n[k];
+                r /= G.n[k];
+                S = S + (G.lo[k] + (double)j * G.h[k]);
+            }
         }
         const double v = p0 + p1 * sin(p2 * S + p3);
         ((T*)G.u0)[p] = (T)v;

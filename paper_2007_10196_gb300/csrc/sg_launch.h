@@ -39,8 +39,10 @@ struct Launch {
     // alpha slot 0 of every grid <- max |u0| (slots must be zero); flags non-finite values.
     static cudaError_t alpha_init(const GridDesc* grids, int ngrids, long long max_pts,
                                   unsigned long long* alpha, int* flags, cudaStream_t s);
-    // u0 of one grid <- p0 + p1 sin(p2 sum x + p3) (FP32: also the compensation term u3).
-    static cudaError_t restrict_sine(const GridDesc& g, int dim, const double* p, cudaStream_t s);
+    // u0 of every grid of the device table <- p0 + p1 sin(p2 sum x + p3) (FP32: also the
+    // compensation term u3), one launch; max_npts = the largest grid's points.
+    static cudaError_t restrict_sine(const GridDesc* grids, int ngrids, long long max_npts, int dim, const double* p,
+                                     cudaStream_t s);
     // One prolongation axis; acc != nullptr fuses "acc += coeff * result"; zero_bc: values
     // beyond the ends of the axis are 0 (Vlasov-Poisson v, every Vlasov-Boltzmann axis), else
     // periodic.

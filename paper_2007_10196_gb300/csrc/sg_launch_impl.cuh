@@ -242,8 +242,12 @@ cudaError_t Launch<T>::alpha_init(const GridDesc* grids, int ngrids, long long m
 }
 
 template <class T>
-cudaError_t Launch<T>::restrict_sine(const GridDesc& g, int dim, const double* p, cudaStream_t s) {
-    sg_restrict_sine_kernel<T><<<detail::grid_for(g.npts, 256), 256, 0, s>>>(g, dim, p[0], p[1], p[2], p[3]);
+cudaError_t Launch<T>::restrict_sine(const GridDesc* grids, int ngrids, long long max_npts, int dim, const double* p,
+                                     cudaStream_t s) {
+    if (ngrids < 1) return cudaSuccess;
+    if (ngrids > 65535) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)detail::grid_for(max_npts, 256), (unsigned)ngrids);
+    sg_restrict_sine_kernel<T><<<grid, 256, 0, s>>>(grids, dim, p[0], p[1], p[2], p[3]);
     return cudaGetLastError();
 }
 
