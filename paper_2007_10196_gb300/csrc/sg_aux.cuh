@@ -27,13 +27,21 @@ __global__ void __launch_bounds__(SG_NT) sg_alpha_init_kernel(const GridDesc* gr
     }
 }
 
-// Per-instance time-step control, one thread per instance.  commit_only = 0 at the start of
-// a step: adds the previous (pending) step to t, then sets dt for the next step or marks the
-// instance inactive.  commit_only = 1 after the last step: only adds the pending step.
+// max over a warp (every lane gets it); exact, and like fmax it ignores a NaN operand
+__device__ __forceinline__ double warp_fmax(double a) {
+    for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    return a;
+}
+
+// Per-instance time-step control, one warp per instance (the lanes split the maxima over the
+// instance's grids; the max is exact in any order).  commit_only = 0 at the start of a step:
+// adds the previous (pending) step to t, then sets dt for the next step or marks the instance
+// inactive.  commit_only = 1 after the last step: only adds the pending step.
 static __global__ void sg_dt_kernel(InstState* inst, int ninst, const GridDesc* grids,
                              const unsigned long long* alpha, PhysParams ph, int commit_only, int* flags) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ninst) return;
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= ninst) return;  // the whole warp
     InstState s = inst[i];
     if (s.pending) {
         s.t = s.last ? s.t_end : s.t + s.dt;
@@ -50,10 +58,11 @@ static __global__ void sg_dt_kernel(InstState* inst, int ninst, const GridDesc* 
             for (int k = 0; k < ph.dim; ++k) {
                 double a = 0.0;
                 if (ph.pde == 1 || (ph.pde == 2 && k == 1)) {  // Burgers max|u|; Vlasov-Poisson max|E|
-                    for (int g = s.grid0; g < s.grid0 + s.ngrids; ++g)
+                    for (int g = s.grid0 + lane; g < s.grid0 + s.ngrids; g += 32)
                         a = fmax(a, ph.alpha_f32 ? (double)alpha_dec<float>(alpha[g * 3]) : bitsd(alpha[g * 3]));
+                    a = warp_fmax(a);
                 } else if (ph.pde == 2) {  // Vlasov-Poisson along x: max |v_j|, at an end node
-                    for (int g = s.grid0; g < s.grid0 + s.ngrids; ++g) {
+                    for (int g = s.grid0 + lane; g < s.grid0 + s.ngrids; g += 32) {
                         const GridDesc& G = grids[g];
                         if (ph.alpha_f32) {
                             const float v0 = (float)G.lo[1], v1 = (float)G.lo[1] + (float)(G.n[1] - 1) * (float)G.h[1];
@@ -63,6 +72,7 @@ static __global__ void sg_dt_kernel(InstState* inst, int ninst, const GridDesc* 
                             a = fmax(a, fmax(fabs(v0), fabs(v1)));
                         }
                     }
+                    a = warp_fmax(a);
                 } else if (ph.pde == 3) {  // Vlasov-Boltzmann: static, from the instance's grids
                     a = s.alpha_vb[k];
                 } else {
@@ -74,8 +84,10 @@ static __global__ void sg_dt_kernel(InstState* inst, int ninst, const GridDesc* 
         }
         s.last = 0;
         if (!(dt > 0.0) || !isfinite(dt)) {  // e.g. alpha overflowed: stop instead of stalling
-            atomicOr(flags + SG_FLAG_BADDT, 1);
-            inst[i] = s;  // inactive, nothing pending
+            if (lane == 0) {
+                atomicOr(flags + SG_FLAG_BADDT, 1);
+                inst[i] = s;  // inactive, nothing pending
+            }
             return;
         }
         if (dt >= s.t_end - s.t) {  // shortened last step: the run ends exactly at t_end
@@ -87,7 +99,7 @@ static __global__ void sg_dt_kernel(InstState* inst, int ninst, const GridDesc* 
         s.pending = 1;
         s.active = 1;
     }
-    inst[i] = s;
+    if (lane == 0) inst[i] = s;
 }
 
 // ------------------------------------------------------------------------------------

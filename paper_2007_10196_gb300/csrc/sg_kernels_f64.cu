@@ -12,7 +12,7 @@ template struct Launch<double>;
 cudaError_t launch_dt(InstState* inst, int ninst, const GridDesc* grids, const unsigned long long* alpha,
                       const PhysParams& ph, int commit_only, int* flags, cudaStream_t s) {
     if (ninst < 1) return cudaSuccess;
-    sg_dt_kernel<<<(ninst + 127) / 128, 128, 0, s>>>(inst, ninst, grids, alpha, ph, commit_only, flags);
+    sg_dt_kernel<<<(ninst + 3) / 4, 128, 0, s>>>(inst, ninst, grids, alpha, ph, commit_only, flags);  // a warp per instance
     return cudaGetLastError();
 }
 
