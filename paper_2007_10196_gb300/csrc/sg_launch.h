@@ -23,9 +23,10 @@ void sweep_tile(const int* n, int* te);
 
 template <class T>
 struct Launch {
-    // Dynamic shared memory (bytes) of the stage kernel: the padded-box kernel (d <= 3) holds
-    // 2 box + flux elements, the line-sweep kernel (d >= 4; variant 2) box + flux (line buffer
-    // and accumulators, from line_footprint) and flux ints (per-line offsets).
+    // Dynamic shared memory (bytes) of the stage kernel: the padded-box and one-line sweep
+    // kernels (d <= 3) hold 2 box + flux elements, the two-line sweep kernel (d = 3, variant 3)
+    // box + flux, the line-sweep kernel (d >= 4; variant 2) box + flux (line buffer and
+    // accumulators, from line_footprint) and flux ints (per-line offsets).
     static size_t stage_smem(int dim, int ppt, long long box, long long flux, int variant = 0);
     // Raises the kernel's shared-memory limit and returns resident blocks per SM (0 if the
     // configuration cannot run).  variant: 0 = the default kernel of the dimension (d = 3:

@@ -88,6 +88,7 @@ inline int grid_for(long long n, int threads) {
 template <class T>
 size_t Launch<T>::stage_smem(int dim, int ppt, long long box, long long flux, int variant) {
     (void)ppt;
+    if (dim == 3 && variant == 3) return sizeof(T) * (size_t)(box + flux);  // u only (split in the sweep)
     if (dim <= 3 && variant != 2) return sizeof(T) * (size_t)(2 * box + flux);
     return sizeof(T) * (size_t)(box + flux) + sizeof(int) * (size_t)flux;  // + per-line offsets
 }
@@ -160,13 +161,14 @@ int prepare_sweep2(size_t smem) {
     } else {
         const void* kk[4] = {(const void*)sg_stage_sweep3x2_kernel<false, 1>, (const void*)sg_stage_sweep3x2_kernel<true, 1>,
                              (const void*)sg_stage_sweep3x2_kernel<false, 2>, (const void*)sg_stage_sweep3x2_kernel<true, 2>};
-        // 72% of the unified L1/shared array as shared memory (164 KB: 5 blocks of ~31 KB per SM)
-        // and the rest as L1 (~92 KB): the update's loads of U and D then mostly hit the lines
-        // the same tile's gather brought in.  Measured faster than 6 blocks with a 28 KB L1
-        // (the register limit) or 4 blocks with a 124 KB L1.
+        // 44% of the unified L1/shared array as shared memory (100 KB: 5 blocks of ~20 KB per SM)
+        // and the rest as L1 (~156 KB): the update's loads of U and D then mostly hit the lines
+        // the same tile's gather brought in.  Measured slightly faster than 6 blocks (the
+        // register limit) with a 92 or 124 KB L1, and 5% faster than the two-array box at 6
+        // blocks with a 28 KB L1.
         for (const void* k : kk) {
             if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-                cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 72) != cudaSuccess) {
+                cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 44) != cudaSuccess) {
                 cudaGetLastError();
                 return 0;
             }

@@ -6,7 +6,10 @@
 // branch, and each WENO5 / Lax-Friedrichs operation of the sweep is one packed f32x2
 // instruction for the two lines.  A block of SG_NT3H = 96 threads holds the 96 line pairs of an
 // 8 x 8 x 8 tile (3 axes x 64 lines / 2); the gather and the update loop over the tile with
-// that many threads.
+// that many threads.  The box holds the stencil input u only (one array, 15 x 14 x 14 floats for
+// a full tile): the sweep forms the Lax-Friedrichs split of each value it reads (for Burgers the
+// same operations as Weno<float>::split_burgers), carrying the last value read into the next
+// interface, so that a block needs ~19 KB of shared memory and leaves room for a large L1.
 #pragma once
 #include "sg_stage.cuh"
 
@@ -95,9 +98,8 @@ __device__ __forceinline__ float2 sweep_flux2(const SweepSide2& P, const SweepSi
 template <bool ZB, int RUN>
 __global__ void __launch_bounds__(SG_NT3H, 6) sg_stage_sweep3x2_kernel(const StageArgs A) {
     extern __shared__ __align__(16) unsigned char sg_smem_raw[];
-    float* bp = reinterpret_cast<float*>(sg_smem_raw);  // f^+ (Burgers) or u (advection)
-    float* bm = bp + A.box_elems;                        // f^-
-    float* Dk = bm + A.box_elems;                        // 3 x SG_DK_AXIS flux differences
+    float* bp = reinterpret_cast<float*>(sg_smem_raw);  // the stencil input u
+    float* Dk = bp + A.box_elems;                        // 3 x SG_DK_AXIS flux differences
 
     const int tid = threadIdx.x;
     const PhysParams& ph = A.phys;
@@ -145,22 +147,12 @@ __global__ void __launch_bounds__(SG_NT3H, 6) sg_stage_sweep3x2_kernel(const Sta
         const int B0 = R0 | 1;    // odd row stride
         const int B1 = e[1] + 6;
         const float alpha_b = alpha_dec<float>(A.alpha[w.grid * 3 + A.stage]);
-        const float half_alpha = 0.5f * alpha_b;
         FDiv fR0, fe0, fe1;
         fR0.init(R0);
         fe0.init(e[0]);
         fe1.init(e[1]);
 
-        auto put = [&](int bidx, float v) {  // split of one loaded stencil value into the box
-            if (burgers) {
-                float fp, fm;
-                Weno<float>::split_burgers(v, half_alpha, fp, fm);
-                bp[bidx] = fp;
-                bm[bidx] = fm;
-            } else {
-                bp[bidx] = v;
-            }
-        };
+        auto put = [&](int bidx, float v) { bp[bidx] = v; };  // the stencil input u
         // ---- 1) gather the padded box (as sg_stage_sweep3_kernel: float4 chunks where the tile
         // is 8 wide at a 4-aligned x origin of a row length divisible by 4 on 16-byte aligned
         // arrays, single values otherwise; zero chunks beyond the ends of zero-boundary axes)
@@ -333,19 +325,22 @@ __global__ void __launch_bounds__(SG_NT3H, 6) sg_stage_sweep3x2_kernel(const Sta
                 const float ak = k == 0 ? adv[0] : (k == 1 ? adv[1] : adv[2]);
                 const float alpha = burgers ? alpha_b : (ak < 0.f ? -ak : ak);
                 const float cp = 0.5f * (ak + alpha), cm = 0.5f * (ak - alpha);
-                // f^+ / f^- of both lines at box coordinate j along them
-                auto fplus = [&](int j) -> float2 {
-                    const float2 v = make_float2(bp[ba + j * S], bp[bb + j * S]);
-                    return burgers ? v : sg_mul2(sg_f2(cp), v);
+                // u of both lines at box coordinate j along them, and its LF split (Burgers:
+                // f^+- = u (u/4 +- alpha/2), Weno<float>::split_burgers lane by lane)
+                auto uval = [&](int j) -> float2 { return make_float2(bp[ba + j * S], bp[bb + j * S]); };
+                const float2 ha2 = sg_f2(0.5f * alpha);
+                auto fplus = [&](float2 v) -> float2 {
+                    return burgers ? sg_mul2(v, sg_fma2(sg_f2(0.25f), v, ha2)) : sg_mul2(sg_f2(cp), v);
                 };
-                auto fminus = [&](int j) -> float2 {
-                    if (burgers) return make_float2(bm[ba + j * S], bm[bb + j * S]);
-                    return sg_mul2(sg_f2(cm), make_float2(bp[ba + j * S], bp[bb + j * S]));
+                auto fminus = [&](float2 v) -> float2 {
+                    return burgers ? sg_mul2(v, sg_fma2(sg_f2(0.25f), v, sg_neg2(ha2))) : sg_mul2(sg_f2(cm), v);
                 };
                 SweepSide2 Pw, Mw;
                 // interface 0 (between local points -1 and 0): f^+ at box 0..4, f^- mirrored at box 5..1
-                Pw.init(fplus(0), fplus(1), fplus(2), fplus(3), fplus(4), ep);
-                Mw.init(fminus(5), fminus(4), fminus(3), fminus(2), fminus(1), ep);
+                const float2 u0 = uval(0), u1 = uval(1), u2 = uval(2), u3 = uval(3), u4 = uval(4);
+                float2 uc = uval(5);  // u at box i + 4 of interface i
+                Pw.init(fplus(u0), fplus(u1), fplus(u2), fplus(u3), fplus(u4), ep);
+                Mw.init(fminus(uc), fminus(u4), fminus(u3), fminus(u2), fminus(u1), ep);
                 float* Da = Dk + k * SG_DK_AXIS + 9 * la;
                 float* Db = Dk + k * SG_DK_AXIS + 9 * lb;
                 float2 Fprev = sweep_flux2(Pw, Mw, ph.scheme);
@@ -353,8 +348,10 @@ __global__ void __launch_bounds__(SG_NT3H, 6) sg_stage_sweep3x2_kernel(const Sta
 #pragma unroll
                 for (int i = 1; i <= 8; ++i) {
                     if (i > ek) break;
-                    Pw.push_back(fplus(i + 4), ep);
-                    Mw.push_front(fminus(i + 5), ep);
+                    const float2 un = uval(i + 5);
+                    Pw.push_back(fplus(uc), ep);
+                    Mw.push_front(fminus(un), ep);
+                    uc = un;
                     const float2 F = sweep_flux2(Pw, Mw, ph.scheme);
                     const float2 D = sg_mul2(sg_sub2(F, Fprev), r2);
                     Da[i - 1] = D.x;
