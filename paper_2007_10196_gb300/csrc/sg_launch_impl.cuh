@@ -161,11 +161,12 @@ int prepare_sweep2(size_t smem) {
     } else {
         const void* kk[4] = {(const void*)sg_stage_sweep3x2_kernel<false, 1>, (const void*)sg_stage_sweep3x2_kernel<true, 1>,
                              (const void*)sg_stage_sweep3x2_kernel<false, 2>, (const void*)sg_stage_sweep3x2_kernel<true, 2>};
-        // 44% of the unified L1/shared array as shared memory (100 KB: 5 blocks of ~20 KB per SM)
-        // and the rest as L1 (~156 KB): the update's loads of U and D then mostly hit the lines
-        // the same tile's gather brought in.  Measured slightly faster than 6 blocks (the
-        // register limit) with a 92 or 124 KB L1, and 5% faster than the two-array box at 6
-        // blocks with a 28 KB L1.
+        // A small preferred shared-memory carveout: the driver takes the smallest configuration
+        // that holds the 6 blocks of ~20 KB the registers allow (ncu: 6 blocks per SM, both
+        // limits), and the rest of the unified array (~124 KB) serves as L1, where the update's
+        // loads of U and D find the lines the same tile's gather brought in.  Measured: 44% and
+        // 58% alike, 72% (~92 KB of L1) 0.6% slower, and the two-array box at 6 blocks with a
+        // 28 KB L1 5% slower.
         for (const void* k : kk) {
             if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
                 cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 44) != cudaSuccess) {
