@@ -217,8 +217,14 @@ __global__ void __launch_bounds__(32 * CY, 2) sg_combine_last_axis_f32x2_kernel(
             auto centre0 = [&](const View& v) -> int { return v.lr == 0 ? j0 + 2 : chunk_centre0(j0, v.lr); };
             auto first = [&](const View& v, float2 (&w)[5]) {
                 const int c0 = centre0(v);
+                if (VEC && c0 >= 2 && c0 + 2 < v.n) {  // interior rows: no wrap, no zero boundary
+                    const float* p = v.col + (long long)(c0 - 2) * below;
 #pragma unroll
-                for (int k = 0; k < 5; ++k) w[k] = row(v, c0 - 2 + k);
+                    for (int k = 0; k < 5; ++k, p += below) w[k] = __ldg(reinterpret_cast<const float2*>(p));
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) w[k] = row(v, c0 - 2 + k);
+                }
             };
             View nv = view(0);
             float2 nw[5];
