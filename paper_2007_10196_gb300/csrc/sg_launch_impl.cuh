@@ -247,11 +247,14 @@ cudaError_t Launch<T>::alpha_init(const GridDesc* grids, int ngrids, long long m
 template <class T>
 cudaError_t Launch<T>::restrict_sine(const GridDesc* grids, int ngrids, long long max_npts, int dim, const double* p,
                                      cudaStream_t s) {
-    if (ngrids < 1) return cudaSuccess;
-    if (ngrids > 65535) return cudaErrorInvalidValue;
-    const dim3 grid((unsigned)detail::grid_for(max_npts, 256), (unsigned)ngrids);
-    sg_restrict_sine_kernel<T><<<grid, 256, 0, s>>>(grids, dim, p[0], p[1], p[2], p[3]);
-    return cudaGetLastError();
+    for (int g0 = 0; g0 < ngrids; g0 += 65535) {  // gridDim.y <= 65535 grids per launch
+        const int ng = ngrids - g0 < 65535 ? ngrids - g0 : 65535;
+        const dim3 grid((unsigned)detail::grid_for(max_npts, 256), (unsigned)ng);
+        sg_restrict_sine_kernel<T><<<grid, 256, 0, s>>>(grids + g0, dim, p[0], p[1], p[2], p[3]);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <class T>
