@@ -602,85 +602,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) sg_combine_last_a
     }
 }
 
-// One prolongation axis, J consecutive fine outputs per thread: the five coarse values around
-// the current centre slide along the axis and their s-independent part is formed once per
-// centre (InterpWin::prepare), so the r fine nodes that share a centre pay only for eval().
-// Axis with stride `below` > 1: threads run along `below`, blockIdx.y over (above, chunk of J
-// fine nodes).  below == 1: threads run over the chunks of a row, blockIdx.y over `above`.
-// zero_bc: values beyond the ends of the axis are 0 (else periodic).
-template <class T, int J>
-__global__ void __launch_bounds__(256) sg_prolong_axis_win_kernel(const T* __restrict__ in, T* __restrict__ out,
-                                                                  long long below, int n, int nf, long long above,
-                                                                  int r, double eps, int lagrange, int zero_bc) {
-    const T e12 = sg_eps4<T>(eps);
-    const int nchunks = (nf + J - 1) / J;
-    const int lr = __ffs(r) - 1;
-    const T inv_r = pow2_neg<T>(lr);
-    auto centre = [&](int jf, int& ic, T& s) {  // as fine_to_coarse
-        const int i = jf >> lr, m = jf & (r - 1);
-        if (2 * m < r) {
-            ic = i;
-            s = (T)m * inv_r;
-        } else {
-            ic = i + 1;
-            s = (T)(m - r) * inv_r;
-        }
-    };
-    auto run = [&](const T* col, T* ocol, long long stride, int j0) {
-        int cur;
-        T s0;
-        centre(j0, cur, s0);
-        auto at = [&](int c) -> T {  // c in [-2, n + 2]
-            if (zero_bc && (c < 0 || c >= n)) return T(0);
-            return col[wrap_index(c, n) * stride];
-        };
-        InterpWin<T> W;
-        W.w0 = at(cur - 2);
-        W.w1 = at(cur - 1);
-        W.w2 = at(cur);
-        W.w3 = at(cur + 1);
-        W.w4 = at(cur + 2);
-        W.prepare(e12, lagrange);
-#pragma unroll 1
-        for (int j = 0; j < J; ++j) {
-            const int jf = j0 + j;
-            if (jf >= nf) break;
-            int ic;
-            T s;
-            centre(jf, ic, s);
-            if (ic != cur) {  // centres advance by one coarse node at a time (r >= 2)
-                W.w0 = W.w1;
-                W.w1 = W.w2;
-                W.w2 = W.w3;
-                W.w3 = W.w4;
-                W.w4 = at(ic + 2);
-                W.prepare(e12, lagrange);
-                cur = ic;
-            }
-            ocol[jf * stride] = W.eval(s, (T)eps, lagrange);
-        }
-    };
-    if (below == 1) {
-        for (long long hi = blockIdx.y; hi < above; hi += gridDim.y)
-            for (int ch = blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks; ch += gridDim.x * blockDim.x)
-                run(in + hi * n, out + hi * nf, 1, ch * J);
-        return;
-    }
-    const long long rows = above * nchunks;
-    for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
-        const long long hi = row / nchunks;  // once per block row
-        const int ch = (int)(row - hi * nchunks);
-        for (long long lo = blockIdx.x * (long long)blockDim.x + threadIdx.x; lo < below;
-             lo += (long long)gridDim.x * blockDim.x)
-            run(in + hi * below * n + lo, out + hi * below * nf + lo, below, ch * J);
-    }
-}
-
 // One prolongation pass over many grids (Step 3, axes 0..d-2, Section 2.2.1): thread u of
 // the pass takes unit u -- J consecutive fine nodes of one line -- of the task whose unit range
-// holds it, and slides the coarse window along the line as sg_prolong_axis_win_kernel does
-// (the same arithmetic per output).  Consecutive units are consecutive columns (below > 1: the
-// loads of a warp are coalesced) or consecutive chunks of one row (below = 1).
+// holds it, and slides the five coarse values around the current centre along the line: their
+// s-independent part is formed once per centre (InterpWin::prepare), so the r fine nodes that
+// share a centre pay only for eval().  Consecutive units are consecutive columns (below > 1:
+// the loads of a warp are coalesced) or consecutive chunks of one row (below = 1).
 template <class T, int J>
 __global__ void __launch_bounds__(256) sg_prolong_multi_kernel(const ProlongTask* __restrict__ tasks, int ntasks,
                                                                long long nunits, double eps, int lagrange) {

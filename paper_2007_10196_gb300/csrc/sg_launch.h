@@ -68,10 +68,6 @@ struct Launch {
     static cudaError_t accumulate(const T* u, double* acc, double coeff, long long n, cudaStream_t s);
     // out[j] = u[idx[j]], j < n (device arrays; indices already checked)
     static cudaError_t gather(const T* u, const long long* idx, T* out, long long n, cudaStream_t s);
-    // One prolongation axis, J = 8 consecutive fine nodes per thread sharing the coarse window;
-    // zero_bc as for prolong_axis.
-    static cudaError_t prolong_axis_win(const T* in, T* out, long long below, int min_, int nf, long long above,
-                                        int r, double eps, int lagrange, int zero_bc, cudaStream_t s);
     // One prolongation pass over the ntasks tasks of a device table (their unit ranges cover
     // [0, nunits)), J = 8 fine nodes per unit.
     static cudaError_t prolong_multi(const ProlongTask* tasks, int ntasks, long long nunits, double eps, int lagrange,

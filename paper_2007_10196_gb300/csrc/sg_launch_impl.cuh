@@ -319,23 +319,6 @@ cudaError_t Launch<T>::gather(const T* u, const long long* idx, T* out, long lon
 }
 
 template <class T>
-cudaError_t Launch<T>::prolong_axis_win(const T* in, T* out, long long below, int min_, int nf, long long above,
-                                        int r, double eps, int lagrange, int zero_bc, cudaStream_t s) {
-    constexpr int J = 8;
-    const long long nchunks = (nf + J - 1) / J;
-    dim3 grid;
-    if (below == 1) {
-        grid.x = (unsigned)std::min<long long>((nchunks + 255) / 256, 65535);
-        grid.y = (unsigned)std::min<long long>(above, 65535);
-    } else {
-        grid.x = (unsigned)std::min<long long>((below + 255) / 256, 65535);
-        grid.y = (unsigned)std::min<long long>(above * nchunks, 65535);
-    }
-    sg_prolong_axis_win_kernel<T, J><<<grid, 256, 0, s>>>(in, out, below, min_, nf, above, r, eps, lagrange, zero_bc);
-    return cudaGetLastError();
-}
-
-template <class T>
 cudaError_t Launch<T>::prolong_multi(const ProlongTask* tasks, int ntasks, long long nunits, double eps, int lagrange,
                                      cudaStream_t s) {
     if (ntasks < 1 || nunits < 1) return cudaSuccess;
