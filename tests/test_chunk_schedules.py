@@ -75,3 +75,25 @@ def test_ragged_chunks_only_for_small_ratios():
             nf = nr << nl
             if nf % 8:
                 assert nl <= 2 and all((1 << lr) <= 4 for lr in range(0, nl + 1))
+
+
+@pytest.mark.parametrize("run", [1, 2])
+@pytest.mark.parametrize("nitems,nblocks", [(1, 760), (759, 760), (1520, 760), (1521, 760), (51101, 760),
+                                            (7, 3), (100, 912)])
+def test_work_item_runs_visit_every_item_once(nitems, nblocks, run):
+    # the two-line stage kernel's traversal: block b takes runs of RUN consecutive items, run
+    # c = b, b + nblocks, ...; the host takes RUN = 2 only with at least two items per block
+    if run == 2 and nitems < 2 * nblocks:
+        pytest.skip("the host launches single items here")
+    begin = 3  # a launch covers items [begin, begin + nitems)
+
+    def next_item(i):
+        return i + 1 if (i - begin + 1) % run else i + 1 + (nblocks - 1) * run
+
+    seen = []
+    for b in range(nblocks):
+        it = begin + b * run
+        while it < begin + nitems:
+            seen.append(it)
+            it = next_item(it)
+    assert sorted(seen) == list(range(begin, begin + nitems))
