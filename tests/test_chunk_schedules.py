@@ -10,6 +10,8 @@ centre computation by closed forms:
   r >= 16: all 8 nodes share one centre and their offsets step by 1 / r.
 Both are checked here against the definition, for every chunk of several axis lengths, and so is
 the row range the kernels read ([-2, n + 2], inside the periodic wrap's [-n, 2n) for n >= 3).
+The last test checks the two-line stage kernel's traversal of a launch's work items in runs of
+consecutive items: every item once.
 """
 import math
 from fractions import Fraction
